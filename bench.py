@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the data-parallel pc-engine: pattern-mode updates per second.
+
+Workload: the far-field 4-mode configuration (probe 128 x 128, 4 probe modes,
+900 Fermat-spiral positions, 640 x 640 object, 5 % bandwidth, sigma = 1.5,
+1e6 photons) from the seeded generator. One step is one full iteration of the
+engine over all positions: exit waves, propagation, the Gaussian intensity
+model and modulus constraint, back-propagation, the object / probe
+scatter-add update, the complex constraint (active in every timed step) and
+the FP64 error. Inputs are resident in HBM when timing starts; L2 is flushed
+with a 256 MiB write before every timed step (outside the step's events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an independent
+replica of the workload (the engine does not shard one reconstruction across
+GPUs); the value is the sum over ranks divided by the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pattern-mode updates/s"
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from synth import make_problem
+
+    prob = make_problem(1)
+    params = dict(prob.params, windows=[(1, 1 << 30)])  # complex constraint in every step
+    return prob, params
+
+
+def config_of(prob, extra=None):
+    p = prob.params
+    cfg = {"workload": "far-field 4-mode pc-engine iteration (probe 128^2, K=4, N=900 Fermat spiral, "
+                       "object 640^2, 5% bandwidth, sigma 1.5, 1e6 photons)",
+           "M": p["M"], "K": p["K"], "N": p["N"], "object": [p["obj_h"], p["obj_w"]], "geometry": p["geometry"],
+           "blur": p["blur_domain"], "kernel_size": p["kernel_size"], "complex_constraint": "every step",
+           "step": "one iteration over all positions", "l2": "flushed before each timed step (256 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def algorithmic_flops(M, K, N, near):
+    """Nominal FLOPs of one iteration: 5 M^2 log2(M^2) per 2-D FFT (2 per pattern-mode in the far
+    field, 4 in the near field), 26 FLOP per pixel per mode and 55 FLOP per pixel per pattern for
+    the elementwise work (exit wave, modulus, blur, ratio, contributions, error)."""
+    fft = 5.0 * M * M * math.log2(M * M)
+    per_mode = (4 if near else 2) * fft + 26.0 * M * M
+    return N * K * per_mode + N * 55.0 * M * M
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, value, device=None):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(prob, params, n_positions, iterations=1):
+    import oracle
+
+    prm = oracle.Params.from_dict(dict(params, N=n_positions))
+    t0 = time.perf_counter()
+    oracle.iterate(prob.I[:n_positions], prob.positions[:n_positions], prob.O0, prob.P0, prm, iterations)
+    dt = time.perf_counter() - t0
+    return n_positions * prob.K * iterations / dt, dt
+
+
+def traffic_record(kernel_tag):
+    """DRAM bytes per launch of the fused kernel from a committed ncu summary, if it was taken on
+    the current kernel source (hash match); None otherwise."""
+    path = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except ValueError:
+        return None
+    if rec.get("source_sha256") != kernel_tag:
+        return None
+    return rec.get("dram_bytes_per_launch_full_size")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fft.cuh", "pc_fused.cu", "engine.h"):
+        h.update(open(os.path.join(ROOT, "paper_2406_06640_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    prob, params = workload()
+    n_pos = 100
+    for _ in range(args.warmup):
+        oracle_rate(prob, params, n_pos)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(prob, params, n_pos)
+        times.append(dt)
+    total = sum(times)
+    units = n_pos * prob.K * args.steps
+    value = units / total
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": config_of(prob, {"sample": f"each step: one oracle iteration over the first {n_pos} "
+                                                 f"of the {prob.N} positions"}),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of one FP64 oracle iteration over {n_pos} positions x "
+                                       f"{prob.K} modes (numpy/scipy, single-threaded)"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    ws, rank, local = dist_setup(args)
+    import torch
+
+    from paper_2406_06640_gb300.engine import Reconstruction
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: a CUDA device is required (no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prob, params = workload()
+    stream = torch.cuda.current_stream(dev)
+    I = torch.from_numpy(prob.I).to(dev)
+    O = torch.from_numpy(prob.O0.astype(np.complex64)).to(dev)
+    P = torch.from_numpy(prob.P0.astype(np.complex64)).to(dev)
+    rec = Reconstruction(params, I, prob.positions, stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    units_per_step = prob.N * prob.K
+
+    for _ in range(max(args.warmup, 3)):
+        rec.iterate(O, P, 1)
+    torch.cuda.synchronize(dev)
+    rec.profile(True)
+    rec.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        rec.iterate(O, P, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    fused_ms, fused_launches = rec.profile_read()
+    rec.profile(False)
+    E_last = rec.error()
+    t_max = max_over_ranks(ws, total_ms, dev)
+    value = ws * units_per_step * args.steps / (t_max / 1e3)
+
+    # roofline of the dominant (fused) kernel: algorithmic FLOPs per launch / its event-timed duration
+    flops = algorithmic_flops(prob.M, prob.K, prob.N, params["geometry"] == "near")
+    fused_avg_s = fused_ms / max(fused_launches, 1) / 1e3
+    achieved = flops / fused_avg_s / 1e12
+    peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = traffic_record(kernel_source_hash())
+
+    # end to end through the public API: object + probe state from pinned host memory, one
+    # iteration, error metric and state back to pinned host memory, every step
+    O_h = torch.from_numpy(prob.O0.astype(np.complex64)).pin_memory()
+    P_h = torch.from_numpy(prob.P0.astype(np.complex64)).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    t_e2e = 0.0
+    for k in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        O.copy_(O_h, non_blocking=True)
+        P.copy_(P_h, non_blocking=True)
+        rec.iterate(O, P, 1)
+        O_h.copy_(O, non_blocking=True)
+        P_h.copy_(P, non_blocking=True)
+        rec.error()  # synchronises the stream; reads E back to the host
+        if k > 0:  # first round trip is a warm-up
+            t_e2e += time.perf_counter() - t0
+    t_e2e = max_over_ranks(ws, t_e2e, dev)
+    e2e_value = ws * units_per_step * e2e_steps / t_e2e
+    state_bytes = O.numel() * 8 + P.numel() * 8
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, dt = oracle_rate(prob, params, prob.N)
+        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle iteration of the full workload ({prob.N} positions x {prob.K} modes, "
+                         f"{dt:.1f} s, numpy/scipy single-threaded)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(prob, {"parallelism": f"replicas{ws}" if ws > 1 else "single GPU"}),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "pc_fused_kernel<128, far>",
+                             "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FMA pipe, max clock)",
+                             "flops_per_launch": flops, "avg_launch_ms": fused_avg_s * 1e3},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
+                        "d2h_bytes_per_step": state_bytes + 8},
+                "gpu_launches": args.steps * rec.launches_per_iteration(True),
+                "clocks": clocks, "nrmse_last": E_last, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
+        print(json.dumps(line), flush=True)
+    rec.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * ptycho.h -- C ABI of the GB300 data-parallel partially coherent ptychographic engine.
+ *
+ * The engine runs the paper's partially coherent ptychographic iteration
+ * (Xu, Ning et al., "A high-performance reconstruction method for partially
+ * coherent ptychography", arXiv 2406.06640) in its simultaneous form: every
+ * scan position n uses the same object O and probe modes P_k, and the object
+ * and probe move by a normalised scatter-add of all positions' corrections.
+ *
+ * One iteration t (1-based):
+ *   psi_{n,k} = P_k . o_n,  o_n the M x M box of O at positions[n]   (Eq. 1, Fig. 1)
+ *   Psi_{n,k} = far field: centred 2-D DFT of psi (Eq. 1);
+ *               near field: IDFT(DFT(psi) H), H = exp(-i pi (u^2 + v^2) / (M F)),
+ *               u, v the signed integer frequencies (Sec. 3.1, near-field setup)
+ *   amplitude blur (default, Eq. 6):  A^G = sqrt(sum_k |Psi_k|^2) (x) g,
+ *       Ihat = (A^G)^2, R = sqrt(I_n) / (A^G + eps)
+ *   intensity blur (Eq. 2):           I_m = (sum_k |Psi_k|^2) (x) g,
+ *       Ihat = I_m, R = sqrt(I_n) / sqrt(I_m + eps^2)
+ *       g: Eq. 7, kernel_size x kernel_size, sigma1 along x (columns),
+ *       sigma2 along y (rows), normalised to sum 1, zero padding; sigma = 0
+ *       makes that axis a delta (the coherent engine)
+ *   Psi' = R Psi (Fig. 1 box 1), psi' = inverse propagation, dpsi = psi' - psi
+ *   O   += beta_obj   sum_n conj(P) dpsi / (D_O + delta_obj   max D_O),  D_O = sum_n sum_k |P_k|^2
+ *   P_k += beta_probe sum_n conj(o_n) dpsi_k / (D_P + delta_probe max D_P), D_P = sum_n |o_n|^2
+ *       (pixels with a zero denominator are left unchanged; the probe moves
+ *        from iteration probe_update_start on)
+ *   inside a complex-constraint window: Eqs. 9-11 on the new object, C_n
+ *       clamped to [cbar_min, cbar_max] (Sec. 4.8) and averaged per pixel
+ *       over the covering boxes
+ *   E_t = sqrt(sum (Ihat - I)^2 / sum I^2) in FP64 (the NRMSE of Sec. 4.2),
+ *       evaluated on the state before the update of iteration t.
+ *
+ * Layouts: complex values are interleaved float pairs (re, im) = complex64.
+ * Object: obj_h x obj_w, row-major. Probe: K x M x M, row-major per mode.
+ * Intensities: N x M x M float32; far field in the detector-centred frame
+ * (zero frequency at (M/2, M/2)); near field in the detector plane.
+ * Positions: N pairs (row, col) of int32, the top-left corner of each box;
+ * every box must lie inside the object.
+ *
+ * Errors: every call returns a ptycho_status; no C++ exception crosses the
+ * ABI. ptycho_last_error() returns a message for the calling thread's last
+ * failure. Calls on one plan must not run concurrently from several threads.
+ */
+#ifndef PTYCHO_H_
+#define PTYCHO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ptycho_plan_s* ptycho_plan_t; /* opaque, owned by the library */
+
+typedef enum {
+  PTYCHO_OK = 0,
+  PTYCHO_EINVAL = 1,       /* invalid parameter, size or position */
+  PTYCHO_ENOMEM = 2,       /* device allocation failed */
+  PTYCHO_ECUDA = 3,        /* a CUDA call failed (message in ptycho_last_error) */
+  PTYCHO_EUNSUPPORTED = 4, /* valid request this build does not handle */
+  PTYCHO_ENUMERIC = 5,     /* non-finite input or non-finite error metric */
+  PTYCHO_ETIMEOUT = 6      /* a bounded device-side wait gave up */
+} ptycho_status;
+
+enum { PTYCHO_FARFIELD = 0, PTYCHO_NEARFIELD = 1 };
+enum { PTYCHO_BLUR_AMPLITUDE = 0 /* Eq. 6 */, PTYCHO_BLUR_INTENSITY = 1 /* Eq. 2 */ };
+
+typedef struct {
+  int32_t M;            /* probe = box = detector side, power of two, 8..128 */
+  int32_t K;            /* probe modes (mixed state, Sec. 4.4), 1..8 */
+  int32_t N;            /* scan positions, >= 1 */
+  int32_t obj_h, obj_w; /* object size, >= M */
+  int32_t geometry;     /* PTYCHO_FARFIELD or PTYCHO_NEARFIELD */
+  int32_t blur_domain;  /* PTYCHO_BLUR_AMPLITUDE (default) or PTYCHO_BLUR_INTENSITY */
+  double fresnel_F;     /* near field: F = M dx^2 / (lambda z) > 0; ignored in the far field */
+  double sigma1;        /* Eq. 7 blur width along x (columns), pixels, >= 0 */
+  double sigma2;        /* Eq. 7 blur width along y (rows), pixels, >= 0 */
+  int32_t kernel_size;  /* odd, 1..31; the paper uses 11 (Sec. 3.1) */
+  double eps_mod;       /* modulus guard in amplitude units; 0 => 1e-6 sqrt(mean I) */
+  double beta_obj, beta_probe;   /* step sizes, typically 1 */
+  double delta_obj, delta_probe; /* relative denominator floors, >= 0, typically 1e-3 */
+  int32_t probe_update_start;    /* first iteration (1-based) that moves the probe */
+  double alpha1, alpha2;         /* Eqs. 9-10 weights in [0, 1] */
+  double cbar_min, cbar_max;     /* Sec. 4.8 clamp of C_n, 0 < cbar_min <= cbar_max */
+  int32_t n_windows;             /* number of complex-constraint windows */
+  const int32_t* windows;        /* host, 2 * n_windows: [first, last], 1-based inclusive */
+  int32_t start_iteration;       /* number of the first iteration (resume), >= 1 */
+} ptycho_params;
+
+/* Build a plan on the current CUDA device.
+ *   p           parameters (copied; `windows` may be freed on return)
+ *   intensities device pointer, N * M * M float32 measured intensities; copied
+ *               into the plan, so the caller may free them on return. Negative
+ *               values give PTYCHO_EINVAL, non-finite ones PTYCHO_ENUMERIC.
+ *   positions   host or device pointer, N * 2 int32 (row, col) top-left corners;
+ *               a box outside the object gives PTYCHO_EINVAL
+ *   cuda_stream cudaStream_t the plan launches on (NULL: the legacy default stream)
+ *   out         receives the plan; the caller releases it with ptycho_destroy
+ * Blocks until the plan-time reductions are done. */
+ptycho_status ptycho_plan(const ptycho_params* p, const float* intensities, const int32_t* positions,
+                          void* cuda_stream, ptycho_plan_t* out);
+
+/* Run n_iter >= 0 iterations in place, asynchronously on the plan's stream.
+ *   object  device, obj_h * obj_w complex64, read and written
+ *   probe   device, K * M * M complex64, read and written
+ * The iteration counter continues across calls (windows and
+ * probe_update_start refer to it). Do not touch object or probe until the
+ * stream has been synchronised (ptycho_error does that). */
+ptycho_status ptycho_iterate(ptycho_plan_t plan, void* object, void* probe, int32_t n_iter);
+
+/* Synchronise the plan's stream and return E of the last iteration run
+ * (host double). PTYCHO_EINVAL if no iteration has run yet; PTYCHO_ENUMERIC
+ * if E is not finite. */
+ptycho_status ptycho_error(ptycho_plan_t plan, double* nrmse_last);
+
+/* Synchronise and copy the errors of the last min(n, runs, 4096) iterations,
+ * oldest first, into out (host, n doubles); *count receives how many. */
+ptycho_status ptycho_error_history(ptycho_plan_t plan, double* out, int32_t n, int32_t* count);
+
+/* Release every device resource of the plan (synchronises its stream). */
+ptycho_status ptycho_destroy(ptycho_plan_t plan);
+
+/* Per-kernel timing for roofline reports. While enabled, ptycho_iterate records
+ * a CUDA event pair on the plan's stream around every launch of the fused
+ * per-position kernel (the dominant kernel of an iteration).
+ * ptycho_profile_read synchronises the stream, returns the summed device time
+ * of those launches in milliseconds and their count, and resets both. At most
+ * 1024 launches are kept between reads (older ones are dropped from the sum). */
+ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
+ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
+
+/* Kernel launches one iteration issues (fused + update, plus the complex
+ * constraint kernels when `in_window` is non-zero). */
+int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* ptycho_last_error(void);
+
+/* Library version string. */
+const char* ptycho_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTYCHO_H_ */

@@ -1,0 +1,22 @@
+"""GB300-native data-parallel partially coherent ptychographic engine (arXiv 2406.06640).
+
+The compute path is libptycho.so (hand-written CUDA for sm_103a) behind the C
+ABI of include/ptycho.h; `binding` marshals arguments with ctypes and
+`engine.Reconstruction` accepts torch CUDA tensors.
+"""
+from .binding import (  # noqa: F401
+    BLUR_AMPLITUDE,
+    BLUR_INTENSITY,
+    EXPORTED,
+    FARFIELD,
+    NEARFIELD,
+    Plan,
+    PtychoError,
+    PtychoParams,
+    library_path,
+    load,
+    make_params,
+    version,
+)
+
+__version__ = "0.1.0"

@@ -1,0 +1,188 @@
+"""ctypes binding of the C ABI in include/ptycho.h (argument marshalling only).
+
+Tensors are passed as raw device pointers; every step of the engine runs in
+libptycho.so. PyTorch provides device memory and streams only. If the shared
+library is missing or fails to load, importing this module raises: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from . import build as _build
+
+PTYCHO_OK = 0
+STATUS_NAMES = {0: "PTYCHO_OK", 1: "PTYCHO_EINVAL", 2: "PTYCHO_ENOMEM", 3: "PTYCHO_ECUDA",
+                4: "PTYCHO_EUNSUPPORTED", 5: "PTYCHO_ENUMERIC", 6: "PTYCHO_ETIMEOUT"}
+FARFIELD, NEARFIELD = 0, 1
+BLUR_AMPLITUDE, BLUR_INTENSITY = 0, 1
+
+EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
+            "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
+            "ptycho_version")
+
+
+class PtychoError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PtychoParams(ctypes.Structure):
+    """Mirror of ptycho_params (field order and types must match include/ptycho.h)."""
+
+    _fields_ = [
+        ("M", ctypes.c_int32), ("K", ctypes.c_int32), ("N", ctypes.c_int32),
+        ("obj_h", ctypes.c_int32), ("obj_w", ctypes.c_int32),
+        ("geometry", ctypes.c_int32), ("blur_domain", ctypes.c_int32),
+        ("fresnel_F", ctypes.c_double), ("sigma1", ctypes.c_double), ("sigma2", ctypes.c_double),
+        ("kernel_size", ctypes.c_int32), ("eps_mod", ctypes.c_double),
+        ("beta_obj", ctypes.c_double), ("beta_probe", ctypes.c_double),
+        ("delta_obj", ctypes.c_double), ("delta_probe", ctypes.c_double),
+        ("probe_update_start", ctypes.c_int32),
+        ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double),
+        ("cbar_min", ctypes.c_double), ("cbar_max", ctypes.c_double),
+        ("n_windows", ctypes.c_int32), ("windows", ctypes.POINTER(ctypes.c_int32)),
+        ("start_iteration", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libptycho.so (building it first if it is missing or stale and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libptycho.so not found at {_build.LIB}; run paper_2406_06640_gb300/build.py")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    st = ctypes.c_int
+    lib.ptycho_plan.argtypes = [ctypes.POINTER(PtychoParams), P, P, P, ctypes.POINTER(P)]
+    lib.ptycho_plan.restype = st
+    lib.ptycho_iterate.argtypes = [P, P, P, ctypes.c_int32]
+    lib.ptycho_iterate.restype = st
+    lib.ptycho_error.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.ptycho_error.restype = st
+    lib.ptycho_error_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)]
+    lib.ptycho_error_history.restype = st
+    lib.ptycho_destroy.argtypes = [P]
+    lib.ptycho_destroy.restype = st
+    lib.ptycho_profile.argtypes = [P, ctypes.c_int32]
+    lib.ptycho_profile.restype = st
+    lib.ptycho_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
+    lib.ptycho_profile_read.restype = st
+    lib.ptycho_launches_per_iteration.argtypes = [P, ctypes.c_int32]
+    lib.ptycho_launches_per_iteration.restype = ctypes.c_int32
+    lib.ptycho_last_error.argtypes = []
+    lib.ptycho_last_error.restype = ctypes.c_char_p
+    lib.ptycho_version.argtypes = []
+    lib.ptycho_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != PTYCHO_OK:
+        raise PtychoError(status, load().ptycho_last_error().decode())
+
+
+def make_params(d: dict) -> tuple:
+    """Build a PtychoParams from a dict with the field names of ptycho_params.
+
+    `geometry` may be "far"/"near", `blur_domain` "amplitude"/"intensity",
+    `windows` a sequence of (first, last). Returns (params, keepalive).
+    """
+    p = PtychoParams()
+    geo = d.get("geometry", FARFIELD)
+    blur = d.get("blur_domain", BLUR_AMPLITUDE)
+    p.M, p.K, p.N = int(d["M"]), int(d["K"]), int(d["N"])
+    p.obj_h, p.obj_w = int(d["obj_h"]), int(d["obj_w"])
+    p.geometry = {"far": FARFIELD, "near": NEARFIELD}.get(geo, geo)
+    p.blur_domain = {"amplitude": BLUR_AMPLITUDE, "intensity": BLUR_INTENSITY}.get(blur, blur)
+    p.fresnel_F = float(d.get("fresnel_F", 0.0))
+    p.sigma1, p.sigma2 = float(d.get("sigma1", 1.0)), float(d.get("sigma2", 1.0))
+    p.kernel_size = int(d.get("kernel_size", 11))
+    p.eps_mod = float(d.get("eps_mod", 0.0))
+    p.beta_obj, p.beta_probe = float(d.get("beta_obj", 1.0)), float(d.get("beta_probe", 1.0))
+    p.delta_obj, p.delta_probe = float(d.get("delta_obj", 1e-3)), float(d.get("delta_probe", 1e-3))
+    p.probe_update_start = int(d.get("probe_update_start", 1))
+    p.alpha1, p.alpha2 = float(d.get("alpha1", 1.0)), float(d.get("alpha2", 0.0))
+    p.cbar_min, p.cbar_max = float(d.get("cbar_min", 0.01)), float(d.get("cbar_max", 10.0))
+    wins = [int(v) for w in d.get("windows", ()) for v in w]
+    arr = (ctypes.c_int32 * max(len(wins), 1))(*wins)
+    p.n_windows = len(wins) // 2
+    p.windows = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)) if wins else None
+    p.start_iteration = int(d.get("start_iteration", 1))
+    return p, arr
+
+
+class Plan:
+    """One reconstruction plan: wraps ptycho_plan / ptycho_iterate / ptycho_error / ptycho_destroy."""
+
+    def __init__(self, params: dict, intensities_ptr: int, positions_ptr: int, stream_ptr: int = 0):
+        lib = load()
+        self._p, self._keep = make_params(params)
+        h = ctypes.c_void_p()
+        _check(lib.ptycho_plan(ctypes.byref(self._p), ctypes.c_void_p(intensities_ptr),
+                               ctypes.c_void_p(positions_ptr), ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+        self._h = h
+
+    def iterate(self, object_ptr: int, probe_ptr: int, n_iter: int):
+        _check(load().ptycho_iterate(self._h, ctypes.c_void_p(object_ptr), ctypes.c_void_p(probe_ptr), int(n_iter)))
+
+    def error(self) -> float:
+        e = ctypes.c_double()
+        _check(load().ptycho_error(self._h, ctypes.byref(e)))
+        return e.value
+
+    def error_history(self, n: int) -> list:
+        buf = (ctypes.c_double * max(n, 1))()
+        c = ctypes.c_int32()
+        _check(load().ptycho_error_history(self._h, buf, int(n), ctypes.byref(c)))
+        return [buf[i] for i in range(c.value)]
+
+    def profile(self, enable: bool):
+        _check(load().ptycho_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> tuple:
+        """(summed fused-kernel milliseconds, launches) since the last read."""
+        ms = ctypes.c_double()
+        c = ctypes.c_int32()
+        _check(load().ptycho_profile_read(self._h, ctypes.byref(ms), ctypes.byref(c)))
+        return ms.value, c.value
+
+    def launches_per_iteration(self, in_window: bool) -> int:
+        return int(load().ptycho_launches_per_iteration(self._h, 1 if in_window else 0))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ptycho_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def version() -> str:
+    return load().ptycho_version().decode()

@@ -1,0 +1,457 @@
+// C ABI of the engine (declared in include/ptycho.h): plan construction,
+// validation, the per-iteration launch sequence and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "ptycho.h"
+
+using namespace ptycho;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ptycho_status fail(ptycho_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+ptycho_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error where possible
+  const ptycho_status s = (e == cudaErrorMemoryAllocation) ? PTYCHO_ENOMEM : PTYCHO_ECUDA;
+  return fail(s, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define PT_CUDA(call, what)                       \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// normalised 1-D factor of Eq. 7 (the 2-D kernel is the outer product; its
+// normalisation factors into the two 1-D normalisations)
+std::vector<double> taps_1d(double sigma, int h) {
+  std::vector<double> g(2 * h + 1);
+  double s = 0.0;
+  for (int d = -h; d <= h; ++d) {
+    const double v = sigma > 0 ? std::exp(-(double)d * d / (2.0 * sigma * sigma)) : (d == 0 ? 1.0 : 0.0);
+    g[d + h] = v;
+    s += v;
+  }
+  for (double& v : g) v /= s;
+  return g;
+}
+
+}  // namespace
+
+struct ptycho_plan_s {
+  ptycho_params p{};
+  std::vector<int32_t> windows;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<void*> allocs;
+  std::vector<int2> h_pos;
+  double errden = 0.0, eps = 0.0;
+  int slots = 0;
+  long long iter = 1;  // number of the next iteration
+  long long runs = 0;  // iterations run so far
+  FusedArgs fa{};
+  UpdateArgs ua{};
+  ConstraintArgs ca{};
+  double* d_errhist = nullptr;
+  // profiling: event pairs around the fused kernel
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;  // 2 * kProfSlots
+  int prof_count = 0;
+  static constexpr int kProfSlots = 1024;
+
+  template <class T>
+  cudaError_t alloc(T** ptr, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) allocs.push_back(q);
+    *ptr = static_cast<T*>(q);
+    return e;
+  }
+  ~ptycho_plan_s() {
+    for (void* q : allocs) cudaFree(q);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  bool in_window(long long t) const {
+    for (size_t i = 0; i + 1 < windows.size(); i += 2)
+      if (t >= windows[i] && t <= windows[i + 1]) return true;
+    return false;
+  }
+};
+
+static ptycho_status validate(const ptycho_params* p) {
+  if (!p) return fail(PTYCHO_EINVAL, "params is NULL");
+  if (!is_pow2(p->M) || p->M < 8 || p->M > 512) return fail(PTYCHO_EINVAL, "M must be a power of two in [8, 512]");
+  if (p->M > 128) return fail(PTYCHO_EUNSUPPORTED, "M > 128 is not handled by this build");
+  if (p->K < 1) return fail(PTYCHO_EINVAL, "K must be >= 1");
+  if (p->K > 8) return fail(PTYCHO_EUNSUPPORTED, "K > 8 probe modes is not handled by this build");
+  if (p->N < 1) return fail(PTYCHO_EINVAL, "N must be >= 1");
+  if (p->obj_h < p->M || p->obj_w < p->M) return fail(PTYCHO_EINVAL, "object must be at least M x M");
+  if (p->geometry != PTYCHO_FARFIELD && p->geometry != PTYCHO_NEARFIELD) return fail(PTYCHO_EINVAL, "bad geometry");
+  if (p->blur_domain != PTYCHO_BLUR_AMPLITUDE && p->blur_domain != PTYCHO_BLUR_INTENSITY)
+    return fail(PTYCHO_EINVAL, "bad blur_domain");
+  if (p->geometry == PTYCHO_NEARFIELD && !(std::isfinite(p->fresnel_F) && p->fresnel_F > 0))
+    return fail(PTYCHO_EINVAL, "near field needs fresnel_F > 0");
+  if (!(std::isfinite(p->sigma1) && p->sigma1 >= 0 && std::isfinite(p->sigma2) && p->sigma2 >= 0))
+    return fail(PTYCHO_EINVAL, "sigma1 and sigma2 must be finite and >= 0");
+  if (p->kernel_size < 1 || p->kernel_size > kMaxTaps || (p->kernel_size % 2) == 0)
+    return fail(PTYCHO_EINVAL, "kernel_size must be odd, 1..31");
+  if (!(std::isfinite(p->eps_mod) && p->eps_mod >= 0)) return fail(PTYCHO_EINVAL, "eps_mod must be >= 0");
+  if (!(std::isfinite(p->beta_obj) && std::isfinite(p->beta_probe))) return fail(PTYCHO_EINVAL, "beta not finite");
+  if (!(std::isfinite(p->delta_obj) && p->delta_obj >= 0 && std::isfinite(p->delta_probe) && p->delta_probe >= 0))
+    return fail(PTYCHO_EINVAL, "delta must be finite and >= 0");
+  if (!(p->alpha1 >= 0 && p->alpha1 <= 1 && p->alpha2 >= 0 && p->alpha2 <= 1))
+    return fail(PTYCHO_EINVAL, "alpha1 and alpha2 must lie in [0, 1]");
+  if (!(std::isfinite(p->cbar_min) && std::isfinite(p->cbar_max) && p->cbar_min > 0 && p->cbar_min <= p->cbar_max))
+    return fail(PTYCHO_EINVAL, "need 0 < cbar_min <= cbar_max");
+  if (p->n_windows < 0 || (p->n_windows > 0 && !p->windows)) return fail(PTYCHO_EINVAL, "bad windows");
+  for (int i = 0; i < p->n_windows; ++i)
+    if (p->windows[2 * i] < 1 || p->windows[2 * i] > p->windows[2 * i + 1])
+      return fail(PTYCHO_EINVAL, "windows must be [first, last] with 1 <= first <= last");
+  if (p->start_iteration < 1) return fail(PTYCHO_EINVAL, "start_iteration must be >= 1");
+  return PTYCHO_OK;
+}
+
+static bool is_device_pointer(const void* ptr) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, const int32_t* positions) {
+  const ptycho_params& p = pl->p;
+  const int M = p.M, K = p.K, N = p.N;
+  const size_t MM = (size_t)M * M;
+  cudaStream_t s = pl->stream;
+
+  // ---- positions
+  pl->h_pos.resize(N);
+  if (is_device_pointer(positions)) {
+    PT_CUDA(cudaMemcpy(pl->h_pos.data(), positions, sizeof(int2) * N, cudaMemcpyDeviceToHost), "copy positions");
+  } else {
+    std::memcpy(pl->h_pos.data(), positions, sizeof(int2) * N);
+  }
+  for (int n = 0; n < N; ++n) {
+    const int2 q = pl->h_pos[n];
+    if (q.x < 0 || q.y < 0 || q.x > p.obj_h - M || q.y > p.obj_w - M)
+      return fail(PTYCHO_EINVAL, "position " + std::to_string(n) + " puts its box outside the object");
+  }
+  if (!is_device_pointer(intensities)) return fail(PTYCHO_EINVAL, "intensities must be a device pointer");
+
+  // ---- slots (co-resident clusters of the fused kernel)
+  int max_slots = 0;
+  PT_CUDA(fused_max_slots(M, K, &max_slots), "occupancy of the fused kernel");
+  if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
+  pl->slots = std::min(max_slots, N);
+
+  // ---- buffers
+  FusedArgs& fa = pl->fa;
+  UpdateArgs& ua = pl->ua;
+  ConstraintArgs& ca = pl->ca;
+  float* d_I;
+  int2* d_pos;
+  PT_CUDA(pl->alloc(&d_I, (size_t)N * MM), "alloc intensities");
+  PT_CUDA(pl->alloc(&d_pos, (size_t)N), "alloc positions");
+  PT_CUDA(cudaMemcpyAsync(d_I, intensities, sizeof(float) * N * MM, cudaMemcpyDeviceToDevice, s), "copy intensities");
+  PT_CUDA(cudaMemcpyAsync(d_pos, pl->h_pos.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, s), "copy positions");
+
+  // plan-time FP64 sums: sum I (for eps), sum I^2 (error denominator), bad values
+  const size_t count = (size_t)N * MM;
+  const int nb = (int)std::min<size_t>(1024, (count + 255) / 256);
+  double* d_part;
+  double* d_sums;
+  PT_CUDA(pl->alloc(&d_part, (size_t)3 * nb), "alloc sums");
+  PT_CUDA(pl->alloc(&d_sums, 3), "alloc sums");
+  PT_CUDA(launch_intensity_sums(d_I, count, d_part, nb, s), "intensity sums");
+  PT_CUDA(launch_finish_sums(d_part, nb, d_sums, s), "intensity sums");
+  double h_sums[3];
+  PT_CUDA(cudaMemcpyAsync(h_sums, d_sums, sizeof(h_sums), cudaMemcpyDeviceToHost, s), "copy sums");
+  PT_CUDA(cudaStreamSynchronize(s), "plan sync");
+  if (h_sums[2] >= 1e30) return fail(PTYCHO_ENUMERIC, "intensities contain non-finite values");
+  if (h_sums[2] > 0) return fail(PTYCHO_EINVAL, "intensities contain negative values");
+  if (!(h_sums[1] > 0)) return fail(PTYCHO_EINVAL, "intensities are all zero");
+  pl->errden = h_sums[1];
+  pl->eps = p.eps_mod > 0 ? p.eps_mod : 1e-6 * std::sqrt(h_sums[0] / (double)count);
+
+  // twiddles, Fresnel factors, taps (FP64 on the host, rounded once)
+  std::vector<float2> tw(M), hq(M);
+  for (int m = 0; m < M; ++m) {
+    const double a = -2.0 * M_PI * m / M;
+    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    const double fu = m < M / 2 ? m : m - M;
+    const double ph = p.geometry == PTYCHO_NEARFIELD ? -M_PI * fu * fu / (M * p.fresnel_F) : 0.0;
+    hq[m] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+  }
+  float2 *d_tw, *d_hq;
+  PT_CUDA(pl->alloc(&d_tw, M), "alloc twiddles");
+  PT_CUDA(pl->alloc(&d_hq, M), "alloc fresnel");
+  PT_CUDA(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float2) * M, cudaMemcpyHostToDevice, s), "copy twiddles");
+  PT_CUDA(cudaMemcpyAsync(d_hq, hq.data(), sizeof(float2) * M, cudaMemcpyHostToDevice, s), "copy fresnel");
+  const int kh = p.kernel_size / 2;
+  const std::vector<double> gx = taps_1d(p.sigma1, kh), gy = taps_1d(p.sigma2, kh);
+
+  // per-position and per-slot work buffers
+  float2 *d_cn, *d_pacc;
+  float* d_dacc;
+  double* d_errpart;
+  PT_CUDA(pl->alloc(&d_cn, (size_t)N * MM), "alloc contributions");
+  PT_CUDA(pl->alloc(&d_pacc, (size_t)pl->slots * K * MM), "alloc probe partials");
+  PT_CUDA(pl->alloc(&d_dacc, (size_t)pl->slots * MM), "alloc probe partials");
+  PT_CUDA(pl->alloc(&d_errpart, (size_t)pl->slots), "alloc error partials");
+
+  // object tiles and their position lists (increasing n)
+  const int tx = (p.obj_w + kObjTile - 1) / kObjTile, ty = (p.obj_h + kObjTile - 1) / kObjTile;
+  std::vector<std::vector<int>> lists((size_t)tx * ty);
+  for (int n = 0; n < N; ++n) {
+    const int2 q = pl->h_pos[n];
+    for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
+      for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
+  }
+  std::vector<int> start((size_t)tx * ty + 1, 0), flat;
+  for (size_t i = 0; i < lists.size(); ++i) {
+    start[i + 1] = start[i] + (int)lists[i].size();
+    flat.insert(flat.end(), lists[i].begin(), lists[i].end());
+  }
+  int *d_start, *d_list;
+  PT_CUDA(pl->alloc(&d_start, start.size()), "alloc tile lists");
+  PT_CUDA(pl->alloc(&d_list, flat.size()), "alloc tile lists");
+  PT_CUDA(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, s), "copy tiles");
+  if (!flat.empty())
+    PT_CUDA(cudaMemcpyAsync(d_list, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, s), "copy tiles");
+
+  const size_t plane = (size_t)p.obj_h * p.obj_w;
+  float2* d_no;
+  float *d_do, *d_bmo;
+  PT_CUDA(pl->alloc(&d_no, (size_t)kObjSplit * plane), "alloc object partials");
+  PT_CUDA(pl->alloc(&d_do, (size_t)kObjSplit * plane), "alloc object partials");
+  PT_CUDA(pl->alloc(&d_bmo, (size_t)tx * ty), "alloc tile maxima");
+  const int pb = (int)((MM + 255) / 256);
+  float2* d_np;
+  float *d_dp, *d_p2, *d_bmp, *d_cbar;
+  PT_CUDA(pl->alloc(&d_np, (size_t)K * MM), "alloc probe sums");
+  PT_CUDA(pl->alloc(&d_dp, MM), "alloc probe sums");
+  PT_CUDA(pl->alloc(&d_p2, MM), "alloc probe sums");
+  PT_CUDA(pl->alloc(&d_bmp, (size_t)pb), "alloc probe maxima");
+  PT_CUDA(pl->alloc(&d_cbar, (size_t)N), "alloc cbar");
+  PT_CUDA(pl->alloc(&pl->d_errhist, (size_t)kErrHistory), "alloc error history");
+
+  // ---- kernel argument blocks
+  fa.I = d_I;
+  fa.pos = d_pos;
+  fa.N = N;
+  fa.K = K;
+  fa.obj_w = p.obj_w;
+  fa.near_field = p.geometry == PTYCHO_NEARFIELD;
+  fa.blur_intensity = p.blur_domain == PTYCHO_BLUR_INTENSITY;
+  fa.kh = kh;
+  fa.eps = (float)pl->eps;
+  for (int i = 0; i < 2 * kh + 1; ++i) {
+    fa.gx[i] = (float)gx[i];
+    fa.gy[i] = (float)gy[i];
+  }
+  fa.tw = d_tw;
+  fa.hq = d_hq;
+  fa.cn = d_cn;
+  fa.pacc = d_pacc;
+  fa.dacc = d_dacc;
+  fa.errpart = d_errpart;
+
+  ua.pos = d_pos;
+  ua.N = N;
+  ua.K = K;
+  ua.M = M;
+  ua.obj_h = p.obj_h;
+  ua.obj_w = p.obj_w;
+  ua.slots = pl->slots;
+  ua.cn = d_cn;
+  ua.pacc = d_pacc;
+  ua.dacc = d_dacc;
+  ua.errpart = d_errpart;
+  ua.tile_start = d_start;
+  ua.tile_pos = d_list;
+  ua.tiles_x = tx;
+  ua.tiles_y = ty;
+  ua.no_part = d_no;
+  ua.do_part = d_do;
+  ua.blk_max_o = d_bmo;
+  ua.np_sum = d_np;
+  ua.dp_sum = d_dp;
+  ua.p2 = d_p2;
+  ua.blk_max_p = d_bmp;
+  ua.probe_blocks = pb;
+  ua.errhist = pl->d_errhist;
+  ua.errden = pl->errden;
+  ua.beta_obj = (float)p.beta_obj;
+  ua.beta_probe = (float)p.beta_probe;
+  ua.delta_obj = (float)p.delta_obj;
+  ua.delta_probe = (float)p.delta_probe;
+
+  ca.pos = d_pos;
+  ca.N = N;
+  ca.M = M;
+  ca.obj_h = p.obj_h;
+  ca.obj_w = p.obj_w;
+  ca.tile_start = d_start;
+  ca.tile_pos = d_list;
+  ca.tiles_x = tx;
+  ca.tiles_y = ty;
+  ca.cbar = d_cbar;
+  ca.alpha1 = (float)p.alpha1;
+  ca.alpha2 = (float)p.alpha2;
+  ca.cbar_min = (float)p.cbar_min;
+  ca.cbar_max = (float)p.cbar_max;
+
+  PT_CUDA(cudaStreamSynchronize(s), "plan sync");
+  return PTYCHO_OK;
+}
+
+extern "C" {
+
+ptycho_status ptycho_plan(const ptycho_params* p, const float* intensities, const int32_t* positions,
+                          void* cuda_stream, ptycho_plan_t* out) {
+  if (!out) return fail(PTYCHO_EINVAL, "out is NULL");
+  *out = nullptr;
+  ptycho_status st = validate(p);
+  if (st != PTYCHO_OK) return st;
+  if (!intensities || !positions) return fail(PTYCHO_EINVAL, "intensities and positions must be non-NULL");
+  ptycho_plan_s* pl = new (std::nothrow) ptycho_plan_s();
+  if (!pl) return fail(PTYCHO_ENOMEM, "host allocation failed");
+  pl->p = *p;
+  pl->windows.assign(p->windows, p->windows + 2 * p->n_windows);
+  pl->p.windows = nullptr;
+  pl->stream = static_cast<cudaStream_t>(cuda_stream);
+  pl->iter = p->start_iteration;
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  st = build_plan(pl, intensities, positions);
+  if (st != PTYCHO_OK) {
+    cudaStreamSynchronize(pl->stream);
+    delete pl;
+    return st;
+  }
+  g_last_error.clear();
+  *out = pl;
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_t n_iter) {
+  if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
+  if (!object || !probe) return fail(PTYCHO_EINVAL, "object and probe must be non-NULL");
+  if (n_iter < 0) return fail(PTYCHO_EINVAL, "n_iter must be >= 0");
+  PT_CUDA(cudaSetDevice(pl->device), "cudaSetDevice");
+  FusedArgs fa = pl->fa;
+  UpdateArgs ua = pl->ua;
+  ConstraintArgs ca = pl->ca;
+  fa.O = static_cast<const float2*>(object);
+  fa.P = static_cast<const float2*>(probe);
+  ua.O = static_cast<float2*>(object);
+  ua.P = static_cast<float2*>(probe);
+  ca.O = static_cast<float2*>(object);
+  for (int i = 0; i < n_iter; ++i) {
+    const long long t = pl->iter;
+    const int ps = pl->prof_count % ptycho_plan_s::kProfSlots;
+    if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], pl->stream), "profile event");
+    PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, pl->stream), "fused kernel launch");
+    if (pl->profiling) {
+      PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], pl->stream), "profile event");
+      pl->prof_count++;
+    }
+    ua.hist_index = (int)(pl->runs % kErrHistory);
+    ua.update_probe = t >= pl->p.probe_update_start;
+    PT_CUDA(launch_update(ua, pl->stream), "update launch");
+    if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, pl->stream), "constraint launch");
+    pl->iter++;
+    pl->runs++;
+  }
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_error(ptycho_plan_t pl, double* nrmse_last) {
+  if (!pl || !nrmse_last) return fail(PTYCHO_EINVAL, "NULL argument");
+  PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
+  if (pl->runs == 0) return fail(PTYCHO_EINVAL, "no iteration has run");
+  double e = 0.0;
+  PT_CUDA(cudaMemcpy(&e, pl->d_errhist + (pl->runs - 1) % kErrHistory, sizeof(double), cudaMemcpyDeviceToHost),
+          "copy error");
+  *nrmse_last = e;
+  if (!std::isfinite(e)) return fail(PTYCHO_ENUMERIC, "error metric is not finite");
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_error_history(ptycho_plan_t pl, double* out, int32_t n, int32_t* count) {
+  if (!pl || !out || !count || n < 0) return fail(PTYCHO_EINVAL, "bad argument");
+  PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
+  const long long c = std::min<long long>({(long long)n, pl->runs, (long long)kErrHistory});
+  std::vector<double> ring(kErrHistory);
+  PT_CUDA(cudaMemcpy(ring.data(), pl->d_errhist, sizeof(double) * kErrHistory, cudaMemcpyDeviceToHost),
+          "copy error history");
+  for (long long i = 0; i < c; ++i) out[i] = ring[(pl->runs - c + i) % kErrHistory];
+  *count = (int32_t)c;
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_destroy(ptycho_plan_t pl) {
+  if (!pl) return PTYCHO_OK;
+  cudaSetDevice(pl->device);
+  cudaStreamSynchronize(pl->stream);
+  delete pl;
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_profile(ptycho_plan_t pl, int32_t enable) {
+  if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
+  if (enable && pl->ev.empty()) {
+    pl->ev.resize(2 * ptycho_plan_s::kProfSlots);
+    for (cudaEvent_t& e : pl->ev) PT_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+  }
+  pl->profiling = enable != 0;
+  pl->prof_count = 0;
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_profile_read(ptycho_plan_t pl, double* fused_ms, int32_t* launches) {
+  if (!pl || !fused_ms || !launches) return fail(PTYCHO_EINVAL, "NULL argument");
+  PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
+  const int c = std::min(pl->prof_count, ptycho_plan_s::kProfSlots);
+  double tot = 0.0;
+  for (int i = 0; i < c; ++i) {
+    float ms = 0.f;
+    PT_CUDA(cudaEventElapsedTime(&ms, pl->ev[2 * i], pl->ev[2 * i + 1]), "cudaEventElapsedTime");
+    tot += ms;
+  }
+  *fused_ms = tot;
+  *launches = c;
+  pl->prof_count = 0;
+  return PTYCHO_OK;
+}
+
+int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
+  (void)pl;
+  return 6 + (in_window ? 2 : 0);
+}
+
+const char* ptycho_last_error(void) { return g_last_error.c_str(); }
+
+const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Internal declarations shared by the engine's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace ptycho {
+
+constexpr int kMaxTaps = 31;        // largest odd Gaussian kernel side accepted (Eq. 7 support)
+constexpr int kObjTile = 32;        // object tile side of the gather kernels
+constexpr int kObjSplit = 8;        // position groups per object tile (partial sums, fixed order)
+constexpr int kErrHistory = 4096;   // ring of per-iteration errors kept on the device
+
+// Arguments of the fused per-position kernel (one cluster of K CTAs per position).
+struct FusedArgs {
+  const float2* O;      // object, obj_h x obj_w, row-major
+  const float2* P;      // probe modes, K x M x M
+  const float* I;       // measured intensities, N x M x M (far field: DC at (M/2, M/2))
+  const int2* pos;      // top-left (row, col) of each box
+  int N, K, obj_w;
+  int near_field;       // 0: centred FFT; 1: Fresnel transfer function
+  int blur_intensity;   // 0: blur the amplitude (Eq. 6); 1: blur the intensity (Eq. 2)
+  int kh;               // kernel half-width, taps in [-kh, kh]
+  float eps;            // modulus guard
+  float gx[kMaxTaps];   // taps along x (columns, sigma_1)
+  float gy[kMaxTaps];   // taps along y (rows, sigma_2)
+  const float2* tw;     // W_M^m, m in [0, M)
+  const float2* hq;     // near field: h[u] = exp(-i pi fu^2 / (M F)), H[u, v] = h[u] h[v]
+  float2* cn;           // out: per-position object numerator contributions, N x M x M
+  float2* pacc;         // out: per-slot probe numerator partials, slots x K x M x M (accumulated)
+  float* dacc;          // out: per-slot probe denominator partials, slots x M x M (accumulated)
+  double* errpart;      // out: per-slot FP64 error numerators
+};
+
+// fused kernel launch; returns the number of slots (co-resident clusters) used
+cudaError_t launch_fused(int M, const FusedArgs& a, int slots, cudaStream_t s);
+cudaError_t fused_max_slots(int M, int K, int* slots);
+size_t fused_smem_bytes(int M);
+
+// update / reduction kernels (update.cu)
+struct UpdateArgs {
+  float2* O; float2* P;
+  const int2* pos;
+  int N, K, M, obj_h, obj_w, slots;
+  const float2* cn; const float2* pacc; const float* dacc; const double* errpart;
+  // object gather
+  const int* tile_start;  // (tiles_y * tiles_x + 1) CSR offsets into tile_pos
+  const int* tile_pos;    // position indices per tile, increasing
+  int tiles_x, tiles_y;
+  float2* no_part; float* do_part;  // kObjSplit x obj_h x obj_w partials
+  float* blk_max_o;                  // per object tile
+  // probe gather
+  float2* np_sum; float* dp_sum; float* p2;  // K x M x M, M x M, M x M
+  float* blk_max_p;
+  int probe_blocks;
+  double* errhist; int hist_index; double errden;
+  float beta_obj, beta_probe, delta_obj, delta_probe;
+  int update_probe;
+};
+cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);
+
+// complex constraint (constraint.cu)
+struct ConstraintArgs {
+  float2* O; const int2* pos; int N, M, obj_h, obj_w;
+  const int* tile_start; const int* tile_pos; int tiles_x, tiles_y;
+  float* cbar; float alpha1, alpha2, cbar_min, cbar_max;
+};
+cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s);
+
+// plan-time helpers (update.cu)
+cudaError_t launch_intensity_sums(const float* I, size_t count, double* partials, int nblocks, cudaStream_t s);
+cudaError_t launch_finish_sums(const double* partials, int nblocks, double* out2, cudaStream_t s);
+
+}  // namespace ptycho

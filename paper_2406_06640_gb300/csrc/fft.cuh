@@ -1,0 +1,308 @@
+// Shared-memory / register radix FFT building blocks for M x M complex64 tiles.
+//
+// The far-field propagator of Eq. 1 is a 2-D DFT; the near-field Fresnel
+// transfer-function propagator is a DFT, a pointwise product and an inverse
+// DFT. One CTA transforms one M x M tile (M a power of two, 8..256) with
+// T = M * G threads, G = M / E, E = min(16, M): every thread keeps E complex
+// values in registers.
+//
+// A length-M 1-D DFT is split as M = E x G (Cooley-Tukey four-step):
+//   pass 1  DFT-E over j of x[t + G j]            (thread t = 0..G-1, in registers)
+//           times the twiddle W_M^(t k2)
+//   swap    through shared memory (exchange "A")
+//   pass 2  DFT-G over t for the E/G values k2 this thread owns
+//           -> X[k2 + E k1]
+// The 2-D transform runs rows then columns with a transpose (exchange "B")
+// between them. The inverse runs the same steps mirrored, so it consumes the
+// register layout that the forward leaves and returns to the starting one.
+//
+// Register layouts (tid in [0, T)):
+//   ROW layout: y = tid / G, t = tid % G, register j holds element (y, t + G j)
+//   COL layout: v = tid / G, t = tid % G, register r = i2 * G + k1 holds
+//               frequency (u, v) with u = t * (E / G) + i2 + E k1
+//
+// Shared-memory swizzles (8-byte elements; a half-warp is conflict-free when
+// its 16 lanes hit 16 distinct slots mod 16):
+//   exchange A (row-internal) at  line * M + (swzA(k2 G + t) ^ ((line G) & (E-1)))
+//   exchange B (transpose)    at  x * M + (y ^ swzB(x))
+// with swzA(o) = 16 (o >> 4) + ((o & 15) ^ ((o >> 4) & 15)) for E = 16 and
+// swzB(x) = (x & (E-1) & ~m) ^ ((x & m) << (log2 E - s)), m = 2^s - 1,
+// s = log2(E / G).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ptycho {
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// multiply by the primitive 4th root used by the transform direction:
+// forward (e^{-2 pi i / 4} = -i), inverse (+i)
+template <bool INV>
+__device__ __forceinline__ float2 mul_w4(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos(2 pi m / 16) and sin(2 pi m / 16), m = 0..15, from the exact values
+// cos(pi/8) = sqrt(2 + sqrt 2) / 2, sin(pi/8) = sqrt(2 - sqrt 2) / 2, sqrt(2)/2.
+__host__ __device__ constexpr float cos16(int m) {
+  return (m & 15) == 0 ? 1.0f : (m & 15) == 1 ? 0.92387953251128674f : (m & 15) == 2 ? 0.70710678118654752f
+       : (m & 15) == 3 ? 0.38268343236508978f : (m & 15) == 4 ? 0.0f : (m & 15) == 5 ? -0.38268343236508978f
+       : (m & 15) == 6 ? -0.70710678118654752f : (m & 15) == 7 ? -0.92387953251128674f : (m & 15) == 8 ? -1.0f
+       : (m & 15) == 9 ? -0.92387953251128674f : (m & 15) == 10 ? -0.70710678118654752f
+       : (m & 15) == 11 ? -0.38268343236508978f : (m & 15) == 12 ? 0.0f : (m & 15) == 13 ? 0.38268343236508978f
+       : (m & 15) == 14 ? 0.70710678118654752f : 0.92387953251128674f;
+}
+__host__ __device__ constexpr float sin16(int m) { return cos16(m + 12); }  // sin(a) = cos(a - pi/2)
+
+// x * W_16^m, W = e^{-2 pi i / 16} (forward) or its conjugate (inverse)
+template <bool INV, int m>
+__device__ __forceinline__ float2 mul_w16(float2 a) {
+  constexpr int mm = m & 15;
+  if constexpr (mm == 0) return a;
+  else if constexpr (mm == 4) return mul_w4<INV>(a);
+  else if constexpr (mm == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (mm == 12) return mul_w4<!INV>(a);
+  else {
+    constexpr float c = cos16(mm);
+    constexpr float s = INV ? sin16(mm) : -sin16(mm);
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+// ------------------------------------------------------------------ register DFTs (natural order in and out)
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+  float2 t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  float2 s13 = cadd(a1, a3), d13 = mul_w4<INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* a) {
+  // decimation in time: even / odd halves
+  float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = mul_w16<INV, 2>(o1);
+  o2 = mul_w16<INV, 4>(o2);
+  o3 = mul_w16<INV, 6>(o3);
+  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* a) {
+  // j = j1 + 4 j2: DFT-4 over j2 for each j1, twiddle W16^(j1 k2), DFT-4 over j1: X[k2 + 4 k1]
+  float2 b[16];
+#pragma unroll
+  for (int j1 = 0; j1 < 4; ++j1) {
+    float2 x0 = a[j1], x1 = a[j1 + 4], x2 = a[j1 + 8], x3 = a[j1 + 12];
+    dft4<INV>(x0, x1, x2, x3);
+    b[j1 * 4 + 0] = x0; b[j1 * 4 + 1] = x1; b[j1 * 4 + 2] = x2; b[j1 * 4 + 3] = x3;
+  }
+  b[1 * 4 + 1] = mul_w16<INV, 1>(b[1 * 4 + 1]);
+  b[1 * 4 + 2] = mul_w16<INV, 2>(b[1 * 4 + 2]);
+  b[1 * 4 + 3] = mul_w16<INV, 3>(b[1 * 4 + 3]);
+  b[2 * 4 + 1] = mul_w16<INV, 2>(b[2 * 4 + 1]);
+  b[2 * 4 + 2] = mul_w16<INV, 4>(b[2 * 4 + 2]);
+  b[2 * 4 + 3] = mul_w16<INV, 6>(b[2 * 4 + 3]);
+  b[3 * 4 + 1] = mul_w16<INV, 3>(b[3 * 4 + 1]);
+  b[3 * 4 + 2] = mul_w16<INV, 6>(b[3 * 4 + 2]);
+  b[3 * 4 + 3] = mul_w16<INV, 9>(b[3 * 4 + 3]);
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 x0 = b[0 * 4 + k2], x1 = b[1 * 4 + k2], x2 = b[2 * 4 + k2], x3 = b[3 * 4 + k2];
+    dft4<INV>(x0, x1, x2, x3);
+    a[k2 + 0] = x0; a[k2 + 4] = x1; a[k2 + 8] = x2; a[k2 + 12] = x3;
+  }
+}
+
+template <int N, bool INV>
+__device__ __forceinline__ void dft(float2* a) {
+  if constexpr (N == 1) {
+  } else if constexpr (N == 2) {
+    dft2<INV>(a[0], a[1]);
+  } else if constexpr (N == 4) {
+    dft4<INV>(a[0], a[1], a[2], a[3]);
+  } else if constexpr (N == 8) {
+    dft8<INV>(a);
+  } else if constexpr (N == 16) {
+    dft16<INV>(a);
+  } else {
+    static_assert(N == 1, "unsupported register DFT size");
+  }
+}
+
+// ------------------------------------------------------------------ tile geometry
+template <int M_>
+struct Tile {
+  static constexpr int M = M_;
+  static constexpr int E = M < 16 ? M : 16;         // registers per thread
+  static constexpr int G = M / E;                    // threads per line
+  static constexpr int T = M * G;                    // threads per tile
+  static constexpr int EG = E / G;                   // pass-2 DFTs per thread
+  static constexpr int LOG2E = E == 16 ? 4 : E == 8 ? 3 : E == 4 ? 2 : E == 2 ? 1 : 0;
+  static constexpr int S = (EG == 16 ? 4 : EG == 8 ? 3 : EG == 4 ? 2 : EG == 2 ? 1 : 0);
+  static_assert(M == 8 || M == 16 || M == 32 || M == 64 || M == 128 || M == 256, "M must be 8..256");
+
+  // exchange A: line-internal swap, element (line, t, k2)
+  __device__ __forceinline__ static int idxA(int line, int t, int k2) {
+    const int o = k2 * G + t;
+    int sw;
+    if constexpr (E == 16) sw = (o & ~15) | ((o & 15) ^ ((o >> 4) & 15));
+    else sw = o;
+    return line * M + (sw ^ ((line * G) & (E - 1)));
+  }
+  // exchange B: transpose, element (y, x)
+  __device__ __forceinline__ static int idxB(int y, int x) {
+    constexpr int m = (1 << S) - 1;
+    const int xl = x & (E - 1);
+    const int sw = (xl & ~m) ^ ((xl & m) << (LOG2E - S));
+    return x * M + (y ^ sw);
+  }
+  // natural [y][x] layout with a row XOR (used for the mode-sum exchanges)
+  __device__ __forceinline__ static int idxN(int y, int x) { return y * M + (x ^ ((y * G) & (E - 1))); }
+};
+
+// ------------------------------------------------------------------ 2-D transform steps
+// tw[m] = W_M^m for m in [0, M) (forward convention); the inverse uses conj.
+
+// ROW layout registers -> COL layout registers (forward 2-D DFT, unscaled)
+template <int M>
+__device__ __forceinline__ void fft2_forward(float2 (&a)[Tile<M>::E], float2* sm, const float2* tw, int tid) {
+  using TL = Tile<M>;
+  constexpr int E = TL::E, G = TL::G, EG = TL::EG;
+  const int line = tid / G, t = tid % G;
+  // ---- rows: pass 1
+  dft<E, false>(a);
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmul(a[k2], tw[t * k2]);
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) sm[TL::idxA(line, t, k2)] = a[k2];
+    __syncthreads();
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+      for (int tt = 0; tt < G; ++tt) a[i2 * G + tt] = sm[TL::idxA(line, tt, t * EG + i2)];
+    // ---- rows: pass 2
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2) dft<G, false>(&a[i2 * G]);
+    __syncthreads();
+  }
+  // ---- transpose: thread (y = line, t) holds x = t * EG + i2 + E k1 at register i2 * G + k1
+#pragma unroll
+  for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+    for (int k1 = 0; k1 < G; ++k1) sm[TL::idxB(line, t * EG + i2 + E * k1)] = a[i2 * G + k1];
+  __syncthreads();
+  // column v = line reads y = t + G j
+#pragma unroll
+  for (int j = 0; j < E; ++j) a[j] = sm[TL::idxB(t + G * j, line)];
+  // ---- columns: pass 1
+  dft<E, false>(a);
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmul(a[k2], tw[t * k2]);
+  if constexpr (G > 1) {
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) sm[TL::idxA(line, t, k2)] = a[k2];
+    __syncthreads();
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+      for (int tt = 0; tt < G; ++tt) a[i2 * G + tt] = sm[TL::idxA(line, tt, t * EG + i2)];
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2) dft<G, false>(&a[i2 * G]);
+  }
+  __syncthreads();  // shared memory free for reuse on return
+}
+
+// COL layout registers -> ROW layout registers (inverse 2-D DFT, unscaled: times M^2)
+template <int M>
+__device__ __forceinline__ void fft2_inverse(float2 (&a)[Tile<M>::E], float2* sm, const float2* tw, int tid) {
+  using TL = Tile<M>;
+  constexpr int E = TL::E, G = TL::G, EG = TL::EG;
+  const int line = tid / G, t = tid % G;
+  // ---- columns: undo pass 2
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2) dft<G, true>(&a[i2 * G]);
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+      for (int tt = 0; tt < G; ++tt) sm[TL::idxA(line, tt, t * EG + i2)] = a[i2 * G + tt];
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) a[k2] = sm[TL::idxA(line, t, k2)];
+    __syncthreads();
+  }
+  // ---- columns: undo pass 1
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmulc(a[k2], tw[t * k2]);
+  dft<E, true>(a);
+  // ---- transpose back
+#pragma unroll
+  for (int j = 0; j < E; ++j) sm[TL::idxB(t + G * j, line)] = a[j];
+  __syncthreads();
+#pragma unroll
+  for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+    for (int k1 = 0; k1 < G; ++k1) a[i2 * G + k1] = sm[TL::idxB(line, t * EG + i2 + E * k1)];
+  __syncthreads();
+  // ---- rows: undo pass 2
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2) dft<G, true>(&a[i2 * G]);
+#pragma unroll
+    for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+      for (int tt = 0; tt < G; ++tt) sm[TL::idxA(line, tt, t * EG + i2)] = a[i2 * G + tt];
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) a[k2] = sm[TL::idxA(line, t, k2)];
+    __syncthreads();
+  }
+  // ---- rows: undo pass 1
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmulc(a[k2], tw[t * k2]);
+  dft<E, true>(a);
+}
+
+// frequency index of COL-layout register r = i2 * G + k1 for thread part t
+template <int M>
+__device__ __forceinline__ int col_freq(int t, int r) {
+  using TL = Tile<M>;
+  return t * TL::EG + (r / TL::G) + TL::E * (r % TL::G);
+}
+
+}  // namespace ptycho

@@ -1,0 +1,268 @@
+// Atomic-free simultaneous object / probe update of the data-parallel engine.
+//
+//   N_O(r) = sum_n c_n(r - r_n),            c_n = sum_k conj(P_k) dpsi_{n,k}
+//   D_O(r) = sum_n sum_k |P_k(r - r_n)|^2
+//   O     += beta_O N_O / (D_O + delta_O max D_O)           (pixels with D_O = 0 unchanged)
+//   N_P,k  = sum_n conj(o_n) dpsi_{n,k},   D_P = sum_n |o_n|^2
+//   P_k   += beta_P N_P,k / (D_P + delta_P max D_P)         (pixels with D_P = 0 unchanged)
+//
+// The paper's engines (ePIE, rPIE, DM, LSQML; Sec. 1 and Sec. 4.5) all move
+// the object and probe with conj(P) dpsi / |P|^2 style steps; this is the
+// simultaneous form of that step. Every sum runs in a fixed order (per-tile
+// position lists in increasing n, per-slot partials in slot order), so an
+// iteration is bitwise reproducible.
+//
+// The intensity error of Sec. 4.2, E = sqrt(sum (Ihat - I)^2 / sum I^2), is
+// finished here in FP64 from the per-slot partials of the fused kernel.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "engine.h"
+#include "fft.cuh"
+
+namespace ptycho {
+
+// ------------------------------------------------------------------ plan-time sums: sum I, sum I^2, bad values
+__global__ void k_intensity_sums(const float* __restrict__ I, size_t count, double* __restrict__ partials) {
+  __shared__ double s1[256], s2[256], s3[256];
+  double a = 0.0, b = 0.0, bad = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = I[i];
+    if (!isfinite(v)) bad += 1e30;
+    else if (v < 0.f) bad += 1.0;
+    else {
+      a += (double)v;
+      b += (double)v * (double)v;
+    }
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  s3[threadIdx.x] = bad;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] += s2[threadIdx.x + w];
+      s3[threadIdx.x] += s3[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x + 0] = s1[0];
+    partials[3 * blockIdx.x + 1] = s2[0];
+    partials[3 * blockIdx.x + 2] = s3[0];
+  }
+}
+
+__global__ void k_finish_sums(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < nblocks; ++i) {
+      a += partials[3 * i];
+      b += partials[3 * i + 1];
+      c += partials[3 * i + 2];
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+  }
+}
+
+cudaError_t launch_intensity_sums(const float* I, size_t count, double* partials, int nblocks, cudaStream_t s) {
+  k_intensity_sums<<<nblocks, 256, 0, s>>>(I, count, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_finish_sums(const double* partials, int nblocks, double* out, cudaStream_t s) {
+  k_finish_sums<<<1, 32, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ probe: sum the per-slot partials
+// grid (ceil(M^2 / 256), K + 1): y < K sums N_P for mode y; y == K sums D_P, |P|^2 map and block max
+__global__ void k_probe_gather(const UpdateArgs u) {
+  const int MM = u.M * u.M;
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  __shared__ float smax[256];
+  if ((int)blockIdx.y < u.K) {
+    if (p >= MM) return;
+    const int k = blockIdx.y;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int s = 0; s < u.slots; ++s) acc = cadd(acc, u.pacc[((size_t)s * u.K + k) * MM + p]);
+    u.np_sum[(size_t)k * MM + p] = acc;
+    return;
+  }
+  float dp = 0.f;
+  if (p < MM) {
+#pragma unroll 8
+    for (int s = 0; s < u.slots; ++s) dp += u.dacc[(size_t)s * MM + p];
+    float p2 = 0.f;
+    for (int k = 0; k < u.K; ++k) p2 += cabs2(u.P[(size_t)k * MM + p]);
+    u.dp_sum[p] = dp;
+    u.p2[p] = p2;
+  }
+  smax[threadIdx.x] = dp;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) u.blk_max_p[blockIdx.x] = smax[0];
+}
+
+// ------------------------------------------------------------------ object: per-tile gather of the contributions
+// grid (tiles_x, tiles_y, kObjSplit), block 32 x 8; thread (tx, ty) owns pixels (Y0 + ty + 8 i, X0 + tx)
+__global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
+  const int tile = blockIdx.y * u.tiles_x + blockIdx.x;
+  const int split = blockIdx.z;
+  const int X = blockIdx.x * kObjTile + threadIdx.x;
+  const int Y0 = blockIdx.y * kObjTile + threadIdx.y;
+  const int M = u.M;
+  const size_t MM = (size_t)M * M;
+  float2 acc[4];
+  float den[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    acc[i] = make_float2(0.f, 0.f);
+    den[i] = 0.f;
+  }
+  const int s0 = u.tile_start[tile], s1 = u.tile_start[tile + 1];
+  for (int idx = s0 + split; idx < s1; idx += kObjSplit) {
+    const int n = u.tile_pos[idx];
+    const int2 pn = u.pos[n];
+    const int cx = X - pn.y;
+    if (cx < 0 || cx >= M) continue;
+    const float2* cn = u.cn + (size_t)n * MM;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int cy = Y0 + 8 * i - pn.x;
+      if (cy >= 0 && cy < M) {
+        acc[i] = cadd(acc[i], cn[(size_t)cy * M + cx]);
+        den[i] += u.p2[cy * M + cx];
+      }
+    }
+  }
+  if (X >= u.obj_w) return;
+  const size_t plane = (size_t)u.obj_h * u.obj_w;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int Y = Y0 + 8 * i;
+    if (Y < u.obj_h) {
+      u.no_part[split * plane + (size_t)Y * u.obj_w + X] = acc[i];
+      u.do_part[split * plane + (size_t)Y * u.obj_w + X] = den[i];
+    }
+  }
+}
+
+// sum the kObjSplit partials in order (into split 0) and take the tile maximum of D_O
+__global__ void __launch_bounds__(256) k_obj_finalize(const UpdateArgs u) {
+  const int tile = blockIdx.y * u.tiles_x + blockIdx.x;
+  const int X = blockIdx.x * kObjTile + threadIdx.x;
+  const int Y0 = blockIdx.y * kObjTile + threadIdx.y;
+  const size_t plane = (size_t)u.obj_h * u.obj_w;
+  __shared__ float smax[256];
+  float m = 0.f;
+  if (X < u.obj_w) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int Y = Y0 + 8 * i;
+      if (Y >= u.obj_h) break;
+      const size_t q = (size_t)Y * u.obj_w + X;
+      float2 a = u.no_part[q];
+      float d = u.do_part[q];
+      for (int s = 1; s < kObjSplit; ++s) {
+        a = cadd(a, u.no_part[s * plane + q]);
+        d += u.do_part[s * plane + q];
+      }
+      u.no_part[q] = a;
+      u.do_part[q] = d;
+      m = fmaxf(m, d);
+    }
+  }
+  const int lt = threadIdx.y * 32 + threadIdx.x;
+  smax[lt] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (lt < w) smax[lt] = fmaxf(smax[lt], smax[lt + w]);
+    __syncthreads();
+  }
+  if (lt == 0) u.blk_max_o[tile] = smax[0];
+}
+
+__device__ float block_max_of(const float* vals, int n) {
+  __shared__ float smax[256];
+  float m = 0.f;
+  const int lt = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nt = blockDim.x * blockDim.y;
+  for (int i = lt; i < n; i += nt) m = fmaxf(m, vals[i]);
+  smax[lt] = m;
+  __syncthreads();
+  for (int w = nt / 2; w > 0; w >>= 1) {
+    if (lt < w) smax[lt] = fmaxf(smax[lt], smax[lt + w]);
+    __syncthreads();
+  }
+  const float r = smax[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_obj_apply(const UpdateArgs u) {
+  const float maxd = block_max_of(u.blk_max_o, u.tiles_x * u.tiles_y);
+  const int X = blockIdx.x * kObjTile + threadIdx.x;
+  const int Y0 = blockIdx.y * kObjTile + threadIdx.y;
+  if (X >= u.obj_w) return;
+  const float floor_d = u.delta_obj * maxd;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int Y = Y0 + 8 * i;
+    if (Y >= u.obj_h) break;
+    const size_t q = (size_t)Y * u.obj_w + X;
+    const float d = u.do_part[q];
+    if (d > 0.f) {
+      const float w = u.beta_obj / (d + floor_d);
+      const float2 num = u.no_part[q];
+      float2 o = u.O[q];
+      o.x = fmaf(w, num.x, o.x);
+      o.y = fmaf(w, num.y, o.y);
+      u.O[q] = o;
+    }
+  }
+}
+
+// grid (ceil(M^2 / 256), K): apply the probe step; block (0, 0) also finishes the FP64 error
+__global__ void k_probe_apply(const UpdateArgs u) {
+  const float maxd = block_max_of(u.blk_max_p, u.probe_blocks);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    double e = 0.0;
+    for (int s = 0; s < u.slots; ++s) e += u.errpart[s];
+    u.errhist[u.hist_index] = sqrt(e / u.errden);
+  }
+  if (!u.update_probe) return;
+  const int MM = u.M * u.M;
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p >= MM) return;
+  const float d = u.dp_sum[p];
+  if (d > 0.f) {
+    const float w = u.beta_probe / (d + u.delta_probe * maxd);
+    const size_t q = (size_t)blockIdx.y * MM + p;
+    const float2 num = u.np_sum[q];
+    float2 pr = u.P[q];
+    pr.x = fmaf(w, num.x, pr.x);
+    pr.y = fmaf(w, num.y, pr.y);
+    u.P[q] = pr;
+  }
+}
+
+cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s) {
+  const int MM = u.M * u.M;
+  const int pb = (MM + 255) / 256;
+  k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+  const dim3 tb(32, 8);
+  k_obj_gather<<<dim3(u.tiles_x, u.tiles_y, kObjSplit), tb, 0, s>>>(u);
+  k_obj_finalize<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
+  k_obj_apply<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
+  k_probe_apply<<<dim3(pb, u.K), 256, 0, s>>>(u);
+  return cudaGetLastError();
+}
+
+}  // namespace ptycho

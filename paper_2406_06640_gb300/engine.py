@@ -1,0 +1,64 @@
+"""Torch-facing wrapper of the C ABI: device tensors in, device tensors updated in place.
+
+PyTorch provides device memory and the stream; every step of the iteration
+runs in libptycho.so. Inputs on the host, or a missing CUDA device, raise.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+import torch
+
+from .binding import Plan
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype: torch.dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Reconstruction:
+    """A plan bound to a torch stream.
+
+    params: dict with the fields of ptycho_params (see include/ptycho.h).
+    intensities: (N, M, M) float32 CUDA tensor.
+    positions: (N, 2) int32 tensor (CPU or CUDA) or numpy array of (row, col) top-left corners.
+    """
+
+    def __init__(self, params: dict, intensities: torch.Tensor, positions, stream: Optional[torch.cuda.Stream] = None):
+        _require_cuda(intensities, "intensities", torch.float32)
+        if isinstance(positions, np.ndarray):
+            positions = torch.from_numpy(np.ascontiguousarray(positions, dtype=np.int32))
+        positions = positions.to(torch.int32).contiguous()
+        self.params = dict(params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(intensities.device)
+        self._positions = positions  # keep alive across the plan call
+        self._plan = Plan(self.params, intensities.data_ptr(), positions.data_ptr(), self.stream.cuda_stream)
+
+    def iterate(self, obj: torch.Tensor, probe: torch.Tensor, n_iter: int = 1):
+        _require_cuda(obj, "object", torch.complex64)
+        _require_cuda(probe, "probe", torch.complex64)
+        self._plan.iterate(obj.data_ptr(), probe.data_ptr(), n_iter)
+
+    def error(self) -> float:
+        return self._plan.error()
+
+    def errors(self, n: int) -> list:
+        return self._plan.error_history(n)
+
+    def profile(self, enable: bool = True):
+        self._plan.profile(enable)
+
+    def profile_read(self) -> tuple:
+        return self._plan.profile_read()
+
+    def launches_per_iteration(self, in_window: bool) -> int:
+        return self._plan.launches_per_iteration(in_window)
+
+    def close(self):
+        self._plan.close()

@@ -1,0 +1,94 @@
+"""C-ABI boundary on the CPU: the library builds, loads, exports every declared
+symbol, the ctypes mirror of ptycho_params matches the C layout, and host-side
+validation rejects bad requests before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2406_06640_gb300 as pg
+from paper_2406_06640_gb300.binding import PtychoParams, make_params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _declared_functions():
+    names = set()
+    for h in os.listdir(INCLUDE):
+        if h.endswith(".h"):
+            text = open(os.path.join(INCLUDE, h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(ptycho_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pg.load()
+    declared = _declared_functions()
+    assert {"ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_destroy"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(pg.EXPORTED) <= declared
+
+
+def test_ctypes_params_layout_matches_c(tmp_path):
+    fields = [f for f, _ in PtychoParams._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "ptycho.h"', "int main(void) {",
+           '  printf("%zu\\n", sizeof(ptycho_params));']
+    src += [f'  printf("%zu\\n", offsetof(ptycho_params, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", f"-I{INCLUDE}", str(c), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(PtychoParams)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(PtychoParams, f).offset == off, f
+
+
+def _plan_status(**over):
+    base = dict(M=64, K=1, N=4, obj_h=128, obj_w=128, geometry="far", sigma1=1.0, sigma2=1.0)
+    base.update(over)
+    p, keep = make_params(base)
+    h = ctypes.c_void_p()
+    lib = pg.load()
+    # valid-looking non-NULL host buffers: validation runs before any device call
+    I = np.zeros(4, np.float32)
+    pos = np.zeros(8, np.int32)
+    st = lib.ptycho_plan(ctypes.byref(p), I.ctypes.data, pos.ctypes.data, None, ctypes.byref(h))
+    return st, lib.ptycho_last_error().decode()
+
+
+@pytest.mark.parametrize("over,expect", [
+    (dict(M=7), 1), (dict(M=1024), 1), (dict(M=256), 4), (dict(K=0), 1), (dict(K=9), 4), (dict(N=0), 1),
+    (dict(obj_h=32), 1), (dict(geometry=5), 1), (dict(blur_domain=3), 1), (dict(geometry="near", fresnel_F=0.0), 1),
+    (dict(sigma1=-1.0), 1), (dict(kernel_size=10), 1), (dict(kernel_size=33), 1), (dict(alpha1=1.5), 1),
+    (dict(cbar_min=0.0), 1), (dict(cbar_min=2.0, cbar_max=1.0), 1), (dict(windows=[(0, 3)]), 1),
+    (dict(windows=[(5, 4)]), 1), (dict(start_iteration=0), 1), (dict(delta_obj=-1.0), 1),
+    (dict(eps_mod=float("nan")), 1),
+])
+def test_validation_rejects_bad_requests(over, expect):
+    st, msg = _plan_status(**over)
+    assert st == expect, msg
+    assert msg
+
+
+def test_null_arguments():
+    lib = pg.load()
+    p, keep = make_params(dict(M=64, K=1, N=4, obj_h=128, obj_w=128))
+    assert lib.ptycho_plan(ctypes.byref(p), None, None, None, None) == 1
+    h = ctypes.c_void_p()
+    assert lib.ptycho_plan(None, None, None, None, ctypes.byref(h)) == 1
+    assert lib.ptycho_iterate(None, None, None, 1) == 1
+    e = ctypes.c_double()
+    assert lib.ptycho_error(None, ctypes.byref(e)) == 1
+    assert lib.ptycho_destroy(None) == 0
+
+
+def test_version_string():
+    assert "sm_103a" in pg.version()

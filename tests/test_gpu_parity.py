@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA engine (through the C ABI) against the FP64 oracle.
+
+Bar: relative L2 <= 1e-4 for the object, the probe and every iteration's
+intensity error (the FP32-engine-vs-FP64 target for config 0 after 50
+iterations), on seeded synthetic inputs. Cases span several object tiles, a
+ragged tile edge, boxes touching the object border, one position, every
+probe size the fused kernel handles (8..128), 1..8 modes, both geometries,
+both blur domains, anisotropic and zero sigma, the smallest and largest
+kernel, complex-constraint windows and a delayed probe update.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from synth import make_problem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return torch.device("cuda:0")
+
+
+def run_gpu(prob, params, n_iter, chunks=None):
+    from paper_2406_06640_gb300.engine import Reconstruction
+
+    dev = _dev()
+    I = torch.from_numpy(np.ascontiguousarray(prob.I)).to(dev)
+    O = torch.from_numpy(np.ascontiguousarray(prob.O0.astype(np.complex64))).to(dev)
+    P = torch.from_numpy(np.ascontiguousarray(prob.P0.astype(np.complex64))).to(dev)
+    rec = Reconstruction(params, I, prob.positions)
+    for c in (chunks or [n_iter]):
+        rec.iterate(O, P, c)
+    E = np.array(rec.errors(n_iter))
+    torch.cuda.synchronize()
+    out = O.cpu().numpy().astype(np.complex128), P.cpu().numpy().astype(np.complex128), E
+    rec.close()
+    return out
+
+
+def run_oracle(prob, params, n_iter):
+    prm = oracle.Params.from_dict(params)
+    return oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, prm, n_iter)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def check(prob, params, n_iter, tol=TOL):
+    Og, Pg, Eg = run_gpu(prob, params, n_iter)
+    Oo, Po, Eo = run_oracle(prob, params, n_iter)
+    eo, ep = rel(Og, Oo), rel(Pg, Po)
+    ee = float(np.max(np.abs(Eg - Eo) / Eo))
+    print(f"rel L2 object {eo:.3e} probe {ep:.3e} error {ee:.3e}")
+    assert Eg.shape == Eo.shape
+    assert eo <= tol and ep <= tol and ee <= tol, (eo, ep, ee)
+    return Og, Pg, Eg
+
+
+def test_config0_50_iterations():
+    p = make_problem(0)
+    check(p, p.params, 50)
+
+
+def test_config0_50_iterations_with_complex_constraint_window():
+    p = make_problem(0)
+    check(p, dict(p.params, windows=[(5, 35)], alpha1=1.0, alpha2=0.0), 50)
+
+
+def test_far_field_modes_intensity_blur_ragged_tiles():
+    p = make_problem(0, scan_side=5, obj_side=150, M=32, K=3, sigma=1.2)
+    rng = np.random.default_rng(5)
+    pos = p.positions.copy()
+    pos[0] = (0, 0)
+    pos[1] = (150 - 32, 150 - 32)
+    pos[2] = (0, 150 - 32)
+    p.positions = pos
+    prm = dict(p.params, blur_domain="intensity", sigma1=0.7, sigma2=1.6, windows=[(2, 3)], alpha1=0.5,
+               alpha2=0.3, probe_update_start=2, beta_obj=0.9, beta_probe=0.7, delta_obj=2e-3, delta_probe=5e-4)
+    del rng
+    check(p, prm, 5)
+
+
+def test_near_field_two_modes():
+    p = make_problem(0, scan_side=4, obj_side=128, M=64, K=2, geometry="near", sigma=2.0)
+    check(p, dict(p.params, sigma1=2.0, sigma2=2.0), 5)
+
+
+def test_near_field_eight_modes_m128():
+    p = make_problem(0, scan_side=3, obj_side=200, M=128, K=8, geometry="near", sigma=1.5)
+    check(p, dict(p.params, sigma1=1.5, sigma2=1.5, blur_domain="intensity"), 3)
+
+
+@pytest.mark.parametrize("M,K,ks,sig", [(8, 2, 11, 1.0), (16, 1, 1, 0.0), (32, 1, 11, 0.0), (64, 4, 31, 3.0)])
+def test_probe_sizes_and_kernels(M, K, ks, sig):
+    p = make_problem(0, scan_side=4, obj_side=M * 3, M=M, K=K, sigma=max(sig, 0.5))
+    check(p, dict(p.params, kernel_size=ks, sigma1=sig, sigma2=sig), 4)
+
+
+def test_single_position():
+    p = make_problem(0, scan_side=1, obj_side=64, M=64)
+    check(p, p.params, 3)
+
+
+def test_config1_full_size_two_iterations():
+    """Full configuration 1 (M = 128, K = 4, 900 positions, 640^2 object) in the launch configuration
+    the benchmark times, compared element by element with the oracle over two iterations."""
+    p = make_problem(1)
+    check(p, p.params, 2)
+
+
+def test_deterministic_and_resumable():
+    p = make_problem(0, scan_side=6, obj_side=144)
+    prm = dict(p.params, windows=[(2, 3)])
+    O1, P1, E1 = run_gpu(p, prm, 5)
+    O2, P2, E2 = run_gpu(p, prm, 5)
+    assert np.array_equal(O1, O2) and np.array_equal(P1, P2) and np.array_equal(E1, E2)
+    O3, P3, E3 = run_gpu(p, prm, 5, chunks=[3, 2])
+    assert np.array_equal(O1, O3) and np.array_equal(P1, P3) and np.array_equal(E1, E3)
+
+
+def test_errors_reported_by_status():
+    from paper_2406_06640_gb300 import PtychoError
+    from paper_2406_06640_gb300.engine import Reconstruction
+
+    dev = _dev()
+    p = make_problem(0, scan_side=2, obj_side=96)
+    I = torch.from_numpy(p.I).to(dev)
+    bad = p.positions.copy()
+    bad[1] = (96 - 63, 0)
+    with pytest.raises(PtychoError) as ei:
+        Reconstruction(p.params, I, torch.from_numpy(bad).to(dev))
+    assert ei.value.status == 1
+    In = I.clone()
+    In[0, 3, 3] = float("nan")
+    with pytest.raises(PtychoError) as ei:
+        Reconstruction(p.params, In, p.positions)
+    assert ei.value.status == 5
+    In = I.clone()
+    In[1, 0, 0] = -1.0
+    with pytest.raises(PtychoError) as ei:
+        Reconstruction(p.params, In, p.positions)
+    assert ei.value.status == 1
+    rec = Reconstruction(p.params, I, p.positions)
+    with pytest.raises(PtychoError) as ei:
+        rec.error()
+    assert ei.value.status == 1
