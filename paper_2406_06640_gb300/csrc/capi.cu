@@ -188,6 +188,10 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   if (h_sums[2] > 0) return fail(PTYCHO_EINVAL, "intensities contain negative values");
   if (!(h_sums[1] > 0)) return fail(PTYCHO_EINVAL, "intensities are all zero");
   pl->errden = h_sums[1];
+  float* d_sqrtI;
+  PT_CUDA(pl->alloc(&d_sqrtI, count), "alloc sqrt intensities");
+  PT_CUDA(launch_sqrt(d_I, d_sqrtI, count, s), "sqrt intensities");
+  pl->fa.sqrtI = d_sqrtI;
   pl->eps = p.eps_mod > 0 ? p.eps_mod : 1e-6 * std::sqrt(h_sums[0] / (double)count);
 
   // twiddles, Fresnel factors, taps (FP64 on the host, rounded once)

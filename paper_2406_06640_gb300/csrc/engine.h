@@ -18,6 +18,7 @@ struct FusedArgs {
   const float2* O;      // object, obj_h x obj_w, row-major
   const float2* P;      // probe modes, K x M x M
   const float* I;       // measured intensities, N x M x M (far field: DC at (M/2, M/2))
+  const float* sqrtI;   // sqrt of the measured intensities (computed once per plan)
   const int2* pos;      // top-left (row, col) of each box
   int N, K, obj_w;
   int near_field;       // 0: centred FFT; 1: Fresnel transfer function
@@ -72,5 +73,6 @@ cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s);
 // plan-time helpers (update.cu)
 cudaError_t launch_intensity_sums(const float* I, size_t count, double* partials, int nblocks, cudaStream_t s);
 cudaError_t launch_finish_sums(const double* partials, int nblocks, double* out2, cudaStream_t s);
+cudaError_t launch_sqrt(const float* I, float* out, size_t count, cudaStream_t s);
 
 }  // namespace ptycho

@@ -16,18 +16,20 @@
 // between them. The inverse runs the same steps mirrored, so it consumes the
 // register layout that the forward leaves and returns to the starting one.
 //
-// Register layouts (tid in [0, T)):
-//   ROW layout: y = tid / G, t = tid % G, register j holds element (y, t + G j)
-//   COL layout: v = tid / G, t = tid % G, register r = i2 * G + k1 holds
-//               frequency (u, v) with u = t * (E / G) + i2 + E k1
+// Thread mappings (virtual thread vt in [0, T)):
+//   ROW phase   (line, t) = (vt / G, vt % G); register j holds element (line, t + G j)
+//   COLUMN phase (c, t)   = (vt / G, vt % G); after the forward transform register
+//               r = i2 * G + k1 holds frequency (u, c), u = t * (E / G) + i2 + E k1
+// The G threads of one line sit in one warp, so the line-internal swaps need
+// only a warp barrier; the transpose needs the whole CTA.
 //
-// Shared-memory swizzles (8-byte elements; a half-warp is conflict-free when
-// its 16 lanes hit 16 distinct slots mod 16):
-//   exchange A (row-internal) at  line * M + (swzA(k2 G + t) ^ ((line G) & (E-1)))
-//   exchange B (transpose)    at  x * M + (y ^ swzB(x))
-// with swzA(o) = 16 (o >> 4) + ((o & 15) ^ ((o >> 4) & 15)) for E = 16 and
-// swzB(x) = (x & (E-1) & ~m) ^ ((x & m) << (log2 E - s)), m = 2^s - 1,
-// s = log2(E / G).
+// Shared-memory layouts are affine in the thread's fixed coordinates plus a
+// compile-time offset (so no per-element address survives across phases), and
+// every exchange is bank-conflict-free for 8-byte elements:
+//   line-internal swap     line * LDA + k2 * SA + t * ST   (SA, ST, LDA per M below)
+//   transpose              x * M + (y ^ hB(x)), hB(x) = (x' & ~m) ^ ((x' & m) << (log2 E - s)),
+//                          x' = x mod E, m = 2^s - 1, s = log2(E / G)  (XOR swizzle)
+//   twiddles W_M^(t k2)    t * (E + 1) + k2
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -166,136 +168,191 @@ __device__ __forceinline__ void dft(float2* a) {
 template <int M_>
 struct Tile {
   static constexpr int M = M_;
-  static constexpr int E = M < 16 ? M : 16;         // registers per thread
-  static constexpr int G = M / E;                    // threads per line
-  static constexpr int T = M * G;                    // threads per tile
-  static constexpr int EG = E / G;                   // pass-2 DFTs per thread
-  static constexpr int LOG2E = E == 16 ? 4 : E == 8 ? 3 : E == 4 ? 2 : E == 2 ? 1 : 0;
-  static constexpr int S = (EG == 16 ? 4 : EG == 8 ? 3 : EG == 4 ? 2 : EG == 2 ? 1 : 0);
+  static constexpr int E = M < 16 ? M : 16;  // registers per line
+  static constexpr int G = M / E;             // threads per line
+  static constexpr int T = M * G;             // virtual threads per tile
+  static constexpr int EG = E / G;            // pass-2 DFTs per thread
   static_assert(M == 8 || M == 16 || M == 32 || M == 64 || M == 128 || M == 256, "M must be 8..256");
+  // row-internal swap strides (searched for conflict-free half-warps)
+  static constexpr int SA = M == 32 ? 3 : M == 64 ? 5 : M == 128 ? 1 : M == 256 ? 17 : 1;
+  static constexpr int ST = M == 32 ? 8 : M == 64 ? 4 : M == 128 ? 18 : M == 256 ? 1 : 1;
+  static constexpr int LDA = M == 32 ? 55 : M == 64 ? 89 : M == 128 ? 143 : M == 256 ? 271 : E;
+  static constexpr int LDN = G > 1 ? M + G : M + 1;   // natural [y][x] layout row stride
+  static constexpr int LDW = E + 1;                   // twiddle table row stride
+  static constexpr int LOG2E = E == 16 ? 4 : E == 8 ? 3 : 0;
+  static constexpr int S = EG == 16 ? 4 : EG == 8 ? 3 : EG == 4 ? 2 : EG == 2 ? 1 : 0;
+  static constexpr int cmax(int a, int b) { return a > b ? a : b; }
+  static constexpr int SMEM = cmax(cmax(G > 1 ? M * LDA : 0, M * M), M * LDN);  // float2 slots
 
-  // exchange A: line-internal swap, element (line, t, k2)
-  __device__ __forceinline__ static int idxA(int line, int t, int k2) {
-    const int o = k2 * G + t;
-    int sw;
-    if constexpr (E == 16) sw = (o & ~15) | ((o & 15) ^ ((o >> 4) & 15));
-    else sw = o;
-    return line * M + (sw ^ ((line * G) & (E - 1)));
-  }
-  // exchange B: transpose, element (y, x)
+  __device__ __forceinline__ static int idxA(int line, int t, int k2) { return line * LDA + k2 * SA + t * ST; }
   __device__ __forceinline__ static int idxB(int y, int x) {
     constexpr int m = (1 << S) - 1;
     const int xl = x & (E - 1);
-    const int sw = (xl & ~m) ^ ((xl & m) << (LOG2E - S));
-    return x * M + (y ^ sw);
+    return x * M + (y ^ ((xl & ~m) ^ ((xl & m) << (LOG2E - S))));
   }
-  // natural [y][x] layout with a row XOR (used for the mode-sum exchanges)
-  __device__ __forceinline__ static int idxN(int y, int x) { return y * M + (x ^ ((y * G) & (E - 1))); }
+  __device__ __forceinline__ static int idxN(int y, int x) { return y * LDN + x; }
 };
 
 // ------------------------------------------------------------------ 2-D transform steps
 // tw[m] = W_M^m for m in [0, M) (forward convention); the inverse uses conj.
+// A CTA of T / V threads runs the tile: thread `tid` plays the V virtual
+// threads vtid = tid + v * (T / V), v in [0, V), and keeps V x E registers.
 
-// ROW layout registers -> COL layout registers (forward 2-D DFT, unscaled)
-template <int M>
-__device__ __forceinline__ void fft2_forward(float2 (&a)[Tile<M>::E], float2* sm, const float2* tw, int tid) {
+// ROW layout registers -> COL layout registers (forward 2-D DFT, unscaled).
+// tw: twiddle table, tw[t * (E + 1) + k2] = W_M^(t k2) for t < G.
+// The shared buffer must be free on entry; it is free again on return.
+template <int M, int V>
+__device__ __forceinline__ void fft2_forward(float2 (&a)[V][Tile<M>::E], float2* sm, const float2* tw, int tid) {
   using TL = Tile<M>;
-  constexpr int E = TL::E, G = TL::G, EG = TL::EG;
-  const int line = tid / G, t = tid % G;
-  // ---- rows: pass 1
-  dft<E, false>(a);
+  constexpr int E = TL::E, G = TL::G, EG = TL::EG, TR = TL::T / V, W = TL::LDW;
+  // ---- rows: pass 1 (ROW mapping)
 #pragma unroll
-  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmul(a[k2], tw[t * k2]);
+  for (int v = 0; v < V; ++v) {
+    const int t = (tid + v * TR) % G;
+    dft<E, false>(a[v]);
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmul(a[v][k2], tw[t * W + k2]);
+  }
   if constexpr (G > 1) {
 #pragma unroll
-    for (int k2 = 0; k2 < E; ++k2) sm[TL::idxA(line, t, k2)] = a[k2];
+    for (int v = 0; v < V; ++v) {
+      const int line = (tid + v * TR) / G, t = (tid + v * TR) % G;
+#pragma unroll
+      for (int k2 = 0; k2 < E; ++k2) sm[TL::idxA(line, t, k2)] = a[v][k2];
+    }
+    __syncwarp();  // the swap stays inside the warp
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int line = (tid + v * TR) / G, t = (tid + v * TR) % G;
+#pragma unroll
+      for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+        for (int tt = 0; tt < G; ++tt) a[v][i2 * G + tt] = sm[TL::idxA(line, tt, t * EG + i2)];
+      // ---- rows: pass 2
+#pragma unroll
+      for (int i2 = 0; i2 < EG; ++i2) dft<G, false>(&a[v][i2 * G]);
+    }
     __syncthreads();
+  }
+  // ---- transpose: ROW thread (line, t) holds x = t * EG + i2 + E k1 at register i2 * G + k1
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int line = (tid + v * TR) / G, t = (tid + v * TR) % G;
 #pragma unroll
     for (int i2 = 0; i2 < EG; ++i2)
 #pragma unroll
-      for (int tt = 0; tt < G; ++tt) a[i2 * G + tt] = sm[TL::idxA(line, tt, t * EG + i2)];
-    // ---- rows: pass 2
-#pragma unroll
-    for (int i2 = 0; i2 < EG; ++i2) dft<G, false>(&a[i2 * G]);
-    __syncthreads();
+      for (int k1 = 0; k1 < G; ++k1) sm[TL::idxB(line, t * EG + i2 + E * k1)] = a[v][i2 * G + k1];
   }
-  // ---- transpose: thread (y = line, t) holds x = t * EG + i2 + E k1 at register i2 * G + k1
-#pragma unroll
-  for (int i2 = 0; i2 < EG; ++i2)
-#pragma unroll
-    for (int k1 = 0; k1 < G; ++k1) sm[TL::idxB(line, t * EG + i2 + E * k1)] = a[i2 * G + k1];
   __syncthreads();
-  // column v = line reads y = t + G j
+  // ---- columns (COLUMN mapping): column c reads y = t + G j
 #pragma unroll
-  for (int j = 0; j < E; ++j) a[j] = sm[TL::idxB(t + G * j, line)];
-  // ---- columns: pass 1
-  dft<E, false>(a);
+  for (int v = 0; v < V; ++v) {
+    const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
 #pragma unroll
-  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmul(a[k2], tw[t * k2]);
+    for (int j = 0; j < E; ++j) a[v][j] = sm[TL::idxB(t + G * j, c)];
+    dft<E, false>(a[v]);
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmul(a[v][k2], tw[t * W + k2]);
+  }
   if constexpr (G > 1) {
     __syncthreads();
 #pragma unroll
-    for (int k2 = 0; k2 < E; ++k2) sm[TL::idxA(line, t, k2)] = a[k2];
-    __syncthreads();
+    for (int v = 0; v < V; ++v) {
+      const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
 #pragma unroll
-    for (int i2 = 0; i2 < EG; ++i2)
+      for (int k2 = 0; k2 < E; ++k2) sm[TL::idxA(c, t, k2)] = a[v][k2];
+    }
+    __syncwarp();  // the swap stays inside the warp
 #pragma unroll
-      for (int tt = 0; tt < G; ++tt) a[i2 * G + tt] = sm[TL::idxA(line, tt, t * EG + i2)];
+    for (int v = 0; v < V; ++v) {
+      const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
 #pragma unroll
-    for (int i2 = 0; i2 < EG; ++i2) dft<G, false>(&a[i2 * G]);
+      for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+        for (int tt = 0; tt < G; ++tt) a[v][i2 * G + tt] = sm[TL::idxA(c, tt, t * EG + i2)];
+#pragma unroll
+      for (int i2 = 0; i2 < EG; ++i2) dft<G, false>(&a[v][i2 * G]);
+    }
   }
-  __syncthreads();  // shared memory free for reuse on return
+  __syncthreads();
 }
 
-// COL layout registers -> ROW layout registers (inverse 2-D DFT, unscaled: times M^2)
-template <int M>
-__device__ __forceinline__ void fft2_inverse(float2 (&a)[Tile<M>::E], float2* sm, const float2* tw, int tid) {
+// COL layout registers -> ROW layout registers (inverse 2-D DFT, unscaled: times M^2).
+// The shared buffer must be free on entry; it is free again on return.
+template <int M, int V>
+__device__ __forceinline__ void fft2_inverse(float2 (&a)[V][Tile<M>::E], float2* sm, const float2* tw, int tid) {
   using TL = Tile<M>;
-  constexpr int E = TL::E, G = TL::G, EG = TL::EG;
-  const int line = tid / G, t = tid % G;
+  constexpr int E = TL::E, G = TL::G, EG = TL::EG, TR = TL::T / V, W = TL::LDW;
   // ---- columns: undo pass 2
   if constexpr (G > 1) {
 #pragma unroll
-    for (int i2 = 0; i2 < EG; ++i2) dft<G, true>(&a[i2 * G]);
+    for (int v = 0; v < V; ++v) {
+      const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
+#pragma unroll
+      for (int i2 = 0; i2 < EG; ++i2) dft<G, true>(&a[v][i2 * G]);
+#pragma unroll
+      for (int i2 = 0; i2 < EG; ++i2)
+#pragma unroll
+        for (int tt = 0; tt < G; ++tt) sm[TL::idxA(c, tt, t * EG + i2)] = a[v][i2 * G + tt];
+    }
+    __syncwarp();  // the swap stays inside the warp
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
+#pragma unroll
+      for (int k2 = 0; k2 < E; ++k2) a[v][k2] = sm[TL::idxA(c, t, k2)];
+    }
+    __syncthreads();
+  }
+  // ---- columns: undo pass 1, then transpose back
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmulc(a[v][k2], tw[t * W + k2]);
+    dft<E, true>(a[v]);
+#pragma unroll
+    for (int j = 0; j < E; ++j) sm[TL::idxB(t + G * j, c)] = a[v][j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int line = (tid + v * TR) / G, t = (tid + v * TR) % G;
 #pragma unroll
     for (int i2 = 0; i2 < EG; ++i2)
 #pragma unroll
-      for (int tt = 0; tt < G; ++tt) sm[TL::idxA(line, tt, t * EG + i2)] = a[i2 * G + tt];
-    __syncthreads();
-#pragma unroll
-    for (int k2 = 0; k2 < E; ++k2) a[k2] = sm[TL::idxA(line, t, k2)];
-    __syncthreads();
+      for (int k1 = 0; k1 < G; ++k1) a[v][i2 * G + k1] = sm[TL::idxB(line, t * EG + i2 + E * k1)];
   }
-  // ---- columns: undo pass 1
-#pragma unroll
-  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmulc(a[k2], tw[t * k2]);
-  dft<E, true>(a);
-  // ---- transpose back
-#pragma unroll
-  for (int j = 0; j < E; ++j) sm[TL::idxB(t + G * j, line)] = a[j];
-  __syncthreads();
-#pragma unroll
-  for (int i2 = 0; i2 < EG; ++i2)
-#pragma unroll
-    for (int k1 = 0; k1 < G; ++k1) a[i2 * G + k1] = sm[TL::idxB(line, t * EG + i2 + E * k1)];
   __syncthreads();
   // ---- rows: undo pass 2
   if constexpr (G > 1) {
 #pragma unroll
-    for (int i2 = 0; i2 < EG; ++i2) dft<G, true>(&a[i2 * G]);
+    for (int v = 0; v < V; ++v) {
+      const int line = (tid + v * TR) / G, t = (tid + v * TR) % G;
 #pragma unroll
-    for (int i2 = 0; i2 < EG; ++i2)
+      for (int i2 = 0; i2 < EG; ++i2) dft<G, true>(&a[v][i2 * G]);
 #pragma unroll
-      for (int tt = 0; tt < G; ++tt) sm[TL::idxA(line, tt, t * EG + i2)] = a[i2 * G + tt];
-    __syncthreads();
+      for (int i2 = 0; i2 < EG; ++i2)
 #pragma unroll
-    for (int k2 = 0; k2 < E; ++k2) a[k2] = sm[TL::idxA(line, t, k2)];
+        for (int tt = 0; tt < G; ++tt) sm[TL::idxA(line, tt, t * EG + i2)] = a[v][i2 * G + tt];
+    }
+    __syncwarp();  // the swap stays inside the warp
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int line = (tid + v * TR) / G, t = (tid + v * TR) % G;
+#pragma unroll
+      for (int k2 = 0; k2 < E; ++k2) a[v][k2] = sm[TL::idxA(line, t, k2)];
+    }
     __syncthreads();
   }
   // ---- rows: undo pass 1
 #pragma unroll
-  for (int k2 = 1; k2 < E; ++k2) a[k2] = cmulc(a[k2], tw[t * k2]);
-  dft<E, true>(a);
+  for (int v = 0; v < V; ++v) {
+    const int t = (tid + v * TR) % G;
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmulc(a[v][k2], tw[t * W + k2]);
+    dft<E, true>(a[v]);
+  }
 }
 
 // frequency index of COL-layout register r = i2 * G + k1 for thread part t

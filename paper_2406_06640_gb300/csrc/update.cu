@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "engine.h"
 #include "fft.cuh"
 
@@ -66,6 +68,17 @@ __global__ void k_finish_sums(const double* __restrict__ partials, int nblocks, 
     out[1] = b;
     out[2] = c;
   }
+}
+
+__global__ void k_sqrt(const float* __restrict__ I, float* __restrict__ out, size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = sqrtf(I[i]);
+}
+
+cudaError_t launch_sqrt(const float* I, float* out, size_t count, cudaStream_t s) {
+  const int nb = (int)std::min<size_t>(4096, (count + 255) / 256);
+  k_sqrt<<<nb, 256, 0, s>>>(I, out, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_intensity_sums(const float* I, size_t count, double* partials, int nblocks, cudaStream_t s) {
