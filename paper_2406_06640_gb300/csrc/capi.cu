@@ -218,7 +218,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_cn, (size_t)N * MM), "alloc contributions");
   PT_CUDA(pl->alloc(&d_pacc, (size_t)pl->slots * K * MM), "alloc probe partials");
   PT_CUDA(pl->alloc(&d_dacc, (size_t)pl->slots * MM), "alloc probe partials");
-  PT_CUDA(pl->alloc(&d_errpart, (size_t)pl->slots), "alloc error partials");
+  PT_CUDA(pl->alloc(&d_errpart, (size_t)pl->slots * K), "alloc error partials");
 
   // object tiles and their position lists (increasing n)
   const int tx = (p.obj_w + kObjTile - 1) / kObjTile, ty = (p.obj_h + kObjTile - 1) / kObjTile;
@@ -288,6 +288,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ua.pacc = d_pacc;
   ua.dacc = d_dacc;
   ua.errpart = d_errpart;
+  ua.nerr = pl->slots * K;
   ua.tile_start = d_start;
   ua.tile_pos = d_list;
   ua.tiles_x = tx;

@@ -32,7 +32,7 @@ struct FusedArgs {
   float2* cn;           // out: per-position object numerator contributions, N x M x M
   float2* pacc;         // out: per-slot probe numerator partials, slots x K x M x M (accumulated)
   float* dacc;          // out: per-slot probe denominator partials, slots x M x M (accumulated)
-  double* errpart;      // out: per-slot FP64 error numerators
+  double* errpart;      // out: per-CTA FP64 error numerators, slots x K
 };
 
 // fused kernel launch; returns the number of slots (co-resident clusters) used
@@ -46,6 +46,7 @@ struct UpdateArgs {
   const int2* pos;
   int N, K, M, obj_h, obj_w, slots;
   const float2* cn; const float2* pacc; const float* dacc; const double* errpart;
+  int nerr;  // entries of errpart
   // object gather
   const int* tile_start;  // (tiles_y * tiles_x + 1) CSR offsets into tile_pos
   const int* tile_pos;    // position indices per tile, increasing

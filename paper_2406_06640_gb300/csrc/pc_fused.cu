@@ -1,24 +1,29 @@
 // Fused per-position pc-engine kernel: one cluster of K CTAs per scan position,
-// CTA rank k owns probe mode k. Everything between the object gather and the
-// scatter contributions stays on chip:
+// CTA rank k owns probe mode k and rows [k R, (k + 1) R) of the detector
+// (R = ceil(M / K)). Everything between the object gather and the per-position
+// contributions stays on chip:
 //
 //   psi_k   = P_k o_n                                       (Eq. 1, Fig. 1)
 //   Psi_k   = centred FFT2 (far field, checkerboard trick)  (Eq. 1)
 //           | IFFT2(FFT2(psi_k) H)  (near field, Fresnel transfer function)
-//   S       = sum_k |Psi_k|^2   -- summed across the cluster through DSMEM
-//   A^G     = sqrt(S) (x) g  (Eq. 6)  or  I_m = S (x) g (Eq. 2), separable,
-//             zero padded, g of Eq. 7 normalised
+//   |Psi_k|^2 is pushed (DSMEM stores) to the rank owning its row; the owner
+//   sums the K modes in rank order:  S = sum_k |Psi_k|^2
+//   A^G     = sqrt(S) (x) g  (Eq. 6)  or  I_m = S (x) g (Eq. 2), separable and
+//             zero padded, g of Eq. 7 normalised; each owner blurs its own
+//             rows and receives the x-blurred halo rows it needs from the others
 //   R       = sqrt(I_n) / (A^G + eps)   or   sqrt(I_n) / sqrt(I_m + eps^2)
-//             (sqrt(I_n) precomputed once per plan; fast 2-ulp divide / rsqrt)
+//             (sqrt(I_n) precomputed once per plan; fast 2-ulp divide / rsqrt),
+//             pushed by its owner to every rank
 //   Psi'_k  = R Psi_k;  psi'_k = inverse propagation;  dpsi_k = psi'_k - psi_k
-//   c_n     = sum_k conj(P_k) dpsi_k -- summed across the cluster through DSMEM,
-//             written once per position (the object update gathers it per tile)
+//   c_n     = sum_k conj(P_k) dpsi_k: pushed to the row owner, summed in rank
+//             order, written once per position (the object update gathers it)
 //   pacc    += conj(o_n) dpsi_k, dacc += |o_n|^2  (per-slot partials, no atomics)
-//   errpart += sum (Ihat - I_n)^2 in FP64  (rank 0)
+//   error   : compensated FP32 per thread of sum (Ihat - I_n)^2 over own rows,
+//             FP64 across threads, ranks and slots
 //
 // Persistent: cluster `slot` handles positions slot, slot + slots, ... so the
 // per-slot partials are written in a fixed order and the iteration is
-// bitwise reproducible.
+// bitwise reproducible. Five cluster barriers per position order the pushes.
 #include <cuda_runtime.h>
 
 #include "engine.h"
@@ -51,13 +56,79 @@ __device__ __forceinline__ float2 ld_cluster_f2(uint32_t addr) {
   return v;
 }
 
-template <int M>
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_f2(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// ---- tensor memory (TMEM) used as per-thread storage: each thread owns a
+// column range in the 32-lane quarter of its warp (warp w accesses lanes
+// 32 (w % 4) .. 32 (w % 4) + 31; address = lane << 16 | column)
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 16 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15},"
+      " [%16];"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]),
+        "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14,"
+      " %15, %16};" ::"r"(taddr),
+      "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]), "f"(r[8]),
+      "f"(r[9]), "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15])
+      : "memory");
+}
+
+// largest K * ceil(M / K) over the cluster sizes 1..8 (rows of the per-source slots)
+constexpr int max_slot_rows(int M) {
+  int best = 0;
+  for (int K = 1; K <= 8; ++K) {
+    const int r = K * ((M + K - 1) / K);
+    best = r > best ? r : best;
+  }
+  return best;
+}
+
+template <int M, int KH>
 struct FusedSmem {
   static constexpr int LD = M + 1;  // padded row stride of the f32 detector buffers
   static constexpr size_t kX = (size_t)Tile<M>::SMEM * 8;  // FFT exchange buffer
-  static constexpr size_t kF = (size_t)2 * M * LD * 4;     // two f32 detector buffers (aliases the exchange buffer)
-  static constexpr size_t CBUF = ((kX > kF ? kX : kF) + 15) / 16 * 16;
-  static constexpr size_t IBUF = ((size_t)M * LD * 4 + 15) / 16 * 16;
+  // modulus phase (aliases the exchange buffer): R (M rows) + own x-blurred rows with halos
+  static constexpr size_t kF = (size_t)(M + M + 2 * KH) * LD * 4;
+  // contributions received from every rank for the own rows
+  static constexpr size_t kR = (size_t)max_slot_rows(M) * Tile<M>::LDN * 8;
+  static constexpr size_t kXF = kX > kF ? kX : kF;
+  static constexpr size_t CBUF = ((kXF > kR ? kXF : kR) + 15) / 16 * 16;
+  static constexpr size_t IBUF = ((size_t)max_slot_rows(M) * LD * 4 + 15) / 16 * 16;
   static constexpr size_t TWT = ((size_t)Tile<M>::G * Tile<M>::LDW * 8 + 15) / 16 * 16;  // twiddle table
   static constexpr size_t HQ = (size_t)M * 8;                                             // Fresnel factors
   static constexpr size_t TAPS = 2 * kMaxTaps * 4 + 8;
@@ -71,6 +142,13 @@ template <int M>
 struct FusedShape {
   static constexpr int V = M == 128 ? 2 : 1;
   static constexpr int TR = Tile<M>::T / V;
+  // TMEM keeps this CTA's probe mode and its probe-numerator partial (V E complex
+  // values each per thread) when the CTA has whole groups of 4 warps
+  static constexpr bool TMEM = TR % 128 == 0;
+  static constexpr int COLS_PER_THREAD = 4 * V * Tile<M>::E;
+  static constexpr int TMEM_COLS = TMEM ? (TR / 128) * COLS_PER_THREAD : 0;
+  static_assert(!TMEM || (TMEM_COLS >= 32 && TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0),
+                "TMEM allocation must be a power of two in [32, 512] columns");
 };
 
 // detector (row, col) of register r: the near field ends the propagation in
@@ -87,19 +165,19 @@ __device__ __forceinline__ void det_coords(int vt, int r, int& row, int& col) {
   }
 }
 
-// E consecutive outputs of a zero-padded correlation along a line of the
-// padded f32 buffer: out[o] = sum_d g[d] in[c0 + o + d - KH]; `stride` steps
-// between consecutive samples (1 along a row, LD along a column).
+// E consecutive outputs of a zero-padded correlation along a line of a f32
+// buffer: out[o] = sum_d g[d] in[c0 + o + d - KH], samples outside [lo, hi)
+// read as zero; `stride` steps between consecutive samples.
 template <int M, int KH>
-__device__ __forceinline__ void blur_strip(const float* in, int base, int stride, int c0, const float* g,
-                                           float (&out)[Tile<M>::E]) {
+__device__ __forceinline__ void blur_strip(const float* in, int base, int stride, int c0, int lo, int hi,
+                                           const float* g, float (&out)[Tile<M>::E]) {
   constexpr int E = Tile<M>::E;
   constexpr int W = E + 2 * KH;
   float win[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) {
     const int c = c0 - KH + i;
-    win[i] = (c >= 0 && c < M) ? in[base + c * stride] : 0.f;
+    win[i] = (c >= lo && c < hi) ? in[base + c * stride] : 0.f;
   }
   if constexpr (KH <= 7) {
     float gr[2 * KH + 1];
@@ -127,14 +205,16 @@ __device__ __forceinline__ void blur_strip(const float* in, int base, int stride
 template <int M, bool NEAR, int KH>
 __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const FusedArgs a) {
   using TL = Tile<M>;
-  using SM = FusedSmem<M>;
-  constexpr int E = TL::E, G = TL::G, LD = SM::LD;
+  using SM = FusedSmem<M, KH>;
+  constexpr int E = TL::E, G = TL::G, LD = SM::LD, LDN = TL::LDN;
   constexpr int V = FusedShape<M>::V, TR = FusedShape<M>::TR;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* cbuf = reinterpret_cast<float2*>(smem);
-  float* fA = reinterpret_cast<float*>(smem);
-  float* fB = fA + M * LD;
-  float* ibuf = reinterpret_cast<float*>(smem + SM::CBUF);
+  float* Z = reinterpret_cast<float*>(smem);  // R for the whole tile, M x LD
+  float* X = Z;                               // own rows of A (aliases Z, dead before R arrives)
+  float* Yb = Z + M * LD;                     // own x-blurred rows with KH halo rows on each side
+  float2* recv = cbuf;                        // contributions for the own rows, one slot per source rank
+  float* ibuf = reinterpret_cast<float*>(smem + SM::CBUF);  // |Psi|^2 for the own rows, one slot per rank
   float2* s_tw = reinterpret_cast<float2*>(smem + SM::CBUF + SM::IBUF);
   float2* s_h = reinterpret_cast<float2*>(smem + SM::CBUF + SM::IBUF + SM::TWT);
   float* s_gx = reinterpret_cast<float*>(smem + SM::CBUF + SM::IBUF + SM::TWT + SM::HQ);
@@ -142,7 +222,7 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
 
   const int tid = threadIdx.x;
   const int K = a.K;
-  const unsigned rank = cluster_ctarank();
+  const int rank = (int)cluster_ctarank();
   const int slot = blockIdx.x / K;
   const int nslots = gridDim.x / K;
 
@@ -170,12 +250,41 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
   }
   const float2* Pk = a.P + (size_t)rank * M * M;
   float2* pacc = a.pacc + ((size_t)slot * K + rank) * M * M;
+  // ---- TMEM: columns [colP, colP + 2 V E) hold P_k, [colA, colA + 2 V E) the probe numerator
+  constexpr bool TM = FusedShape<M>::TMEM;
+  uint32_t t_lane = 0, colP = 0, colA = 0;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_gy + kMaxTaps);
+  if constexpr (TM) {
+    const int warp = tid / 32;
+    if (warp == 0) tmem_alloc(smem_addr(s_tmem), FusedShape<M>::TMEM_COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    t_lane = *s_tmem + ((uint32_t)(32 * (warp % 4)) << 16);
+    colP = (uint32_t)((warp / 4) * FusedShape<M>::COLS_PER_THREAD);
+    colA = colP + 2 * V * E;
+#pragma unroll
+    for (int q = 0; q < V; ++q)
+#pragma unroll
+      for (int h = 0; h < E / 8; ++h) {
+        float pr[16];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const float2 p = Pk[line[q] * M + tp[q] + G * (8 * h + jj)];
+          pr[2 * jj] = p.x;
+          pr[2 * jj + 1] = p.y;
+        }
+        tmem_st16(t_lane + colP + 2 * (q * E + 8 * h), pr);
+      }
+    tmem_wait_st();
+  }
   float* dacc = a.dacc + (size_t)slot * M * M;
-  const int r0 = (int)rank * M / K, r1 = ((int)rank + 1) * M / K;
+  const int RPO = (M + K - 1) / K;  // rows per owner
+  const int r0 = min(M, rank * RPO), r1 = min(M, r0 + RPO), nrow = r1 - r0;
   const float inv_m2 = 1.0f / (float)(M * M);
-  const uint32_t ibuf_s = smem_addr(ibuf), cbuf_s = smem_addr(cbuf);
+  const uint32_t ibuf_s = smem_addr(ibuf), z_s = smem_addr(Z), yb_s = smem_addr(Yb), recv_s = smem_addr(recv);
   const float eps = a.eps;
-  float err_s = 0.f, err_c = 0.f;  // compensated per-thread sum of (Ihat - I)^2
+  float err_s = 0.f, err_c = 0.f;  // compensated per-thread sum of (Ihat - I)^2 over own rows
 
   for (int n = slot; n < a.N; n += nslots) {
     const bool first = (n == slot);
@@ -183,15 +292,36 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     const float2* On = a.O + (size_t)pn.x * a.obj_w + pn.y;
     float2 v[V][E];
     // ---- exit wave in ROW layout
+    if constexpr (TM) {
 #pragma unroll
-    for (int q = 0; q < V; ++q)
+      for (int q = 0; q < V; ++q)
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int x = tp[q] + G * j;
-        float2 psi = cmul(Pk[line[q] * M + x], On[(size_t)line[q] * a.obj_w + x]);
-        if (!NEAR && ((line[q] + x) & 1)) psi = make_float2(-psi.x, -psi.y);
-        v[q][j] = psi;
-      }
+        for (int h = 0; h < E / 4; ++h) {
+          float pr[8];
+          tmem_ld8(t_lane + colP + 2 * (q * E + 4 * h), pr);
+          float2 o[4];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) o[jj] = On[(size_t)line[q] * a.obj_w + tp[q] + G * (4 * h + jj)];
+          tmem_wait_ld();
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int x = tp[q] + G * (4 * h + jj);
+            float2 psi = cmul(make_float2(pr[2 * jj], pr[2 * jj + 1]), o[jj]);
+            if (!NEAR && ((line[q] + x) & 1)) psi = make_float2(-psi.x, -psi.y);
+            v[q][4 * h + jj] = psi;
+          }
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int x = tp[q] + G * j;
+          float2 psi = cmul(Pk[line[q] * M + x], On[(size_t)line[q] * a.obj_w + x]);
+          if (!NEAR && ((line[q] + x) & 1)) psi = make_float2(-psi.x, -psi.y);
+          v[q][j] = psi;
+        }
+    }
     // ---- forward propagation
     fft2_forward<M, V>(v, cbuf, s_tw, tid);  // COL layout
     if constexpr (NEAR) {
@@ -208,52 +338,67 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
 #pragma unroll
         for (int j = 0; j < E; ++j) v[q][j] = cscale(v[q][j], inv_m2);
     }
-    // ---- |Psi_k|^2 of this mode, then the cluster-wide mode sum
+    // ---- (1) push |Psi_k|^2 into slot `rank` of the row owner's buffer
 #pragma unroll
     for (int q = 0; q < V; ++q)
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         int row, col;
         det_coords<M, NEAR>(tid + q * TR, r, row, col);
-        ibuf[row * LD + col] = cabs2(v[q][r]);
+        const int ow = row / RPO;
+        const int lr = row - ow * RPO;
+        st_cluster_f32(map_rank(ibuf_s + (uint32_t)(((rank * RPO + lr) * LD + col) * 4), (unsigned)ow),
+                       cabs2(v[q][r]));
       }
     cluster_sync_all();
-#pragma unroll 4
-    for (int i = 0; i < V * E; ++i) {
-      const int p = tid + TR * i;
-      const int row = p / M, col = p % M;
-      const uint32_t off = (uint32_t)(row * LD + col) * 4u;
+    // ---- (2) own rows: mode sum in rank order -> X; zero the halo rows that lie outside the tile
+    for (int p = tid; p < nrow * M; p += TR) {
+      const int lr = p / M, col = p % M;
       float s = 0.f;
-      for (int q = 0; q < K; ++q) s += ld_cluster_f32(map_rank(ibuf_s + off, (unsigned)q));
-      fA[row * LD + col] = a.blur_intensity ? s : sqrtf(s);
+      for (int q = 0; q < K; ++q) s += ibuf[(q * RPO + lr) * LD + col];
+      X[lr * LD + col] = a.blur_intensity ? s : sqrtf(s);
+    }
+    for (int p = tid; p < 2 * KH * M; p += TR) {
+      const int h = p / M, col = p % M;
+      const int gr = h < KH ? r0 - KH + h : r1 + (h - KH);
+      if (gr < 0 || gr >= M) Yb[(gr - r0 + KH) * LD + col] = 0.f;
     }
     __syncthreads();
-    // ---- separable blur, x (columns, sigma_1): virtual thread (row, column strip)
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const int vt = tid + q * TR;
-      const int row = vt % M, c0 = (vt / M) * E;
+    // ---- (3) blur along x (columns, sigma_1) of the own rows; push the rows other ranks need as halo
+    for (int w = tid; w < nrow * (M / E); w += TR) {
+      const int lr = w % nrow, c0 = (w / nrow) * E;
+      const int gr = r0 + lr;
       float out[E];
-      blur_strip<M, KH>(fA, row * LD, 1, c0, s_gx, out);
+      blur_strip<M, KH>(X, lr * LD, 1, c0, 0, M, s_gx, out);
 #pragma unroll
-      for (int o = 0; o < E; ++o) fB[row * LD + c0 + o] = out[o];
+      for (int o = 0; o < E; ++o) Yb[(lr + KH) * LD + c0 + o] = out[o];
+      for (int q = 0; q < K; ++q) {
+        if (q == rank) continue;
+        const int q0 = min(M, q * RPO), q1 = min(M, q0 + RPO);
+        if ((gr >= q0 - KH && gr < q0) || (gr >= q1 && gr < q1 + KH)) {
+          const uint32_t base = map_rank(yb_s + (uint32_t)(((gr - q0 + KH) * LD + c0) * 4), (unsigned)q);
+#pragma unroll
+          for (int o = 0; o < E; ++o) st_cluster_f32(base + 4u * o, out[o]);
+        }
+      }
     }
-    __syncthreads();
-    // ---- blur y (rows, sigma_2), modulus ratio and error: virtual thread (column, row strip)
+    cluster_sync_all();
+    // ---- (4) blur along y (rows, sigma_2), modulus ratio and error for the own rows; push R to every rank
     {
       const float* In = a.I + (size_t)n * M * M;
       const float* Sn = a.sqrtI + (size_t)n * M * M;
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const int vt = tid + q * TR;
-        const int col = vt % M, rs = (vt / M) * E;
+      const int nstrip = (nrow + E - 1) / E;
+      for (int w = tid; w < M * nstrip; w += TR) {
+        const int col = w % M, rs = (w / M) * E;
         float out[E];
-        blur_strip<M, KH>(fB, col, LD, rs, s_gy, out);
+        blur_strip<M, KH>(Yb, col, LD, rs + KH, 0, nrow + 2 * KH, s_gy, out);
 #pragma unroll
         for (int o = 0; o < E; ++o) {
-          const int row = rs + o;
+          const int lr = rs + o;
+          if (lr >= nrow) break;
+          const int gr = r0 + lr;
           const float acc = out[o];
-          const float sq = Sn[row * M + col];
+          const float sq = Sn[gr * M + col];
           float ihat, R;
           if (a.blur_intensity) {
             ihat = acc;
@@ -262,28 +407,28 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
             ihat = acc * acc;
             R = __fdividef(sq, acc + eps);
           }
-          if (rank == 0) {
-            const float d = ihat - In[row * M + col];
-            const float y = fmaf(d, d, -err_c);
-            const float tt = err_s + y;
-            err_c = (tt - err_s) - y;
-            err_s = tt;
-          }
-          fA[row * LD + col] = R;
+          const float d = ihat - In[gr * M + col];
+          const float y = fmaf(d, d, -err_c);
+          const float tt = err_s + y;
+          err_c = (tt - err_s) - y;
+          err_s = tt;
+          const uint32_t zoff = z_s + (uint32_t)((gr * LD + col) * 4);
+          for (int q = 0; q < K; ++q) st_cluster_f32(map_rank(zoff, (unsigned)q), R);
         }
       }
     }
-    __syncthreads();
+    cluster_sync_all();
+    // ---- (5) Psi' = R Psi
 #pragma unroll
     for (int q = 0; q < V; ++q)
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         int row, col;
         det_coords<M, NEAR>(tid + q * TR, r, row, col);
-        v[q][r] = cscale(v[q][r], fA[row * LD + col]);
+        v[q][r] = cscale(v[q][r], Z[row * LD + col]);
       }
-    __syncthreads();  // fA overlaps cbuf
-    // ---- back-propagation to ROW layout
+    __syncthreads();  // Z aliases the exchange buffer
+    // ---- (6) back-propagation to ROW layout
     if constexpr (NEAR) {
       fft2_forward<M, V>(v, cbuf, s_tw, tid);
 #pragma unroll
@@ -295,39 +440,93 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
         }
     }
     fft2_inverse<M, V>(v, cbuf, s_tw, tid);
-    // ---- dpsi, contributions
+    cluster_sync_all();  // every rank is done with its exchange buffer, which now receives contributions
+    // ---- (7) dpsi; probe partials; conj(P) dpsi pushed to the row owner
 #pragma unroll
-    for (int q = 0; q < V; ++q)
+    for (int q = 0; q < V; ++q) {
+      const int ln = line[q];
+      const int ow = ln / RPO;
+      const uint32_t dst = map_rank(recv_s + (uint32_t)((rank * RPO + ln - ow * RPO) * LDN * 8), (unsigned)ow);
+      if constexpr (TM) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const int ln = line[q];
-        const int x = tp[q] + G * j;
-        float2 psi_new = cscale(v[q][j], inv_m2);
-        if (!NEAR && ((ln + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
-        const float2 p = Pk[ln * M + x];
-        const float2 o = On[(size_t)ln * a.obj_w + x];
-        const float2 dpsi = csub(psi_new, cmul(p, o));
-        cbuf[TL::idxN(ln, x)] = cconjmul(p, dpsi);
-        const int qi = ln * M + x;
-        const float2 pc = cconjmul(o, dpsi);
-        pacc[qi] = first ? pc : cadd(pacc[qi], pc);
-        if (ln >= r0 && ln < r1) dacc[qi] = first ? cabs2(o) : dacc[qi] + cabs2(o);
-      }
-    cluster_sync_all();
-    {
-      float2* cn = a.cn + (size_t)n * M * M;
-      for (int p = r0 * M + tid; p < r1 * M; p += TR) {
-        const int row = p / M, col = p % M;
-        const uint32_t off = (uint32_t)TL::idxN(row, col) * 8u;
-        float2 s = make_float2(0.f, 0.f);
-        for (int q = 0; q < K; ++q) s = cadd(s, ld_cluster_f2(map_rank(cbuf_s + off, (unsigned)q)));
-        cn[p] = s;
+        for (int h = 0; h < E / 4; ++h) {
+          float pr[8], ac[8];
+          tmem_ld8(t_lane + colP + 2 * (q * E + 4 * h), pr);
+          if (!first) tmem_ld8(t_lane + colA + 2 * (q * E + 4 * h), ac);
+          float2 o[4];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) o[jj] = On[(size_t)ln * a.obj_w + tp[q] + G * (4 * h + jj)];
+          tmem_wait_ld();
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * h + jj;
+            const int x = tp[q] + G * j;
+            float2 psi_new = cscale(v[q][j], inv_m2);
+            if (!NEAR && ((ln + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
+            const float2 p = make_float2(pr[2 * jj], pr[2 * jj + 1]);
+            const float2 dpsi = csub(psi_new, cmul(p, o[jj]));
+            st_cluster_f2(dst + 8u * x, cconjmul(p, dpsi));
+            const float2 pc = cconjmul(o[jj], dpsi);
+            ac[2 * jj] = first ? pc.x : ac[2 * jj] + pc.x;
+            ac[2 * jj + 1] = first ? pc.y : ac[2 * jj + 1] + pc.y;
+            if (ln >= r0 && ln < r1) {
+              const int qi = ln * M + x;
+              dacc[qi] = first ? cabs2(o[jj]) : dacc[qi] + cabs2(o[jj]);
+            }
+          }
+          tmem_st8(t_lane + colA + 2 * (q * E + 4 * h), ac);
+        }
+        tmem_wait_st();
+      } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int x = tp[q] + G * j;
+          float2 psi_new = cscale(v[q][j], inv_m2);
+          if (!NEAR && ((ln + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
+          const float2 p = Pk[ln * M + x];
+          const float2 o = On[(size_t)ln * a.obj_w + x];
+          const float2 dpsi = csub(psi_new, cmul(p, o));
+          st_cluster_f2(dst + 8u * x, cconjmul(p, dpsi));
+          const int qi = ln * M + x;
+          const float2 pc = cconjmul(o, dpsi);
+          pacc[qi] = first ? pc : cadd(pacc[qi], pc);
+          if (ln >= r0 && ln < r1) dacc[qi] = first ? cabs2(o) : dacc[qi] + cabs2(o);
+        }
       }
     }
     cluster_sync_all();
+    // ---- (8) own rows of c_n: sum over the source ranks in order
+    {
+      float2* cn = a.cn + (size_t)n * M * M;
+      for (int p = tid; p < nrow * M; p += TR) {
+        const int lr = p / M, col = p % M;
+        float2 s = make_float2(0.f, 0.f);
+        for (int q = 0; q < K; ++q) s = cadd(s, recv[(q * RPO + lr) * LDN + col]);
+        cn[(size_t)(r0 + lr) * M + col] = s;
+      }
+    }
+    __syncthreads();  // the next position reuses the exchange buffer
   }
-  // ---- per-slot FP64 error numerator: the compensated FP32 thread sums, added in thread order
-  if (rank == 0) {
+  // ---- probe-numerator partial from TMEM to global, then release TMEM
+  if constexpr (TM) {
+#pragma unroll
+    for (int q = 0; q < V; ++q)
+#pragma unroll
+      for (int h = 0; h < E / 4; ++h) {
+        float ac[8];
+        tmem_ld8(t_lane + colA + 2 * (q * E + 4 * h), ac);
+        tmem_wait_ld();
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          pacc[line[q] * M + tp[q] + G * (4 * h + jj)] = make_float2(ac[2 * jj], ac[2 * jj + 1]);
+      }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (tid / 32 == 0) tmem_dealloc(*s_tmem, FusedShape<M>::TMEM_COLS);
+  }
+  // ---- per-CTA FP64 error numerator: the compensated FP32 thread sums, added in thread order
+  {
     double* red = reinterpret_cast<double*>(smem);
     red[tid] = (double)err_s - (double)err_c;
     __syncthreads();
@@ -335,27 +534,27 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
       if (tid < w) red[tid] += red[tid + w];
       __syncthreads();
     }
-    if (tid == 0) a.errpart[slot] = red[0];
+    if (tid == 0) a.errpart[(size_t)slot * K + rank] = red[0];
   }
 }
 
 size_t fused_smem_bytes(int M) {
   switch (M) {
-    case 8: return FusedSmem<8>::BYTES;
-    case 16: return FusedSmem<16>::BYTES;
-    case 32: return FusedSmem<32>::BYTES;
-    case 64: return FusedSmem<64>::BYTES;
-    case 128: return FusedSmem<128>::BYTES;
+    case 8: return FusedSmem<8, 15>::BYTES;
+    case 16: return FusedSmem<16, 15>::BYTES;
+    case 32: return FusedSmem<32, 15>::BYTES;
+    case 64: return FusedSmem<64, 15>::BYTES;
+    case 128: return FusedSmem<128, 15>::BYTES;
     default: return 0;
   }
 }
 
-template <int M>
+template <int M, int KH>
 static cudaLaunchConfig_t fused_config(const FusedArgs& a, int slots, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(slots * a.K));
   cfg.blockDim = dim3(FusedShape<M>::TR);
-  cfg.dynamicSmemBytes = FusedSmem<M>::BYTES;
+  cfg.dynamicSmemBytes = FusedSmem<M, KH>::BYTES;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)a.K;
@@ -369,10 +568,10 @@ static cudaLaunchConfig_t fused_config(const FusedArgs& a, int slots, cudaStream
 template <int M, bool NEAR, int KH>
 static cudaError_t launch_kh(const FusedArgs& a, int slots, cudaStream_t s) {
   auto kern = pc_fused_kernel<M, NEAR, KH>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M>::BYTES);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M, KH>::BYTES);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = fused_config<M>(a, slots, s, attr);
+  cudaLaunchConfig_t cfg = fused_config<M, KH>(a, slots, s, attr);
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
@@ -383,15 +582,16 @@ static cudaError_t launch_t(const FusedArgs& a, int slots, cudaStream_t s) {
   return a.kh == 5 ? launch_kh<M, NEAR, 5>(a, slots, s) : launch_kh<M, NEAR, 15>(a, slots, s);
 }
 
+// co-resident clusters, taken for the largest shared-memory variant (KH = 15)
 template <int M>
 static cudaError_t max_slots_t(int K, int* slots) {
-  auto kern = pc_fused_kernel<M, false, 5>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M>::BYTES);
+  auto kern = pc_fused_kernel<M, false, 15>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M, 15>::BYTES);
   if (e != cudaSuccess) return e;
   FusedArgs a = {};
   a.K = K;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = fused_config<M>(a, 1, 0, attr);
+  cudaLaunchConfig_t cfg = fused_config<M, 15>(a, 1, 0, attr);
   int n = 0;
   e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
   *slots = n;

@@ -247,7 +247,7 @@ __global__ void k_probe_apply(const UpdateArgs u) {
   const float maxd = block_max_of(u.blk_max_p, u.probe_blocks);
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     double e = 0.0;
-    for (int s = 0; s < u.slots; ++s) e += u.errpart[s];
+    for (int s = 0; s < u.nerr; ++s) e += u.errpart[s];
     u.errhist[u.hist_index] = sqrt(e / u.errden);
   }
   if (!u.update_probe) return;

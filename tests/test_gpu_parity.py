@@ -98,7 +98,8 @@ def test_near_field_eight_modes_m128():
     check(p, dict(p.params, sigma1=1.5, sigma2=1.5, blur_domain="intensity"), 3)
 
 
-@pytest.mark.parametrize("M,K,ks,sig", [(8, 2, 11, 1.0), (16, 1, 1, 0.0), (32, 1, 11, 0.0), (64, 4, 31, 3.0)])
+@pytest.mark.parametrize("M,K,ks,sig", [(8, 2, 11, 1.0), (8, 7, 11, 1.0), (16, 1, 1, 0.0), (16, 5, 13, 1.3),
+                                        (32, 1, 11, 0.0), (64, 4, 31, 3.0), (64, 3, 11, 2.0)])
 def test_probe_sizes_and_kernels(M, K, ks, sig):
     p = make_problem(0, scan_side=4, obj_side=M * 3, M=M, K=K, sigma=max(sig, 0.5))
     check(p, dict(p.params, kernel_size=ks, sigma1=sig, sigma2=sig), 4)
