@@ -133,6 +133,31 @@ ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t*
  * constraint kernels when `in_window` is non-zero). */
 int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
 
+/* Allocation-free one-shot run (this entry point has no counterpart in the paper).
+ * For callers that must not call cudaMalloc -- e.g. code running while a
+ * device memory pool or budget is locked, latency-critical loops that cannot
+ * afford an allocation's implicit synchronisation, or hosts that own all
+ * device memory -- it runs n_iter iterations exactly like ptycho_plan +
+ * ptycho_iterate, but takes every scratch buffer from one file-scope device
+ * array of 32 MiB that the library holds on each device until the process
+ * exits. It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   p, intensities, positions  as for ptycho_plan (intensities: device)
+ *   object, probe              device, updated in place as by ptycho_iterate
+ *   n_iter                     0..4096
+ *   errors                     host, n_iter doubles (E of each iteration), or NULL
+ *   cuda_stream                stream to run on (NULL: the legacy default stream)
+ * The scratch needed is about N M^2 (4 + 8) bytes + slots K M^2 8 bytes
+ * + 8 obj_h obj_w 12 bytes + small tables; a request larger than 32 MiB is
+ * rejected with PTYCHO_EINVAL and a message giving the bytes it needs.
+ * The call synchronises the stream before returning. The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. Every call shares the one
+ * scratch array and overwrites it (nothing in it has to start at zero), so
+ * calls that overlap on the GPU -- from several host threads or streams --
+ * race and must be serialised by the caller. */
+ptycho_status ptycho_iterate_static(const ptycho_params* p, const float* intensities, const int32_t* positions,
+                                    void* object, void* probe, int32_t n_iter, double* errors, void* cuda_stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ptycho_last_error(void);
 

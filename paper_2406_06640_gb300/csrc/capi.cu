@@ -460,3 +460,13 @@ const char* ptycho_last_error(void) { return g_last_error.c_str(); }
 const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---- helpers shared with the allocation-free entry point (capi_static.cu)
+namespace ptycho {
+ptycho_status capi_validate(const ptycho_params* p) { return validate(p); }
+ptycho_status capi_fail(ptycho_status s, const std::string& msg) { return fail(s, msg); }
+ptycho_status capi_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+std::vector<double> capi_taps(double sigma, int h) { return taps_1d(sigma, h); }
+bool capi_is_device_pointer(const void* ptr) { return is_device_pointer(ptr); }
+void capi_clear_error() { g_last_error.clear(); }
+}  // namespace ptycho
