@@ -129,8 +129,8 @@ ptycho_status ptycho_destroy(ptycho_plan_t plan);
 ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
 ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
 
-/* Kernel launches one iteration issues (fused + update, plus the complex
- * constraint kernels when `in_window` is non-zero). */
+/* Kernel launches one iteration issues: 6 (fused + update) plus 6 complex-
+ * constraint kernels when `in_window` is non-zero (memsets not counted). */
 int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
 
 /* Allocation-free one-shot run (this entry point has no counterpart in the paper).
@@ -147,7 +147,7 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
  *   errors                     host, n_iter doubles (E of each iteration), or NULL
  *   cuda_stream                stream to run on (NULL: the legacy default stream)
  * The scratch needed is about N M^2 (4 + 8) bytes + slots K M^2 8 bytes
- * + 8 obj_h obj_w 12 bytes + small tables; a request larger than 32 MiB is
+ * + obj_h obj_w (8 x 12 + 28) bytes + small tables; a request larger than 32 MiB is
  * rejected with PTYCHO_EINVAL and a message giving the bytes it needs.
  * The call synchronises the stream before returning. The first call on a
  * device looks up the scratch's device address (cudaGetSymbolAddress); make

@@ -228,17 +228,19 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
     for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
       for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
   }
-  std::vector<int> start((size_t)tx * ty + 1, 0), flat;
+  std::vector<int> start((size_t)tx * ty + 1, 0);
+  std::vector<int4> flat;
   for (size_t i = 0; i < lists.size(); ++i) {
     start[i + 1] = start[i] + (int)lists[i].size();
-    flat.insert(flat.end(), lists[i].begin(), lists[i].end());
+    for (int n : lists[i]) flat.push_back(make_int4(n, pl->h_pos[n].x, pl->h_pos[n].y, 0));
   }
-  int *d_start, *d_list;
+  int* d_start;
+  int4* d_list;
   PT_CUDA(pl->alloc(&d_start, start.size()), "alloc tile lists");
   PT_CUDA(pl->alloc(&d_list, flat.size()), "alloc tile lists");
-  PT_CUDA(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, s), "copy tiles");
+  PT_CUDA(cudaMemcpy(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice), "copy tiles");
   if (!flat.empty())
-    PT_CUDA(cudaMemcpyAsync(d_list, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, s), "copy tiles");
+    PT_CUDA(cudaMemcpy(d_list, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice), "copy tiles");
 
   const size_t plane = (size_t)p.obj_h * p.obj_w;
   float2* d_no;
@@ -254,6 +256,16 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_p2, MM), "alloc probe sums");
   PT_CUDA(pl->alloc(&d_bmp, (size_t)pb), "alloc probe maxima");
   PT_CUDA(pl->alloc(&d_cbar, (size_t)N), "alloc cbar");
+  long long *d_lna, *d_phi, *d_diff;
+  int* d_cover;
+  PT_CUDA(pl->alloc(&d_lna, (size_t)(p.obj_h + 1) * (p.obj_w + 1)), "alloc constraint tables");
+  PT_CUDA(pl->alloc(&d_phi, (size_t)(p.obj_h + 1) * (p.obj_w + 1)), "alloc constraint tables");
+  PT_CUDA(pl->alloc(&d_diff, (size_t)(p.obj_h + 1) * (p.obj_w + 1)), "alloc constraint sums");
+  PT_CUDA(pl->alloc(&d_cover, plane), "alloc coverage");
+  {
+    const std::vector<int> cover = coverage_counts(pl->h_pos, M, p.obj_h, p.obj_w);
+    PT_CUDA(cudaMemcpy(d_cover, cover.data(), sizeof(int) * plane, cudaMemcpyHostToDevice), "copy coverage");
+  }
   PT_CUDA(pl->alloc(&pl->d_errhist, (size_t)kErrHistory), "alloc error history");
 
   // ---- kernel argument blocks
@@ -313,11 +325,11 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ca.M = M;
   ca.obj_h = p.obj_h;
   ca.obj_w = p.obj_w;
-  ca.tile_start = d_start;
-  ca.tile_pos = d_list;
-  ca.tiles_x = tx;
-  ca.tiles_y = ty;
   ca.cbar = d_cbar;
+  ca.sat_lna = d_lna;
+  ca.sat_phi = d_phi;
+  ca.diff = d_diff;
+  ca.cover = d_cover;
   ca.alpha1 = (float)p.alpha1;
   ca.alpha2 = (float)p.alpha2;
   ca.cbar_min = (float)p.cbar_min;
@@ -452,7 +464,7 @@ ptycho_status ptycho_profile_read(ptycho_plan_t pl, double* fused_ms, int32_t* l
 
 int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
   (void)pl;
-  return 6 + (in_window ? 2 : 0);
+  return 6 + (in_window ? 6 : 0);
 }
 
 const char* ptycho_last_error(void) { return g_last_error.c_str(); }
@@ -463,6 +475,25 @@ const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }
 
 // ---- helpers shared with the allocation-free entry point (capi_static.cu)
 namespace ptycho {
+std::vector<int> coverage_counts(const std::vector<int2>& pos, int M, int obj_h, int obj_w) {
+  // 2-D difference array of the boxes, then prefix sums along both axes
+  std::vector<int> d((size_t)(obj_h + 1) * (obj_w + 1), 0);
+  const int W1 = obj_w + 1;
+  for (const int2& q : pos) {
+    d[(size_t)q.x * W1 + q.y] += 1;
+    d[(size_t)q.x * W1 + q.y + M] -= 1;
+    d[(size_t)(q.x + M) * W1 + q.y] -= 1;
+    d[(size_t)(q.x + M) * W1 + q.y + M] += 1;
+  }
+  for (int y = 0; y <= obj_h; ++y)
+    for (int x = 1; x <= obj_w; ++x) d[(size_t)y * W1 + x] += d[(size_t)y * W1 + x - 1];
+  for (int y = 1; y <= obj_h; ++y)
+    for (int x = 0; x <= obj_w; ++x) d[(size_t)y * W1 + x] += d[(size_t)(y - 1) * W1 + x];
+  std::vector<int> out((size_t)obj_h * obj_w);
+  for (int y = 0; y < obj_h; ++y)
+    for (int x = 0; x < obj_w; ++x) out[(size_t)y * obj_w + x] = d[(size_t)y * W1 + x];
+  return out;
+}
 ptycho_status capi_validate(const ptycho_params* p) { return validate(p); }
 ptycho_status capi_fail(ptycho_status s, const std::string& msg) { return fail(s, msg); }
 ptycho_status capi_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }

@@ -114,10 +114,11 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     for (int by = hpos[n].x / kObjTile; by <= (hpos[n].x + M - 1) / kObjTile; ++by)
       for (int bx = hpos[n].y / kObjTile; bx <= (hpos[n].y + M - 1) / kObjTile; ++bx)
         lists[(size_t)by * tx + bx].push_back(n);
-  std::vector<int> start((size_t)tx * ty + 1, 0), flat;
+  std::vector<int> start((size_t)tx * ty + 1, 0);
+  std::vector<int4> flat;
   for (size_t i = 0; i < lists.size(); ++i) {
     start[i + 1] = start[i] + (int)lists[i].size();
-    flat.insert(flat.end(), lists[i].begin(), lists[i].end());
+    for (int n : lists[i]) flat.push_back(make_int4(n, hpos[n].x, hpos[n].y, 0));
   }
   const size_t count = (size_t)N * MM;
   const int nb = (int)std::min<size_t>(1024, (count + 255) / 256);
@@ -139,7 +140,7 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     fa.dacc = cv.take<float>((size_t)slots * MM);
     fa.errpart = cv.take<double>((size_t)slots * K);
     ua.tile_start = cv.take<int>(start.size());
-    ua.tile_pos = cv.take<int>(flat.size());
+    ua.tile_pos = cv.take<int4>(flat.size());
     ua.no_part = cv.take<float2>((size_t)kObjSplit * plane);
     ua.do_part = cv.take<float>((size_t)kObjSplit * plane);
     ua.blk_max_o = cv.take<float>((size_t)tx * ty);
@@ -149,6 +150,10 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     ua.blk_max_p = cv.take<float>((size_t)pb);
     ua.errhist = cv.take<double>((size_t)kErrHistory);
     ca.cbar = cv.take<float>((size_t)N);
+    ca.sat_lna = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
+    ca.sat_phi = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
+    ca.diff = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
+    ca.cover = cv.take<int>(plane);
   };
   FusedArgs fa{};
   UpdateArgs ua{};
@@ -175,8 +180,13 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   PS_CUDA(cudaMemcpyAsync(const_cast<int*>(ua.tile_start), start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, s),
           "copy tile lists");
   if (!flat.empty())
-    PS_CUDA(cudaMemcpyAsync(const_cast<int*>(ua.tile_pos), flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, s),
+    PS_CUDA(cudaMemcpyAsync(const_cast<int4*>(ua.tile_pos), flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice, s),
             "copy tile lists");
+  {
+    const std::vector<int> cover = coverage_counts(hpos, M, p->obj_h, p->obj_w);
+    PS_CUDA(cudaMemcpyAsync(const_cast<int*>(ca.cover), cover.data(), sizeof(int) * plane, cudaMemcpyHostToDevice, s),
+            "copy coverage");
+  }
   std::vector<float2> tw(M), hq(M);
   for (int m = 0; m < M; ++m) {
     const double a = -2.0 * M_PI * m / M;
@@ -245,10 +255,6 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   ca.M = M;
   ca.obj_h = p->obj_h;
   ca.obj_w = p->obj_w;
-  ca.tile_start = ua.tile_start;
-  ca.tile_pos = ua.tile_pos;
-  ca.tiles_x = tx;
-  ca.tiles_y = ty;
   ca.alpha1 = (float)p->alpha1;
   ca.alpha2 = (float)p->alpha2;
   ca.cbar_min = (float)p->cbar_min;

@@ -49,7 +49,7 @@ struct UpdateArgs {
   int nerr;  // entries of errpart
   // object gather
   const int* tile_start;  // (tiles_y * tiles_x + 1) CSR offsets into tile_pos
-  const int* tile_pos;    // position indices per tile, increasing
+  const int4* tile_pos;   // per tile, (n, row, col, 0) of each overlapping position, increasing n
   int tiles_x, tiles_y;
   float2* no_part; float* do_part;  // kObjSplit x obj_h x obj_w partials
   float* blk_max_o;                  // per object tile
@@ -66,9 +66,14 @@ cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);
 // complex constraint (constraint.cu)
 struct ConstraintArgs {
   float2* O; const int2* pos; int N, M, obj_h, obj_w;
-  const int* tile_start; const int* tile_pos; int tiles_x, tiles_y;
   float* cbar; float alpha1, alpha2, cbar_min, cbar_max;
+  long long* sat_lna; long long* sat_phi;  // summed-area tables of |ln a| and |phi|, 32.32 fixed point
+  long long* diff;                 // (obj_h + 1) x (obj_w + 1) difference array, 32.32 fixed point
+  const int* cover;                // boxes covering each object pixel (fixed per plan)
 };
+
+// boxes covering each object pixel, obj_h x obj_w (host helper, plan time)
+std::vector<int> coverage_counts(const std::vector<int2>& pos, int M, int obj_h, int obj_w);
 cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s);
 
 // plan-time helpers (update.cu)

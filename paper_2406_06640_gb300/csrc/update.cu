@@ -141,14 +141,13 @@ __global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
   }
   const int s0 = u.tile_start[tile], s1 = u.tile_start[tile + 1];
   for (int idx = s0 + split; idx < s1; idx += kObjSplit) {
-    const int n = u.tile_pos[idx];
-    const int2 pn = u.pos[n];
-    const int cx = X - pn.y;
+    const int4 ent = u.tile_pos[idx];  // (n, row, col)
+    const int cx = X - ent.z;
     if (cx < 0 || cx >= M) continue;
-    const float2* cn = u.cn + (size_t)n * MM;
+    const float2* cn = u.cn + (size_t)ent.x * MM;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int cy = Y0 + 8 * i - pn.x;
+      const int cy = Y0 + 8 * i - ent.y;
       if (cy >= 0 && cy < M) {
         acc[i] = cadd(acc[i], cn[(size_t)cy * M + cx]);
         den[i] += u.p2[cy * M + cx];
