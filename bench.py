@@ -49,21 +49,33 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="far128x4",
+                    help="far128x4: the benchmark workload; near256x8 and far64x1 for reference runs")
     return ap.parse_args()
+
+
+WORKLOADS = {
+    "far128x4": (1, "far-field 4-mode pc-engine iteration (probe 128^2, K=4, N=900 Fermat spiral, "
+                    "object 640^2, 5% bandwidth, sigma 1.5, 1e6 photons)"),
+    "near256x8": (2, "near-field 8-mode pc-engine iteration (Fresnel F=10, probe 256^2, K=8, N=256 raster, "
+                     "object 1024^2, sigma 2, 1e5 photons)"),
+    "far64x1": (0, "far-field single-mode pc-engine iteration (probe 64^2, N=100 raster, object 192^2, "
+                   "sigma 1, 1e5 photons)"),
+}
+_WORKLOAD = "far128x4"
 
 
 def workload():
     from synth import make_problem
 
-    prob = make_problem(1)
+    prob = make_problem(WORKLOADS[_WORKLOAD][0])
     params = dict(prob.params, windows=[(1, 1 << 30)])  # complex constraint in every step
     return prob, params
 
 
 def config_of(prob, extra=None):
     p = prob.params
-    cfg = {"workload": "far-field 4-mode pc-engine iteration (probe 128^2, K=4, N=900 Fermat spiral, "
-                       "object 640^2, 5% bandwidth, sigma 1.5, 1e6 photons)",
+    cfg = {"workload": WORKLOADS[_WORKLOAD][1],
            "M": p["M"], "K": p["K"], "N": p["N"], "object": [p["obj_h"], p["obj_w"]], "geometry": p["geometry"],
            "blur": p["blur_domain"], "kernel_size": p["kernel_size"], "complex_constraint": "every step",
            "step": "one iteration over all positions", "l2": "flushed before each timed step (256 MiB write)"}
@@ -274,7 +286,7 @@ def run_ours(args):
     fused_avg_s = fused_ms / max(fused_launches, 1) / 1e3
     achieved = flops / fused_avg_s / 1e12
     peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = traffic_record(kernel_source_hash())
+    traffic = traffic_record(kernel_source_hash()) if _WORKLOAD == "far128x4" else None
 
     # end to end through the public API: object + probe state from pinned host memory, one
     # iteration, error metric and state back to pinned host memory, every step
@@ -312,7 +324,7 @@ def run_ours(args):
                 "config": config_of(prob, {"parallelism": f"replicas{ws}" if ws > 1 else "single GPU"}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "kernel": "pc_fused_kernel<128, far>",
+                             "kernel": "pc_fused_kernel<128, far>" if prob.M <= 128 else "staged passes (M=256)",
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FMA pipe, max clock)",
                              "flops_per_launch": flops, "avg_launch_ms": fused_avg_s * 1e3},
                 "cpu_baseline": cpu,
@@ -330,7 +342,9 @@ def run_ours(args):
 
 
 def main():
+    global _WORKLOAD
     args = parse()
+    _WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -66,7 +66,7 @@ enum { PTYCHO_FARFIELD = 0, PTYCHO_NEARFIELD = 1 };
 enum { PTYCHO_BLUR_AMPLITUDE = 0 /* Eq. 6 */, PTYCHO_BLUR_INTENSITY = 1 /* Eq. 2 */ };
 
 typedef struct {
-  int32_t M;            /* probe = box = detector side, power of two, 8..128 */
+  int32_t M;            /* probe = box = detector side, power of two, 8..256 */
   int32_t K;            /* probe modes (mixed state, Sec. 4.4), 1..8 */
   int32_t N;            /* scan positions, >= 1 */
   int32_t obj_h, obj_w; /* object size, >= M */
@@ -122,15 +122,18 @@ ptycho_status ptycho_destroy(ptycho_plan_t plan);
 
 /* Per-kernel timing for roofline reports. While enabled, ptycho_iterate records
  * a CUDA event pair on the plan's stream around every launch of the fused
- * per-position kernel (the dominant kernel of an iteration).
+ * per-position kernel (the dominant kernel of an iteration); for M = 256 the
+ * pair brackets the staged FFT / modulus passes of the iteration.
  * ptycho_profile_read synchronises the stream, returns the summed device time
  * of those launches in milliseconds and their count, and resets both. At most
  * 1024 launches are kept between reads (older ones are dropped from the sum). */
 ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
 ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
 
-/* Kernel launches one iteration issues: 6 (fused + update) plus 6 complex-
- * constraint kernels when `in_window` is non-zero (memsets not counted). */
+/* Kernel launches one iteration issues: the fused kernel (M <= 128) or 5 (far)
+ * / 7 (near) staged passes per chunk of 16 positions (M = 256), 5 update
+ * kernels, and 6 complex-constraint kernels when `in_window` is non-zero
+ * (memsets not counted). */
 int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
 
 /* Allocation-free one-shot run (this entry point has no counterpart in the paper).
@@ -143,7 +146,7 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
  * exits. It calls no cudaMalloc, cudaFree or other allocating routine.
  *   p, intensities, positions  as for ptycho_plan (intensities: device)
  *   object, probe              device, updated in place as by ptycho_iterate
- *   n_iter                     0..4096
+ *   n_iter                     0..4096 (M <= 128; larger M gives PTYCHO_EUNSUPPORTED)
  *   errors                     host, n_iter doubles (E of each iteration), or NULL
  *   cuda_stream                stream to run on (NULL: the legacy default stream)
  * The scratch needed is about N M^2 (4 + 8) bytes + slots K M^2 8 bytes

@@ -1,0 +1,343 @@
+// Staged path for probe sizes whose M x M complex tile exceeds one SM's
+// shared memory (M = 256). Same iteration as the fused kernel (Eqs. 1, 2, 6, 7,
+// Fig. 1 box 1), split into passes over an L2-sized scratch W that holds a
+// chunk of C positions x K modes:
+//
+//   far field:  rows(exit wave, DFT) -> cols(DFT) -> modulus -> cols(IDFT)
+//               -> rows(IDFT, dpsi, contributions)
+//   near field: rows(exit wave, DFT) -> cols(DFT, x H, IDFT) -> rows(IDFT)
+//               -> modulus -> rows(DFT) -> cols(DFT, x conj H, IDFT)
+//               -> rows(IDFT, dpsi, contributions)
+//
+// A length-256 line is transformed by 16 threads: a radix-16 pass in
+// registers over x = t + 16 j, the twiddle W_256^(t k2), a warp-local swap in
+// shared memory, and a second radix-16 pass; thread t then holds frequencies
+// t + 16 k1. The inverse consumes that layout and returns x = t + 16 j.
+// All sums that cross CTAs are written to per-(slot, mode) or per-(position,
+// row-block) partials and added in a fixed order, as on the fused path.
+#include <cuda_runtime.h>
+
+#include "engine.h"
+#include "fft.cuh"
+
+namespace ptycho {
+
+namespace {
+
+constexpr int BL = 256;       // line length handled here
+constexpr int BT = 16;        // threads per line
+constexpr int BS = BT + 1;    // padded stride of the line-internal swap
+constexpr int LINES = 32;     // columns per CTA in the column passes (512 threads)
+constexpr int LROW = 16;      // lines per CTA in the row passes (256 threads)
+constexpr int RB = 16;        // rows per modulus block
+
+// forward: thread t holds x[t + 16 j] in a[j]; returns X[t + 16 k1] in a[k1] (unscaled)
+template <bool INV>
+__device__ __forceinline__ void line_fft(float2 (&a)[16], float2* sw, const float2* tw, int t) {
+  if constexpr (!INV) {
+    dft<16, false>(a);  // a[k2] = Y[t][k2]
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[t * BS + k2]);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) sw[k2 * BS + t] = a[k2];
+    __syncwarp();
+#pragma unroll
+    for (int tt = 0; tt < 16; ++tt) a[tt] = sw[t * BS + tt];  // Y[tt][k2 = t]
+    __syncwarp();
+    dft<16, false>(a);  // a[k1] = X[t + 16 k1]
+  } else {
+    dft<16, true>(a);  // a[tt] = Y[tt][k2 = t]
+#pragma unroll
+    for (int tt = 0; tt < 16; ++tt) sw[t * BS + tt] = a[tt];
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) a[k2] = sw[k2 * BS + t];  // Y[t][k2]
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmulc(a[k2], tw[t * BS + k2]);
+    dft<16, true>(a);  // a[j] = x[t + 16 j] * 256
+  }
+}
+
+__device__ __forceinline__ void load_tw(float2* s_tw, const float2* tw) {
+  for (int i = threadIdx.x; i < BT * BS; i += blockDim.x) {
+    const int t = i / BS, k2 = i % BS;
+    s_tw[i] = k2 < 16 ? tw[(t * k2) % BL] : make_float2(0.f, 0.f);
+  }
+}
+
+}  // namespace
+
+// ---- row passes. mode 0: exit wave + forward DFT; 1: forward DFT in place; 2: inverse DFT in place, / M^2
+template <int MODE, bool NEAR>
+__global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
+  __shared__ float2 s_tw[BT * BS];
+  __shared__ float2 s_sw[LROW][BT * BS];
+  load_tw(s_tw, b.tw);
+  __syncthreads();
+  const int li = threadIdx.x / BT, t = threadIdx.x % BT;
+  const int y = blockIdx.x * LROW + li;
+  const int k = blockIdx.y, c = blockIdx.z;
+  const int n = b.n0 + c;
+  const size_t MM = (size_t)BL * BL;
+  float2* row = b.W + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
+  float2 a[16];
+  if constexpr (MODE == 0) {
+    const int2 pn = b.pos[n];
+    const float2* Pk = b.P + (size_t)k * MM + (size_t)y * BL;
+    const float2* On = b.O + (size_t)(pn.x + y) * b.obj_w + pn.y;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int x = t + 16 * j;
+      float2 psi = cmul(Pk[x], On[x]);
+      if (!NEAR && ((y + x) & 1)) psi = make_float2(-psi.x, -psi.y);
+      a[j] = psi;
+    }
+  } else if constexpr (MODE == 1) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];  // X[t + 16 k1]
+  }
+  if constexpr (MODE == 2) {
+    line_fft<true>(a, s_sw[li], s_tw, t);
+    const float s = 1.0f / (float)(BL * BL);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) row[t + 16 * j] = cscale(a[j], s);
+  } else {
+    line_fft<false>(a, s_sw[li], s_tw, t);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) row[t + 16 * k1] = a[k1];
+  }
+}
+
+// ---- column passes on a 256 x 32 tile staged through shared memory.
+// op 0: forward DFT; 1: inverse DFT; 2: DFT, x H, IDFT (near forward); 3: DFT, x conj H, IDFT (near backward)
+template <int OP>
+__global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
+  constexpr int TP = LINES + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [BL][TP]
+  float2* s_tw = tile + BL * TP;
+  float2* s_sw = s_tw + BT * BS;  // [LINES][BT * BS]
+  float2* s_h = s_sw + LINES * BT * BS;
+  load_tw(s_tw, b.tw);
+  if constexpr (OP >= 2)
+    for (int i = threadIdx.x; i < BL; i += blockDim.x) s_h[i] = b.hq[i];
+  const int x0 = blockIdx.x * LINES, k = blockIdx.y, c = blockIdx.z;
+  const size_t MM = (size_t)BL * BL;
+  float2* Wk = b.W + ((size_t)c * b.K + k) * MM;
+  // coalesced tile load: 32 consecutive columns per row
+  for (int i = threadIdx.x; i < BL * LINES; i += blockDim.x) {
+    const int yy = i / LINES, xx = i % LINES;
+    tile[yy * TP + xx] = Wk[(size_t)yy * BL + x0 + xx];
+  }
+  __syncthreads();
+  const int cl = threadIdx.x / BT, t = threadIdx.x % BT;
+  float2* sw = s_sw + cl * BT * BS;
+  float2 a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = tile[(t + 16 * j) * TP + cl];
+  if constexpr (OP == 1) {
+    line_fft<true>(a, sw, s_tw, t);
+  } else {
+    line_fft<false>(a, sw, s_tw, t);  // a[k1] = column spectrum at u = t + 16 k1
+    if constexpr (OP >= 2) {
+      const float2 hv = s_h[x0 + cl];  // H(u, v) = h[u] h[v], v = this column's frequency
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) {
+        const float2 hh = cmul(s_h[t + 16 * k1], hv);
+        a[k1] = OP == 2 ? cmul(a[k1], hh) : cmulc(a[k1], hh);
+      }
+      line_fft<true>(a, sw, s_tw, t);
+    }
+  }
+  __syncthreads();
+  if constexpr (OP == 0) {
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) tile[(t + 16 * k1) * TP + cl] = a[k1];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) tile[(t + 16 * j) * TP + cl] = a[j];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < BL * LINES; i += blockDim.x) {
+    const int yy = i / LINES, xx = i % LINES;
+    Wk[(size_t)yy * BL + x0 + xx] = tile[yy * TP + xx];
+  }
+}
+
+// ---- modulus: rows [y0, y0 + RB) of one position, with KH halo rows for the y blur
+template <int KH>
+__global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
+  constexpr int HR = RB + 2 * KH;  // rows held
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sA = reinterpret_cast<float*>(smem_raw);  // HR x BL
+  float* sB = sA + HR * BL;                          // HR x BL
+  __shared__ float s_gx[2 * KH + 1], s_gy[2 * KH + 1];
+  __shared__ double s_red[256];
+  for (int i = threadIdx.x; i < 2 * KH + 1; i += blockDim.x) {
+    const int d = i - KH;
+    const bool in = d >= -b.kh && d <= b.kh;
+    s_gx[i] = in ? b.gx[d + b.kh] : 0.f;
+    s_gy[i] = in ? b.gy[d + b.kh] : 0.f;
+  }
+  const int y0 = blockIdx.x * RB, c = blockIdx.y;
+  const int n = b.n0 + c;
+  const size_t MM = (size_t)BL * BL;
+  const float2* Wc = b.W + (size_t)c * b.K * MM;
+  // mode sum (rank order k = 0..K-1), amplitude or intensity
+  for (int i = threadIdx.x; i < HR * BL; i += blockDim.x) {
+    const int yy = y0 - KH + i / BL, x = i % BL;
+    float s = 0.f;
+    if (yy >= 0 && yy < BL)
+      for (int k = 0; k < b.K; ++k) s += cabs2(Wc[(size_t)k * MM + (size_t)yy * BL + x]);
+    sA[i] = b.blur_intensity ? s : sqrtf(s);
+  }
+  __syncthreads();
+  // blur along x (columns, sigma_1), zero padded
+  for (int i = threadIdx.x; i < HR * BL; i += blockDim.x) {
+    const int r = i / BL, x = i % BL;
+    float acc = 0.f;
+#pragma unroll
+    for (int d = -KH; d <= KH; ++d) {
+      const int xx = x + d;
+      if (xx >= 0 && xx < BL) acc = fmaf(s_gx[d + KH], sA[r * BL + xx], acc);
+    }
+    sB[i] = acc;
+  }
+  __syncthreads();
+  // blur along y (rows, sigma_2) for the own rows, ratio, error; Psi' = R Psi for every mode
+  const float eps = b.eps;
+  float es = 0.f, ec = 0.f;
+  const float* In = b.I + (size_t)n * MM;
+  const float* Sn = b.sqrtI + (size_t)n * MM;
+  for (int i = threadIdx.x; i < RB * BL; i += blockDim.x) {
+    const int r = i / BL, x = i % BL, y = y0 + r;
+    float acc = 0.f;
+#pragma unroll
+    for (int d = -KH; d <= KH; ++d) acc = fmaf(s_gy[d + KH], sB[(r + KH + d) * BL + x], acc);
+    const float sq = Sn[(size_t)y * BL + x];
+    float ihat, R;
+    if (b.blur_intensity) {
+      ihat = acc;
+      R = sq * rsqrtf(acc + eps * eps);
+    } else {
+      ihat = acc * acc;
+      R = __fdividef(sq, acc + eps);
+    }
+    const float dd = ihat - In[(size_t)y * BL + x];
+    const float yv = fmaf(dd, dd, -ec);
+    const float tt = es + yv;
+    ec = (tt - es) - yv;
+    es = tt;
+    for (int k = 0; k < b.K; ++k) {
+      float2* w = b.W + ((size_t)c * b.K + k) * MM + (size_t)y * BL + x;
+      *w = cscale(*w, R);
+    }
+  }
+  s_red[threadIdx.x] = (double)es - (double)ec;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s_red[threadIdx.x] += s_red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) b.errpart[(size_t)n * (BL / RB) + blockIdx.x] = s_red[0];
+}
+
+// ---- final inverse row DFT of every mode, dpsi, contributions
+template <bool NEAR>
+__global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
+  __shared__ float2 s_tw[BT * BS];
+  __shared__ float2 s_sw[LROW][BT * BS];
+  load_tw(s_tw, b.tw);
+  __syncthreads();
+  const int li = threadIdx.x / BT, t = threadIdx.x % BT;
+  const int y = blockIdx.x * LROW + li;
+  const int c = blockIdx.y;
+  const int n = b.n0 + c;
+  const bool first = b.n0 == 0;
+  const size_t MM = (size_t)BL * BL;
+  const int2 pn = b.pos[n];
+  const float2* On = b.O + (size_t)(pn.x + y) * b.obj_w + pn.y;
+  const float s = 1.0f / (float)(BL * BL);
+  float2 cacc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) cacc[j] = make_float2(0.f, 0.f);
+  for (int k = 0; k < b.K; ++k) {
+    const float2* row = b.W + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
+    float2 a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];
+    line_fft<true>(a, s_sw[li], s_tw, t);
+    const float2* Pk = b.P + (size_t)k * MM + (size_t)y * BL;
+    float2* pacc = b.pacc + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int x = t + 16 * j;
+      float2 psi_new = cscale(a[j], s);
+      if (!NEAR && ((y + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
+      const float2 p = Pk[x], o = On[x];
+      const float2 dpsi = csub(psi_new, cmul(p, o));
+      cacc[j] = cadd(cacc[j], cconjmul(p, dpsi));
+      const float2 pc = cconjmul(o, dpsi);
+      pacc[x] = first ? pc : cadd(pacc[x], pc);
+    }
+  }
+  float2* cn = b.cn + (size_t)n * MM + (size_t)y * BL;
+  float* dacc = b.dacc + (size_t)c * MM + (size_t)y * BL;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int x = t + 16 * j;
+    cn[x] = cacc[j];
+    const float o2 = cabs2(On[x]);
+    dacc[x] = first ? o2 : dacc[x] + o2;
+  }
+}
+
+size_t big_cols_smem() {
+  return sizeof(float2) * ((size_t)BL * (LINES + 1) + BT * BS + (size_t)LINES * BT * BS + BL);
+}
+
+int big_row_blocks() { return BL / RB; }
+
+template <int KH>
+constexpr size_t big_mod_smem() { return sizeof(float) * 2 * (size_t)(RB + 2 * KH) * BL; }
+
+cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) {
+  const dim3 blk(LINES * BT), rblk(LROW * BT);
+  const dim3 grow(BL / LROW, b.K, nc), gcol(BL / LINES, b.K, nc), gfin(BL / LROW, nc), gmod(BL / RB, nc);
+  const size_t cs = big_cols_smem();
+  cudaError_t e;
+  for (auto kern : {k_big_cols<0>, k_big_cols<1>, k_big_cols<2>, k_big_cols<3>})
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs)) != cudaSuccess)
+      return e;
+  if ((e = cudaFuncSetAttribute(k_big_modulus<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)big_mod_smem<5>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_big_modulus<15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)big_mod_smem<15>())) != cudaSuccess)
+    return e;
+  if (b.near_field) {
+    k_big_rows<0, true><<<grow, rblk, 0, s>>>(b);
+    k_big_cols<2><<<gcol, blk, cs, s>>>(b);
+    k_big_rows<2, true><<<grow, rblk, 0, s>>>(b);
+  } else {
+    k_big_rows<0, false><<<grow, rblk, 0, s>>>(b);
+    k_big_cols<0><<<gcol, blk, cs, s>>>(b);
+  }
+  if (b.kh == 5) k_big_modulus<5><<<gmod, 256, big_mod_smem<5>(), s>>>(b);
+  else k_big_modulus<15><<<gmod, 256, big_mod_smem<15>(), s>>>(b);
+  if (b.near_field) {
+    k_big_rows<1, true><<<grow, rblk, 0, s>>>(b);
+    k_big_cols<3><<<gcol, blk, cs, s>>>(b);
+    k_big_final<true><<<gfin, rblk, 0, s>>>(b);
+  } else {
+    k_big_cols<1><<<gcol, blk, cs, s>>>(b);
+    k_big_final<false><<<gfin, rblk, 0, s>>>(b);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ptycho

@@ -67,6 +67,9 @@ struct ptycho_plan_s {
   FusedArgs fa{};
   UpdateArgs ua{};
   ConstraintArgs ca{};
+  BigArgs ba{};
+  bool big = false;  // M = 256: staged passes over a chunk of positions
+  int chunk = 0;
   double* d_errhist = nullptr;
   // profiling: event pairs around the fused kernel
   bool profiling = false;
@@ -96,7 +99,7 @@ struct ptycho_plan_s {
 static ptycho_status validate(const ptycho_params* p) {
   if (!p) return fail(PTYCHO_EINVAL, "params is NULL");
   if (!is_pow2(p->M) || p->M < 8 || p->M > 512) return fail(PTYCHO_EINVAL, "M must be a power of two in [8, 512]");
-  if (p->M > 128) return fail(PTYCHO_EUNSUPPORTED, "M > 128 is not handled by this build");
+  if (p->M > 256) return fail(PTYCHO_EUNSUPPORTED, "M > 256 is not handled by this build");
   if (p->K < 1) return fail(PTYCHO_EINVAL, "K must be >= 1");
   if (p->K > 8) return fail(PTYCHO_EUNSUPPORTED, "K > 8 probe modes is not handled by this build");
   if (p->N < 1) return fail(PTYCHO_EINVAL, "N must be >= 1");
@@ -155,11 +158,18 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   }
   if (!is_device_pointer(intensities)) return fail(PTYCHO_EINVAL, "intensities must be a device pointer");
 
-  // ---- slots (co-resident clusters of the fused kernel)
-  int max_slots = 0;
-  PT_CUDA(fused_max_slots(M, K, &max_slots), "occupancy of the fused kernel");
-  if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
-  pl->slots = std::min(max_slots, N);
+  // ---- slots: co-resident clusters of the fused kernel (M <= 128), or the position chunk of
+  // the staged path (M = 256), whose per-slot partials are summed in slot order
+  pl->big = M > 128;
+  if (pl->big) {
+    pl->chunk = std::min(N, 16);
+    pl->slots = pl->chunk;
+  } else {
+    int max_slots = 0;
+    PT_CUDA(fused_max_slots(M, K, &max_slots), "occupancy of the fused kernel");
+    if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
+    pl->slots = std::min(max_slots, N);
+  }
 
   // ---- buffers
   FusedArgs& fa = pl->fa;
@@ -218,7 +228,10 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_cn, (size_t)N * MM), "alloc contributions");
   PT_CUDA(pl->alloc(&d_pacc, (size_t)pl->slots * K * MM), "alloc probe partials");
   PT_CUDA(pl->alloc(&d_dacc, (size_t)pl->slots * MM), "alloc probe partials");
-  PT_CUDA(pl->alloc(&d_errpart, (size_t)pl->slots * K), "alloc error partials");
+  const size_t nerr = pl->big ? (size_t)N * big_row_blocks() : (size_t)pl->slots * K;
+  PT_CUDA(pl->alloc(&d_errpart, nerr), "alloc error partials");
+  float2* d_W = nullptr;
+  if (pl->big) PT_CUDA(pl->alloc(&d_W, (size_t)pl->chunk * K * MM), "alloc staged scratch");
 
   // object tiles and their position lists (increasing n)
   const int tx = (p.obj_w + kObjTile - 1) / kObjTile, ty = (p.obj_h + kObjTile - 1) / kObjTile;
@@ -300,7 +313,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ua.pacc = d_pacc;
   ua.dacc = d_dacc;
   ua.errpart = d_errpart;
-  ua.nerr = pl->slots * K;
+  ua.nerr = (int)nerr;
   ua.tile_start = d_start;
   ua.tile_pos = d_list;
   ua.tiles_x = tx;
@@ -334,6 +347,29 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ca.alpha2 = (float)p.alpha2;
   ca.cbar_min = (float)p.cbar_min;
   ca.cbar_max = (float)p.cbar_max;
+
+  BigArgs& ba = pl->ba;
+  ba.I = d_I;
+  ba.sqrtI = fa.sqrtI;
+  ba.pos = d_pos;
+  ba.N = N;
+  ba.K = K;
+  ba.obj_w = p.obj_w;
+  ba.near_field = fa.near_field;
+  ba.blur_intensity = fa.blur_intensity;
+  ba.kh = kh;
+  ba.eps = fa.eps;
+  for (int i = 0; i < kMaxTaps; ++i) {
+    ba.gx[i] = fa.gx[i];
+    ba.gy[i] = fa.gy[i];
+  }
+  ba.tw = d_tw;
+  ba.hq = d_hq;
+  ba.W = d_W;
+  ba.cn = d_cn;
+  ba.pacc = d_pacc;
+  ba.dacc = d_dacc;
+  ba.errpart = d_errpart;
 
   PT_CUDA(cudaStreamSynchronize(s), "plan sync");
   return PTYCHO_OK;
@@ -388,7 +424,17 @@ ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_
     const long long t = pl->iter;
     const int ps = pl->prof_count % ptycho_plan_s::kProfSlots;
     if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], pl->stream), "profile event");
-    PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, pl->stream), "fused kernel launch");
+    if (pl->big) {
+      BigArgs ba = pl->ba;
+      ba.O = static_cast<const float2*>(object);
+      ba.P = static_cast<const float2*>(probe);
+      for (int n0 = 0; n0 < pl->p.N; n0 += pl->chunk) {
+        ba.n0 = n0;
+        PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, pl->p.N - n0), pl->stream), "staged pass launch");
+      }
+    } else {
+      PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, pl->stream), "fused kernel launch");
+    }
     if (pl->profiling) {
       PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], pl->stream), "profile event");
       pl->prof_count++;
@@ -463,8 +509,13 @@ ptycho_status ptycho_profile_read(ptycho_plan_t pl, double* fused_ms, int32_t* l
 }
 
 int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
-  (void)pl;
-  return 6 + (in_window ? 6 : 0);
+  if (!pl) return 0;
+  int fft = 1;
+  if (pl->big) {
+    const int chunks = (pl->p.N + pl->chunk - 1) / pl->chunk;
+    fft = chunks * (pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5);
+  }
+  return fft + 5 + (in_window ? 6 : 0);
 }
 
 const char* ptycho_last_error(void) { return g_last_error.c_str(); }

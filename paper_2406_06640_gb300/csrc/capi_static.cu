@@ -89,6 +89,7 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   if (!intensities || !positions || !object || !probe) return capi_fail(PTYCHO_EINVAL, "NULL argument");
   if (n_iter < 0 || n_iter > kErrHistory) return capi_fail(PTYCHO_EINVAL, "n_iter must lie in [0, 4096]");
   if (!capi_is_device_pointer(intensities)) return capi_fail(PTYCHO_EINVAL, "intensities must be a device pointer");
+  if (p->M > 128) return capi_fail(PTYCHO_EUNSUPPORTED, "the static entry point handles M <= 128");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int M = p->M, K = p->K, N = p->N;
   const size_t MM = (size_t)M * M;

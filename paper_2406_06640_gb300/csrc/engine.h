@@ -40,6 +40,26 @@ cudaError_t launch_fused(int M, const FusedArgs& a, int slots, cudaStream_t s);
 cudaError_t fused_max_slots(int M, int K, int* slots);
 size_t fused_smem_bytes(int M);
 
+// staged path for M = 256 (big.cu): a chunk of C positions x K modes in the scratch W
+constexpr int kBigM = 256;
+struct BigArgs {
+  const float2* O; const float2* P; const float* I; const float* sqrtI; const int2* pos;
+  int N, K, obj_w;
+  int near_field, blur_intensity, kh;
+  float eps;
+  float gx[kMaxTaps], gy[kMaxTaps];
+  const float2* tw;   // W_M^m, m in [0, M)
+  const float2* hq;   // near field: h[u]
+  float2* W;          // C x K x M x M scratch
+  int n0;             // first position of the chunk
+  float2* cn;         // N x M x M contributions
+  float2* pacc;       // C x K x M x M probe partials (slot = position within the chunk)
+  float* dacc;        // C x M x M
+  double* errpart;    // N x (M / 16) error partials
+};
+cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s);
+int big_row_blocks();
+
 // update / reduction kernels (update.cu)
 struct UpdateArgs {
   float2* O; float2* P;

@@ -105,6 +105,27 @@ def test_probe_sizes_and_kernels(M, K, ks, sig):
     check(p, dict(p.params, kernel_size=ks, sigma1=sig, sigma2=sig), 4)
 
 
+@pytest.mark.parametrize("windows", [(), ((2, 2),)])
+def test_m256_near_field_two_modes(windows):
+    p = make_problem(0, scan_side=2, obj_side=320, M=256, K=2, geometry="near", sigma=2.0)
+    check(p, dict(p.params, sigma1=2.0, sigma2=1.5, windows=list(windows)), 3)
+
+
+def test_m256_far_field_two_chunks_wide_kernel():
+    """20 positions run as two chunks of the staged path; 31-tap kernel, intensity blur."""
+    p = make_problem(0, scan_side=5, obj_side=400, M=256, K=3, sigma=1.0)
+    p.positions = p.positions[:20].copy()
+    p.I = p.I[:20].copy()
+    prm = dict(p.params, N=20, kernel_size=31, sigma1=2.5, sigma2=0.8, blur_domain="intensity")
+    check(p, prm, 2)
+
+
+def test_config2_full_size_one_iteration():
+    """Full configuration 2 (near field F = 10, M = 256, K = 8, 256 positions, 1024^2 object)."""
+    p = make_problem(2)
+    check(p, p.params, 1)
+
+
 def test_single_position():
     p = make_problem(0, scan_side=1, obj_side=64, M=64)
     check(p, p.params, 3)
