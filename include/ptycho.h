@@ -120,6 +120,25 @@ ptycho_status ptycho_error_history(ptycho_plan_t plan, double* out, int32_t n, i
 /* Release every device resource of the plan (synchronises its stream). */
 ptycho_status ptycho_destroy(ptycho_plan_t plan);
 
+/* Batched reconstructions: B independent problems (each with its own sizes,
+ * geometry, blur and schedule), built once and iterated together. One
+ * iteration of every problem is captured into a CUDA graph whose branches run
+ * the problems concurrently on up to 8 streams; every later iteration with
+ * the same pattern of probe updates and constraint windows (and the same
+ * object / probe pointers) replays that graph with a single launch.
+ *   params, intensities, positions  arrays of B entries, as for ptycho_plan
+ *   cuda_stream  the caller's stream; each iteration waits for it and it
+ *                waits for the iteration (events), so ordering is preserved
+ * ptycho_plan_batch fails with the status of the first invalid problem and a
+ * message naming it. ptycho_iterate_batch takes B object and B probe device
+ * pointers (updated in place); ptycho_error_batch synchronises and writes the
+ * last E of every problem (host, B doubles). ptycho_destroy releases a batch
+ * plan and all its problems. Single-plan calls reject batch plans. */
+ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, const float* const* intensities,
+                                const int32_t* const* positions, void* cuda_stream, ptycho_plan_t* out);
+ptycho_status ptycho_iterate_batch(ptycho_plan_t plan, void* const* objects, void* const* probes, int32_t n_iter);
+ptycho_status ptycho_error_batch(ptycho_plan_t plan, double* nrmse_last);
+
 /* Per-kernel timing for roofline reports. While enabled, ptycho_iterate records
  * a CUDA event pair on the plan's stream around every launch of the fused
  * per-position kernel (the dominant kernel of an iteration); for M = 256 the
@@ -155,7 +174,8 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
  * The call synchronises the stream before returning. The first call on a
  * device looks up the scratch's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture. Every call shares the one
- * scratch array and overwrites it (nothing in it has to start at zero), so
+ * scratch array and overwrites it (the call clears the one counter in it that
+ * has to start at zero), so
  * calls that overlap on the GPU -- from several host threads or streams --
  * race and must be serialised by the caller. */
 ptycho_status ptycho_iterate_static(const ptycho_params* p, const float* intensities, const int32_t* positions,

@@ -20,6 +20,7 @@ FARFIELD, NEARFIELD = 0, 1
 BLUR_AMPLITUDE, BLUR_INTENSITY = 0, 1
 
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
+            "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
             "ptycho_version")
 
@@ -85,6 +86,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_profile_read.restype = st
     lib.ptycho_launches_per_iteration.argtypes = [P, ctypes.c_int32]
     lib.ptycho_launches_per_iteration.restype = ctypes.c_int32
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.ptycho_plan_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.POINTER(PtychoParams)), PP, PP, P,
+                                      ctypes.POINTER(P)]
+    lib.ptycho_plan_batch.restype = st
+    lib.ptycho_iterate_batch.argtypes = [P, PP, PP, ctypes.c_int32]
+    lib.ptycho_iterate_batch.restype = st
+    lib.ptycho_error_batch.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.ptycho_error_batch.restype = st
     lib.ptycho_last_error.argtypes = []
     lib.ptycho_last_error.restype = ctypes.c_char_p
     lib.ptycho_version.argtypes = []
@@ -182,6 +191,44 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchPlan:
+    """Several independent reconstructions iterated together (ptycho_plan_batch / ptycho_iterate_batch)."""
+
+    def __init__(self, params: Sequence[dict], intensities_ptrs: Sequence[int], positions_ptrs: Sequence[int],
+                 stream_ptr: int = 0):
+        lib = load()
+        self.B = len(params)
+        made = [make_params(p) for p in params]
+        self._keep = made
+        arr = (ctypes.POINTER(PtychoParams) * self.B)(*[ctypes.pointer(m[0]) for m in made])
+        ip = (ctypes.c_void_p * self.B)(*intensities_ptrs)
+        pp = (ctypes.c_void_p * self.B)(*positions_ptrs)
+        h = ctypes.c_void_p()
+        _check(lib.ptycho_plan_batch(self.B, arr, ip, pp, ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+        self._h = h
+
+    def iterate(self, object_ptrs: Sequence[int], probe_ptrs: Sequence[int], n_iter: int):
+        op = (ctypes.c_void_p * self.B)(*object_ptrs)
+        pp = (ctypes.c_void_p * self.B)(*probe_ptrs)
+        _check(load().ptycho_iterate_batch(self._h, op, pp, int(n_iter)))
+
+    def errors(self) -> list:
+        out = (ctypes.c_double * self.B)()
+        _check(load().ptycho_error_batch(self._h, out))
+        return list(out)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ptycho_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:

@@ -3,10 +3,10 @@
 // Fig. 1 box 1), split into passes over an L2-sized scratch W that holds a
 // chunk of C positions x K modes:
 //
-//   far field:  rows(exit wave, DFT) -> cols(DFT) -> modulus -> cols(IDFT)
+//   far field:  rows(exit wave, DFT) -> cols(DFT) -> modulus (R) -> cols(R x, IDFT)
 //               -> rows(IDFT, dpsi, contributions)
 //   near field: rows(exit wave, DFT) -> cols(DFT, x H, IDFT) -> rows(IDFT)
-//               -> modulus -> rows(DFT) -> cols(DFT, x conj H, IDFT)
+//               -> modulus (R) -> rows(R x, DFT) -> cols(DFT, x conj H, IDFT)
 //               -> rows(IDFT, dpsi, contributions)
 //
 // A length-256 line is transformed by 16 threads: a radix-16 pass in
@@ -68,7 +68,8 @@ __device__ __forceinline__ void load_tw(float2* s_tw, const float2* tw) {
 
 }  // namespace
 
-// ---- row passes. mode 0: exit wave + forward DFT; 1: forward DFT in place; 2: inverse DFT in place, / M^2
+// ---- row passes. mode 0: exit wave + forward DFT; 1: R x (row) then forward DFT in place;
+// 2: inverse DFT in place, / M^2
 template <int MODE, bool NEAR>
 __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
   __shared__ float2 s_tw[BT * BS];
@@ -94,8 +95,10 @@ __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
       a[j] = psi;
     }
   } else if constexpr (MODE == 1) {
+    // Psi' = R Psi (the modulus ratio of this position) on the way in
+    const float* Rr = b.R + (size_t)c * MM + (size_t)y * BL;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];
+    for (int j = 0; j < 16; ++j) a[j] = cscale(row[t + 16 * j], Rr[t + 16 * j]);
   } else {
 #pragma unroll
     for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];  // X[t + 16 k1]
@@ -113,7 +116,8 @@ __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
 }
 
 // ---- column passes on a 256 x 32 tile staged through shared memory.
-// op 0: forward DFT; 1: inverse DFT; 2: DFT, x H, IDFT (near forward); 3: DFT, x conj H, IDFT (near backward)
+// op 0: forward DFT; 1: R x (tile), inverse DFT (far backward); 2: DFT, x H, IDFT (near forward);
+// 3: DFT, x conj H, IDFT (near backward)
 template <int OP>
 __global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
   constexpr int TP = LINES + 1;
@@ -128,10 +132,13 @@ __global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
   const int x0 = blockIdx.x * LINES, k = blockIdx.y, c = blockIdx.z;
   const size_t MM = (size_t)BL * BL;
   float2* Wk = b.W + ((size_t)c * b.K + k) * MM;
-  // coalesced tile load: 32 consecutive columns per row
+  // coalesced tile load: 32 consecutive columns per row; the far-field inverse pass
+  // applies Psi' = R Psi (the modulus ratio of this position) on the way in
+  const float* Rc = b.R + (size_t)c * MM;
   for (int i = threadIdx.x; i < BL * LINES; i += blockDim.x) {
     const int yy = i / LINES, xx = i % LINES;
-    tile[yy * TP + xx] = Wk[(size_t)yy * BL + x0 + xx];
+    const float2 w = Wk[(size_t)yy * BL + x0 + xx];
+    tile[yy * TP + xx] = OP == 1 ? cscale(w, Rc[(size_t)yy * BL + x0 + xx]) : w;
   }
   __syncthreads();
   const int cl = threadIdx.x / BT, t = threadIdx.x % BT;
@@ -168,7 +175,9 @@ __global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
   }
 }
 
-// ---- modulus: rows [y0, y0 + RB) of one position, with KH halo rows for the y blur
+// ---- modulus: rows [y0, y0 + RB) of one position, with KH halo rows for the y blur.
+// Writes the ratio R to its own buffer (W is still read by the neighbouring
+// blocks' halos); the next pass applies Psi' = R Psi as it loads W.
 template <int KH>
 __global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
   constexpr int HR = RB + 2 * KH;  // rows held
@@ -232,10 +241,7 @@ __global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
     const float tt = es + yv;
     ec = (tt - es) - yv;
     es = tt;
-    for (int k = 0; k < b.K; ++k) {
-      float2* w = b.W + ((size_t)c * b.K + k) * MM + (size_t)y * BL + x;
-      *w = cscale(*w, R);
-    }
+    b.R[(size_t)c * MM + (size_t)y * BL + x] = R;
   }
   s_red[threadIdx.x] = (double)es - (double)ec;
   __syncthreads();

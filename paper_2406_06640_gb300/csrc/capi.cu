@@ -69,6 +69,13 @@ struct ptycho_plan_s {
   ConstraintArgs ca{};
   BigArgs ba{};
   bool big = false;  // M = 256: staged passes over a chunk of positions
+  // batch plans: independent member plans replayed as one CUDA graph per iteration
+  std::vector<ptycho_plan_s*> members;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> branch_ev;
+  std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
+  cudaStream_t origin = nullptr;          // capture / replay stream of a batch plan
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int chunk = 0;
   double* d_errhist = nullptr;
   // profiling: event pairs around the fused kernel
@@ -86,6 +93,13 @@ struct ptycho_plan_s {
     return e;
   }
   ~ptycho_plan_s() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    for (cudaEvent_t e : branch_ev) cudaEventDestroy(e);
+    for (cudaStream_t s : branch) cudaStreamDestroy(s);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (origin) cudaStreamDestroy(origin);
+    for (ptycho_plan_s* m : members) delete m;
     for (void* q : allocs) cudaFree(q);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
@@ -231,7 +245,11 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   const size_t nerr = pl->big ? (size_t)N * big_row_blocks() : (size_t)pl->slots * K;
   PT_CUDA(pl->alloc(&d_errpart, nerr), "alloc error partials");
   float2* d_W = nullptr;
-  if (pl->big) PT_CUDA(pl->alloc(&d_W, (size_t)pl->chunk * K * MM), "alloc staged scratch");
+  float* d_R = nullptr;
+  if (pl->big) {
+    PT_CUDA(pl->alloc(&d_W, (size_t)pl->chunk * K * MM), "alloc staged scratch");
+    PT_CUDA(pl->alloc(&d_R, (size_t)pl->chunk * MM), "alloc staged ratios");
+  }
 
   // object tiles and their position lists (increasing n)
   const int tx = (p.obj_w + kObjTile - 1) / kObjTile, ty = (p.obj_h + kObjTile - 1) / kObjTile;
@@ -280,6 +298,9 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
     PT_CUDA(cudaMemcpy(d_cover, cover.data(), sizeof(int) * plane, cudaMemcpyHostToDevice), "copy coverage");
   }
   PT_CUDA(pl->alloc(&pl->d_errhist, (size_t)kErrHistory), "alloc error history");
+  unsigned long long* d_runs;
+  PT_CUDA(pl->alloc(&d_runs, 1), "alloc run counter");
+  PT_CUDA(cudaMemset(d_runs, 0, sizeof(unsigned long long)), "clear run counter");
 
   // ---- kernel argument blocks
   fa.I = d_I;
@@ -327,6 +348,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ua.blk_max_p = d_bmp;
   ua.probe_blocks = pb;
   ua.errhist = pl->d_errhist;
+  ua.run_counter = d_runs;
   ua.errden = pl->errden;
   ua.beta_obj = (float)p.beta_obj;
   ua.beta_probe = (float)p.beta_probe;
@@ -366,6 +388,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ba.tw = d_tw;
   ba.hq = d_hq;
   ba.W = d_W;
+  ba.R = d_R;
   ba.cn = d_cn;
   ba.pacc = d_pacc;
   ba.dacc = d_dacc;
@@ -407,11 +430,8 @@ ptycho_status ptycho_plan(const ptycho_params* p, const float* intensities, cons
   return PTYCHO_OK;
 }
 
-ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_t n_iter) {
-  if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
-  if (!object || !probe) return fail(PTYCHO_EINVAL, "object and probe must be non-NULL");
-  if (n_iter < 0) return fail(PTYCHO_EINVAL, "n_iter must be >= 0");
-  PT_CUDA(cudaSetDevice(pl->device), "cudaSetDevice");
+// Enqueue one iteration (number t) of plan pl on stream s.
+static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* probe, long long t, cudaStream_t s) {
   FusedArgs fa = pl->fa;
   UpdateArgs ua = pl->ua;
   ConstraintArgs ca = pl->ca;
@@ -420,37 +440,177 @@ ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_
   ua.O = static_cast<float2*>(object);
   ua.P = static_cast<float2*>(probe);
   ca.O = static_cast<float2*>(object);
+  const int ps = pl->prof_count % ptycho_plan_s::kProfSlots;
+  if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], s), "profile event");
+  if (pl->big) {
+    BigArgs ba = pl->ba;
+    ba.O = static_cast<const float2*>(object);
+    ba.P = static_cast<const float2*>(probe);
+    for (int n0 = 0; n0 < pl->p.N; n0 += pl->chunk) {
+      ba.n0 = n0;
+      PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, pl->p.N - n0), s), "staged pass launch");
+    }
+  } else {
+    PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, s), "fused kernel launch");
+  }
+  if (pl->profiling) {
+    PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], s), "profile event");
+    pl->prof_count++;
+  }
+  ua.update_probe = t >= pl->p.probe_update_start;
+  PT_CUDA(launch_update(ua, s), "update launch");
+  if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_t n_iter) {
+  if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
+  if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "batch plans run through ptycho_iterate_batch");
+  if (!object || !probe) return fail(PTYCHO_EINVAL, "object and probe must be non-NULL");
+  if (n_iter < 0) return fail(PTYCHO_EINVAL, "n_iter must be >= 0");
+  PT_CUDA(cudaSetDevice(pl->device), "cudaSetDevice");
   for (int i = 0; i < n_iter; ++i) {
-    const long long t = pl->iter;
-    const int ps = pl->prof_count % ptycho_plan_s::kProfSlots;
-    if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], pl->stream), "profile event");
-    if (pl->big) {
-      BigArgs ba = pl->ba;
-      ba.O = static_cast<const float2*>(object);
-      ba.P = static_cast<const float2*>(probe);
-      for (int n0 = 0; n0 < pl->p.N; n0 += pl->chunk) {
-        ba.n0 = n0;
-        PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, pl->p.N - n0), pl->stream), "staged pass launch");
-      }
-    } else {
-      PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, pl->stream), "fused kernel launch");
-    }
-    if (pl->profiling) {
-      PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], pl->stream), "profile event");
-      pl->prof_count++;
-    }
-    ua.hist_index = (int)(pl->runs % kErrHistory);
-    ua.update_probe = t >= pl->p.probe_update_start;
-    PT_CUDA(launch_update(ua, pl->stream), "update launch");
-    if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, pl->stream), "constraint launch");
+    const ptycho_status st = enqueue_iteration(pl, object, probe, pl->iter, pl->stream);
+    if (st != PTYCHO_OK) return st;
     pl->iter++;
     pl->runs++;
   }
   return PTYCHO_OK;
 }
 
+ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, const float* const* intensities,
+                                const int32_t* const* positions, void* cuda_stream, ptycho_plan_t* out) {
+  if (!out) return fail(PTYCHO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (B < 1 || !params || !intensities || !positions) return fail(PTYCHO_EINVAL, "need B >= 1 and non-NULL arrays");
+  for (int b = 0; b < B; ++b) {
+    ptycho_status st = validate(params[b]);
+    if (st == PTYCHO_OK && (!intensities[b] || !positions[b]))
+      st = fail(PTYCHO_EINVAL, "intensities and positions must be non-NULL");
+    if (st != PTYCHO_OK) return fail(st, "problem " + std::to_string(b) + ": " + g_last_error);
+  }
+  ptycho_plan_s* pl = new (std::nothrow) ptycho_plan_s();
+  if (!pl) return fail(PTYCHO_ENOMEM, "host allocation failed");
+  pl->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  for (int b = 0; b < B; ++b) {
+    ptycho_status st = PTYCHO_OK;
+    ptycho_plan_s* m = new (std::nothrow) ptycho_plan_s();
+    if (!m) st = fail(PTYCHO_ENOMEM, "host allocation failed");
+    if (st == PTYCHO_OK) {
+      pl->members.push_back(m);
+      m->p = *params[b];
+      m->windows.assign(params[b]->windows, params[b]->windows + 2 * params[b]->n_windows);
+      m->p.windows = nullptr;
+      m->stream = pl->stream;
+      m->iter = params[b]->start_iteration;
+      m->device = pl->device;
+      st = build_plan(m, intensities[b], positions[b]);
+    }
+    if (st != PTYCHO_OK) {
+      const std::string msg = "problem " + std::to_string(b) + ": " + g_last_error;
+      cudaStreamSynchronize(pl->stream);
+      delete pl;
+      return fail(st, msg);
+    }
+  }
+  const int S = std::min(B, 8);
+  pl->branch.resize(S);
+  pl->branch_ev.resize(S + 1);
+  for (int i = 0; i < S; ++i) PT_CUDA(cudaStreamCreateWithFlags(&pl->branch[i], cudaStreamNonBlocking), "branch stream");
+  for (auto& ev : pl->branch_ev) PT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "branch event");
+  PT_CUDA(cudaStreamCreateWithFlags(&pl->origin, cudaStreamNonBlocking), "origin stream");
+  PT_CUDA(cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming), "event");
+  PT_CUDA(cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming), "event");
+  g_last_error.clear();
+  *out = pl;
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void* const* probes, int32_t n_iter) {
+  if (!pl || pl->members.empty()) return fail(PTYCHO_EINVAL, "not a batch plan");
+  if (!objects || !probes || n_iter < 0) return fail(PTYCHO_EINVAL, "bad arguments");
+  const int B = (int)pl->members.size();
+  for (int b = 0; b < B; ++b)
+    if (!objects[b] || !probes[b]) return fail(PTYCHO_EINVAL, "object and probe pointers must be non-NULL");
+  PT_CUDA(cudaSetDevice(pl->device), "cudaSetDevice");
+  const int S = (int)pl->branch.size();
+  for (int i = 0; i < n_iter; ++i) {
+    // the graph depends on which members update the probe / apply the constraint this iteration
+    std::vector<uintptr_t> key;
+    key.reserve(3 * B);
+    for (int b = 0; b < B; ++b) {
+      const ptycho_plan_s* m = pl->members[b];
+      key.push_back((uintptr_t)((m->iter >= m->p.probe_update_start ? 1 : 0) | (m->in_window(m->iter) ? 2 : 0)));
+      key.push_back((uintptr_t)objects[b]);
+      key.push_back((uintptr_t)probes[b]);
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : pl->graphs)
+      if (g.first == key) exec = g.second;
+    if (!exec) {
+      PT_CUDA(cudaStreamBeginCapture(pl->origin, cudaStreamCaptureModeRelaxed), "begin capture");
+      ptycho_status st = PTYCHO_OK;
+      cudaError_t ce = cudaEventRecord(pl->branch_ev[S], pl->origin);
+      for (int j = 0; j < S && ce == cudaSuccess; ++j) ce = cudaStreamWaitEvent(pl->branch[j], pl->branch_ev[S], 0);
+      for (int b = 0; b < B && ce == cudaSuccess && st == PTYCHO_OK; ++b)
+        st = enqueue_iteration(pl->members[b], objects[b], probes[b], pl->members[b]->iter, pl->branch[b % S]);
+      for (int j = 0; j < S && ce == cudaSuccess && st == PTYCHO_OK; ++j) {
+        ce = cudaEventRecord(pl->branch_ev[j], pl->branch[j]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(pl->origin, pl->branch_ev[j], 0);
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(pl->origin, &graph);
+      if (st != PTYCHO_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ce, "capture of the batch iteration");
+      }
+      PT_CUDA(ee, "end capture");
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      PT_CUDA(ie, "instantiate the batch graph");
+      pl->graphs.emplace_back(key, exec);
+    }
+    PT_CUDA(cudaEventRecord(pl->ev_in, pl->stream), "event");
+    PT_CUDA(cudaStreamWaitEvent(pl->origin, pl->ev_in, 0), "wait");
+    PT_CUDA(cudaGraphLaunch(exec, pl->origin), "graph launch");
+    PT_CUDA(cudaEventRecord(pl->ev_out, pl->origin), "event");
+    PT_CUDA(cudaStreamWaitEvent(pl->stream, pl->ev_out, 0), "wait");
+    for (ptycho_plan_s* m : pl->members) {
+      m->iter++;
+      m->runs++;
+    }
+  }
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_error_batch(ptycho_plan_t pl, double* nrmse_last) {
+  if (!pl || pl->members.empty() || !nrmse_last) return fail(PTYCHO_EINVAL, "not a batch plan or NULL output");
+  PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
+  bool finite = true;
+  for (size_t b = 0; b < pl->members.size(); ++b) {
+    const ptycho_plan_s* m = pl->members[b];
+    if (m->runs == 0) return fail(PTYCHO_EINVAL, "no iteration has run");
+    PT_CUDA(cudaMemcpy(&nrmse_last[b], m->d_errhist + (m->runs - 1) % kErrHistory, sizeof(double),
+                       cudaMemcpyDeviceToHost),
+            "copy error");
+    finite = finite && std::isfinite(nrmse_last[b]);
+  }
+  if (!finite) return fail(PTYCHO_ENUMERIC, "an error metric is not finite");
+  return PTYCHO_OK;
+}
+
 ptycho_status ptycho_error(ptycho_plan_t pl, double* nrmse_last) {
   if (!pl || !nrmse_last) return fail(PTYCHO_EINVAL, "NULL argument");
+  if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "batch plans report through ptycho_error_batch");
   PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
   if (pl->runs == 0) return fail(PTYCHO_EINVAL, "no iteration has run");
   double e = 0.0;
@@ -463,6 +623,7 @@ ptycho_status ptycho_error(ptycho_plan_t pl, double* nrmse_last) {
 
 ptycho_status ptycho_error_history(ptycho_plan_t pl, double* out, int32_t n, int32_t* count) {
   if (!pl || !out || !count || n < 0) return fail(PTYCHO_EINVAL, "bad argument");
+  if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "batch plans report through ptycho_error_batch");
   PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
   const long long c = std::min<long long>({(long long)n, pl->runs, (long long)kErrHistory});
   std::vector<double> ring(kErrHistory);
@@ -477,12 +638,14 @@ ptycho_status ptycho_destroy(ptycho_plan_t pl) {
   if (!pl) return PTYCHO_OK;
   cudaSetDevice(pl->device);
   cudaStreamSynchronize(pl->stream);
+  if (pl->origin) cudaStreamSynchronize(pl->origin);
   delete pl;
   return PTYCHO_OK;
 }
 
 ptycho_status ptycho_profile(ptycho_plan_t pl, int32_t enable) {
   if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
+  if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "profiling applies to single plans");
   if (enable && pl->ev.empty()) {
     pl->ev.resize(2 * ptycho_plan_s::kProfSlots);
     for (cudaEvent_t& e : pl->ev) PT_CUDA(cudaEventCreate(&e), "cudaEventCreate");

@@ -150,6 +150,7 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     ua.p2 = cv.take<float>(MM);
     ua.blk_max_p = cv.take<float>((size_t)pb);
     ua.errhist = cv.take<double>((size_t)kErrHistory);
+    ua.run_counter = cv.take<unsigned long long>(1);
     ca.cbar = cv.take<float>((size_t)N);
     ca.sat_lna = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
     ca.sat_phi = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
@@ -178,6 +179,7 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
 
   // ---- per-call set-up, all through the scratch
   PS_CUDA(cudaMemcpyAsync(dpos, hpos.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, s), "copy positions");
+  PS_CUDA(cudaMemsetAsync(ua.run_counter, 0, sizeof(unsigned long long), s), "clear the run counter");
   PS_CUDA(cudaMemcpyAsync(const_cast<int*>(ua.tile_start), start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, s),
           "copy tile lists");
   if (!flat.empty())
@@ -264,7 +266,6 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   for (int i = 0; i < n_iter; ++i) {
     const long long t = (long long)p->start_iteration + i;
     PS_CUDA(launch_fused(M, fa, slots, s), "fused kernel launch");
-    ua.hist_index = i;
     ua.update_probe = t >= p->probe_update_start;
     PS_CUDA(launch_update(ua, s), "update launch");
     bool win = false;

@@ -51,6 +51,7 @@ struct BigArgs {
   const float2* tw;   // W_M^m, m in [0, M)
   const float2* hq;   // near field: h[u]
   float2* W;          // C x K x M x M scratch
+  float* R;           // C x M x M modulus ratios
   int n0;             // first position of the chunk
   float2* cn;         // N x M x M contributions
   float2* pacc;       // C x K x M x M probe partials (slot = position within the chunk)
@@ -77,7 +78,8 @@ struct UpdateArgs {
   float2* np_sum; float* dp_sum; float* p2;  // K x M x M, M x M, M x M
   float* blk_max_p;
   int probe_blocks;
-  double* errhist; int hist_index; double errden;
+  double* errhist; double errden;
+  unsigned long long* run_counter;  // device: iterations finished; E goes to errhist[counter % kErrHistory]
   float beta_obj, beta_probe, delta_obj, delta_probe;
   int update_probe;
 };

@@ -247,7 +247,9 @@ __global__ void k_probe_apply(const UpdateArgs u) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     double e = 0.0;
     for (int s = 0; s < u.nerr; ++s) e += u.errpart[s];
-    u.errhist[u.hist_index] = sqrt(e / u.errden);
+    const unsigned long long r = *u.run_counter;
+    u.errhist[r % kErrHistory] = sqrt(e / u.errden);
+    *u.run_counter = r + 1;
   }
   if (!u.update_probe) return;
   const int MM = u.M * u.M;

@@ -10,7 +10,7 @@ from typing import Optional
 import numpy as np
 import torch
 
-from .binding import Plan
+from .binding import BatchPlan, Plan
 
 
 def _require_cuda(t: torch.Tensor, name: str, dtype: torch.dtype):
@@ -59,6 +59,42 @@ class Reconstruction:
 
     def launches_per_iteration(self, in_window: bool) -> int:
         return self._plan.launches_per_iteration(in_window)
+
+    def close(self):
+        self._plan.close()
+
+
+class ReconstructionBatch:
+    """Independent reconstructions of uneven sizes, iterated together as one CUDA graph per iteration.
+
+    problems: sequence of (params dict, intensities CUDA tensor, positions) as for Reconstruction.
+    """
+
+    def __init__(self, problems, stream: Optional[torch.cuda.Stream] = None):
+        self._pos = []
+        iptr, pptr, params = [], [], []
+        for prm, I, pos in problems:
+            _require_cuda(I, "intensities", torch.float32)
+            if isinstance(pos, np.ndarray):
+                pos = torch.from_numpy(np.ascontiguousarray(pos, dtype=np.int32))
+            pos = pos.to(torch.int32).contiguous()
+            self._pos.append(pos)
+            params.append(dict(prm))
+            iptr.append(I.data_ptr())
+            pptr.append(pos.data_ptr())
+        dev = problems[0][1].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._plan = BatchPlan(params, iptr, pptr, self.stream.cuda_stream)
+
+    def iterate(self, objects, probes, n_iter: int = 1):
+        for o in objects:
+            _require_cuda(o, "object", torch.complex64)
+        for p in probes:
+            _require_cuda(p, "probe", torch.complex64)
+        self._plan.iterate([o.data_ptr() for o in objects], [p.data_ptr() for p in probes], n_iter)
+
+    def errors(self) -> list:
+        return self._plan.errors()
 
     def close(self):
         self._plan.close()

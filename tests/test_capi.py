@@ -92,3 +92,16 @@ def test_null_arguments():
 
 def test_version_string():
     assert "sm_103a" in pg.version()
+
+
+def test_batch_validation_names_the_problem():
+    lib = pg.load()
+    good, k1 = make_params(dict(M=64, K=1, N=4, obj_h=128, obj_w=128))
+    bad, k2 = make_params(dict(M=64, K=0, N=4, obj_h=128, obj_w=128))
+    arr = (ctypes.POINTER(pg.PtychoParams) * 2)(ctypes.pointer(good), ctypes.pointer(bad))
+    ip = (ctypes.c_void_p * 2)(1, 1)
+    pp = (ctypes.c_void_p * 2)(1, 1)
+    h = ctypes.c_void_p()
+    assert lib.ptycho_plan_batch(2, arr, ip, pp, None, ctypes.byref(h)) == 1
+    assert lib.ptycho_last_error().decode().startswith("problem 1:")
+    assert lib.ptycho_plan_batch(0, arr, ip, pp, None, ctypes.byref(h)) == 1

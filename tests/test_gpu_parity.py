@@ -138,8 +138,13 @@ def test_config1_full_size_two_iterations():
     check(p, p.params, 2)
 
 
-def test_deterministic_and_resumable():
-    p = make_problem(0, scan_side=6, obj_side=144)
+@pytest.mark.parametrize("M,geometry", [(64, "far"), (256, "near")])
+def test_deterministic_and_resumable(M, geometry):
+    """Bitwise-equal reruns (no atomics, fixed reduction orders, no cross-block races) and resume."""
+    if M == 64:
+        p = make_problem(0, scan_side=6, obj_side=144)
+    else:
+        p = make_problem(0, scan_side=5, obj_side=448, M=256, K=2, geometry=geometry, sigma=1.5)
     prm = dict(p.params, windows=[(2, 3)])
     O1, P1, E1 = run_gpu(p, prm, 5)
     O2, P2, E2 = run_gpu(p, prm, 5)
