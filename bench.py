@@ -61,6 +61,8 @@ WORKLOADS = {
                      "object 1024^2, sigma 2, 1e5 photons)"),
     "far64x1": (0, "far-field single-mode pc-engine iteration (probe 64^2, N=100 raster, object 192^2, "
                    "sigma 1, 1e5 photons)"),
+    "batch64": (3, "64 independent reconstructions of uneven sizes (probe 64-256, 100-1600 positions, K 1-4, "
+                   "far/near 50/50, sigma 0.5-3), one CUDA graph launch per iteration"),
 }
 _WORKLOAD = "far128x4"
 
@@ -235,7 +237,103 @@ def run_reference(args):
     return 0
 
 
+def run_ours_batch(args):
+    """The batched workload: one step = one iteration of every problem (one graph launch)."""
+    ws, rank, local = dist_setup(args)
+    import torch
+
+    from paper_2406_06640_gb300.engine import ReconstructionBatch
+    from synth.generators import cfg3_members, make_cfg3_member
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    descr = cfg3_members()
+    problems, objs, prbs, host = [], [], [], []
+    units, flops = 0, 0.0
+    for i, (M, K, N, geo, sig) in enumerate(descr):
+        p = make_cfg3_member(i)
+        prm = dict(p.params, windows=[(1, 1 << 30)])
+        I = torch.from_numpy(p.I).to(dev)
+        problems.append((prm, I, p.positions))
+        objs.append(torch.from_numpy(p.O0.astype(np.complex64)).to(dev))
+        prbs.append(torch.from_numpy(p.P0.astype(np.complex64)).to(dev))
+        host.append((p.O0.astype(np.complex64), p.P0.astype(np.complex64)))
+        units += p.N * p.K
+        flops += algorithmic_flops(p.M, p.K, p.N, geo == "near")
+        del p
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.current_stream(dev)
+    batch = ReconstructionBatch(problems, stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        batch.iterate(objs, prbs, 1)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        batch.iterate(objs, prbs, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = max_over_ranks(ws, total_ms, dev)
+    value = ws * units * args.steps / (t_max / 1e3)
+    # end to end: every problem's state from pinned host memory and back, errors read back
+    hO = [torch.from_numpy(o).pin_memory() for o, _ in host]
+    hP = [torch.from_numpy(q).pin_memory() for _, q in host]
+    e2e_steps = 3
+    t_e2e = 0.0
+    for k in range(e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for o, h in zip(objs, hO):
+            o.copy_(h, non_blocking=True)
+        for q, h in zip(prbs, hP):
+            q.copy_(h, non_blocking=True)
+        batch.iterate(objs, prbs, 1)
+        for o, h in zip(objs, hO):
+            h.copy_(o, non_blocking=True)
+        for q, h in zip(prbs, hP):
+            h.copy_(q, non_blocking=True)
+        E = batch.errors()
+        if k > 0:
+            t_e2e += time.perf_counter() - t0
+    t_e2e = max_over_ranks(ws, t_e2e, dev)
+    state_bytes = sum(o.numel() * 8 for o in objs) + sum(q.numel() * 8 for q in prbs)
+    per_step_s = t_max / args.steps / 1e3
+    achieved = flops / per_step_s / 1e12
+    peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["batch64"][1], "problems": len(descr), "pattern_modes": units,
+                           "complex_constraint": "every step", "step": "one iteration of all 64 problems",
+                           "l2": "flushed before each timed step (256 MiB write)",
+                           "generation_s": round(t_gen, 1)},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": "whole batch graph",
+                             "flops_per_launch": flops},
+                "cpu_baseline": None,
+                "e2e": {"value": ws * units * e2e_steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
+                        "d2h_bytes_per_step": state_bytes + 8 * len(descr)},
+                "gpu_launches": None, "clocks": clocks, "nrmse_mean_last": float(np.mean(E))}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def run_ours(args):
+    if _WORKLOAD == "batch64":
+        return run_ours_batch(args)
     ws, rank, local = dist_setup(args)
     import torch
 
