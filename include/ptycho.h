@@ -139,6 +139,17 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
 ptycho_status ptycho_iterate_batch(ptycho_plan_t plan, void* const* objects, void* const* probes, int32_t n_iter);
 ptycho_status ptycho_error_batch(ptycho_plan_t plan, double* nrmse_last);
 
+/* Tensor-core GEMM used by the warm-start network (the paper has no learned
+ * component; this is the contraction under its 3x3 convolutions):
+ *   D[M x N] = A[M x K] . B[N x K]^T      (accumulate != 0: D += A . B^T)
+ * A, B: device, bf16 bit patterns, row-major with K contiguous; D: device fp32,
+ * row-major N x ... (leading dimension N). BF16 products, FP32 accumulation in
+ * tensor memory (tcgen05). Requires M % 128 == 0, N % 16 == 0, K % 64 == 0,
+ * 16-byte aligned A and B (PTYCHO_EINVAL otherwise). Synchronises `stream`;
+ * PTYCHO_ETIMEOUT if a bounded device-side wait gave up. */
+int ptycho_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K, int accumulate,
+                     void* stream);
+
 /* Per-kernel timing for roofline reports. While enabled, ptycho_iterate records
  * a CUDA event pair on the plan's stream around every launch of the fused
  * per-position kernel (the dominant kernel of an iteration); for M = 256 the

@@ -61,6 +61,18 @@ struct BigArgs {
 cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s);
 int big_row_blocks();
 
+// tcgen05 BF16 GEMM (unet_gemm.cu): D[M x Ntot] (+)= A[M x K] . B[Ntot x K]^T, bf16 operands
+// stored as raw 16-bit words, K contiguous
+struct GemmArgs {
+  const uint16_t* A; const uint16_t* B;
+  float* D; uint16_t* Dh; const float* bias;
+  int M, Ntot, K, ldd;
+  int mode;   // 0: D = AB^T (fp32); 1: D += AB^T (fp32); 2: Dh = act(AB^T + bias) (bf16)
+  int relu;
+  int* status;  // set to 1 when a bounded wait gave up
+};
+cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
+
 // update / reduction kernels (update.cu)
 struct UpdateArgs {
   float2* O; float2* P;
