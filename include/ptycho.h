@@ -192,6 +192,84 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
 ptycho_status ptycho_iterate_static(const ptycho_params* p, const float* intensities, const int32_t* positions,
                                     void* object, void* probe, int32_t n_iter, double* errors, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (the paper has no learned component; it asks for no prior
+ * knowledge of the source, so these calls estimate the object and the blur width
+ * sigma from the patterns themselves before the iteration starts).
+ *
+ * A U-Net with 4 levels (base width C) maps log1p(I) / 4 of each S x S pattern to
+ * (ln |o|, arg o) / target_scale on the central S/2 x S/2 box of its object patch
+ * and to the pattern's sigma. 3x3 convolutions, ReLU, 2x2 average pooling,
+ * nearest 2x upsampling with skip concatenation; BF16 activations and weights,
+ * FP32 accumulation on the tcgen05 tensor cores, FP32 master weights and Adam.
+ * Loss = mean((out - target)^2) + lam mean((sigma - sigma_t)^2).
+ * ------------------------------------------------------------------------- */
+typedef struct ptycho_unet_s* ptycho_unet_t;
+
+/* Create a network for batches of `batch` patterns of S x S pixels (S % 16 == 0,
+ * 16 <= S <= 512; C % 16 == 0, C <= 64; 1 <= batch <= 1024; batch (S/8)^2 a
+ * multiple of 128), He-initialised from `seed`, on `cuda_stream`. */
+ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t seed, void* cuda_stream,
+                                 ptycho_unet_t* out);
+/* Number of floats of the flat parameter vector: for each convolution i = 0..6,
+ * w_i (C_out, 9 taps, C_in) then b_i (C_out), tap = 3 (dy + 1) + (dx + 1); then
+ * the sigma head w7 (8C) and b7 (1). */
+int64_t ptycho_unet_param_count(ptycho_unet_t net);
+/* Copy the parameters in (set) or out (get); host float arrays of param_count
+ * entries. Both synchronise the network's stream. */
+ptycho_status ptycho_unet_set_params(ptycho_unet_t net, const float* params, int64_t count);
+ptycho_status ptycho_unet_get_params(ptycho_unet_t net, float* params_out, int64_t count);
+/* Forward pass on `batch` inputs x (device, batch x S x S f32). out2: device,
+ * batch x (S/2) x (S/2) x 2, or NULL; sigma: device, batch floats, or NULL.
+ * Synchronises; PTYCHO_ETIMEOUT if a bounded tensor-core wait gave up. */
+ptycho_status ptycho_unet_forward(ptycho_unet_t net, const float* x, float* out2, float* sigma);
+/* Loss (host double) and every parameter gradient (host, param_count floats in the
+ * flat order, or NULL) for one batch: x as above, target device batch x (S/2)^2 x 2,
+ * sigma_t device batch floats. Synchronises. */
+ptycho_status ptycho_unet_gradients(ptycho_unet_t net, const float* x, const float* target, const float* sigma_t,
+                                    float lam, double* loss, float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on one batch.
+ * With loss != NULL it synchronises and writes the batch loss (before the step);
+ * with loss == NULL it only enqueues on the network's stream. */
+ptycho_status ptycho_unet_train_step(ptycho_unet_t net, const float* x, const float* target, const float* sigma_t,
+                                     float lam, float lr, double* loss);
+ptycho_status ptycho_unet_destroy(ptycho_unet_t net);
+
+/* Forward-model training data: far-field patterns of random hexagonal crystals
+ * (Gaussian phase peaks of height `peak` rad and sd `peak_sd` px, lattice
+ * constant `lattice_a` px, each site vacant with probability `vacancy` by
+ * Philox4x32-10((i, j, sample, 1), key)), psi = P exp(i phi), the centred DFT
+ * (Eq. 1), |Psi|^2 blurred by an isotropic Gaussian of the pattern's sigma
+ * (Eq. 2; taps +-min(ceil(5 sigma), 15)), scaled to sum `dose`, then Poisson
+ * counts (Philox4x32-10((pixel, sample, attempt, 2), key)) unless noise == 0. */
+typedef struct {
+  int32_t S;                /* pattern side: 64 or 128 */
+  int32_t noise;            /* 0: counts are the noise-free intensities */
+  double dose;              /* counts per pattern */
+  double lattice_a, peak, peak_sd, cutoff, vacancy;  /* px, rad, px, px (peak radius, <= 2 lattice_a), probability */
+  double target_scale;      /* targets = (ln |o|, arg o) / target_scale */
+  uint64_t key;             /* Philox key (low word first) */
+} ptycho_gen_spec;
+/* params: device, n x 4 floats (lattice rotation rad, origin row px, origin col
+ * px, sigma px), 16-byte aligned; probe: device complex64 S x S. Outputs
+ * (device, each optional): x (n x S x S, log1p(counts)/4), counts, clean
+ * (dose-scaled noise-free intensities), target (n x (S/2)^2 x 2, central box),
+ * sigma (n). Pattern i uses sample index first + i. Asynchronous on `stream`. */
+ptycho_status ptycho_generate(const ptycho_gen_spec* spec, const void* probe, const float* params, int32_t n,
+                              uint32_t first, float* x, float* counts, float* clean, float* target, float* sigma,
+                              void* cuda_stream);
+
+/* Warm start: run the network over N measured patterns (device, N x S x S counts,
+ * S the network's side), stitch the predicted central boxes (corner = position +
+ * (S/4, S/4), side S/2, value exp(target_scale (out0 + i out1))) with a separable
+ * Hann window into object_out (device complex64 obj_h x obj_w; 1 where no box
+ * covers a pixel) and write the median predicted sigma to *sigma_out (host).
+ * positions: host or device, N (row, col) int32 box corners; every box of side S
+ * must lie inside the object. Runs on the network's stream and synchronises. */
+ptycho_status ptycho_warmstart(ptycho_unet_t net, const float* intensities, const int32_t* positions, int32_t N,
+                               int32_t obj_h, int32_t obj_w, double target_scale, void* object_out,
+                               double* sigma_out);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ptycho_last_error(void);
 

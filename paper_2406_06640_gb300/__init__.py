@@ -10,11 +10,15 @@ from .binding import (  # noqa: F401
     EXPORTED,
     FARFIELD,
     NEARFIELD,
+    GenSpec,
     Plan,
     PtychoError,
     PtychoParams,
+    UNet,
+    generate,
     library_path,
     load,
+    make_gen_spec,
     make_params,
     version,
 )

@@ -22,7 +22,9 @@ BLUR_AMPLITUDE, BLUR_INTENSITY = 0, 1
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
-            "ptycho_version")
+            "ptycho_version", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
+            "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
+            "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart")
 
 
 class PtychoError(RuntimeError):
@@ -47,6 +49,17 @@ class PtychoParams(ctypes.Structure):
         ("cbar_min", ctypes.c_double), ("cbar_max", ctypes.c_double),
         ("n_windows", ctypes.c_int32), ("windows", ctypes.POINTER(ctypes.c_int32)),
         ("start_iteration", ctypes.c_int32),
+    ]
+
+
+class GenSpec(ctypes.Structure):
+    """Mirror of ptycho_gen_spec."""
+
+    _fields_ = [
+        ("S", ctypes.c_int32), ("noise", ctypes.c_int32), ("dose", ctypes.c_double),
+        ("lattice_a", ctypes.c_double), ("peak", ctypes.c_double), ("peak_sd", ctypes.c_double),
+        ("cutoff", ctypes.c_double), ("vacancy", ctypes.c_double), ("target_scale", ctypes.c_double),
+        ("key", ctypes.c_uint64),
     ]
 
 
@@ -98,6 +111,29 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_last_error.restype = ctypes.c_char_p
     lib.ptycho_version.argtypes = []
     lib.ptycho_version.restype = ctypes.c_char_p
+    F32 = ctypes.c_float
+    lib.ptycho_unet_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P,
+                                       ctypes.POINTER(P)]
+    lib.ptycho_unet_create.restype = st
+    lib.ptycho_unet_param_count.argtypes = [P]
+    lib.ptycho_unet_param_count.restype = ctypes.c_int64
+    lib.ptycho_unet_set_params.argtypes = [P, P, ctypes.c_int64]
+    lib.ptycho_unet_set_params.restype = st
+    lib.ptycho_unet_get_params.argtypes = [P, P, ctypes.c_int64]
+    lib.ptycho_unet_get_params.restype = st
+    lib.ptycho_unet_forward.argtypes = [P, P, P, P]
+    lib.ptycho_unet_forward.restype = st
+    lib.ptycho_unet_gradients.argtypes = [P, P, P, P, F32, ctypes.POINTER(ctypes.c_double), P]
+    lib.ptycho_unet_gradients.restype = st
+    lib.ptycho_unet_train_step.argtypes = [P, P, P, P, F32, F32, ctypes.POINTER(ctypes.c_double)]
+    lib.ptycho_unet_train_step.restype = st
+    lib.ptycho_unet_destroy.argtypes = [P]
+    lib.ptycho_unet_destroy.restype = st
+    lib.ptycho_generate.argtypes = [ctypes.POINTER(GenSpec), P, P, ctypes.c_int32, ctypes.c_uint32, P, P, P, P, P, P]
+    lib.ptycho_generate.restype = st
+    lib.ptycho_warmstart.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P,
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.ptycho_warmstart.restype = st
     _lib = lib
     return lib
 
@@ -233,3 +269,81 @@ class BatchPlan:
 
 def version() -> str:
     return load().ptycho_version().decode()
+
+
+class UNet:
+    """The warm-start network (ptycho_unet_*): device pointers in, status checked."""
+
+    def __init__(self, S: int, C: int, batch: int, seed: int = 0, stream_ptr: int = 0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.ptycho_unet_create(S, C, batch, seed, stream_ptr, ctypes.byref(self._h)))
+        self.S, self.C, self.batch = S, C, batch
+
+    def param_count(self) -> int:
+        return int(self._lib.ptycho_unet_param_count(self._h))
+
+    def set_params(self, flat):
+        """flat: contiguous float32 host array (numpy) of param_count() values."""
+        _check(self._lib.ptycho_unet_set_params(self._h, flat.ctypes.data, flat.size))
+
+    def get_params(self, out):
+        _check(self._lib.ptycho_unet_get_params(self._h, out.ctypes.data, out.size))
+        return out
+
+    def forward(self, x_ptr: int, out2_ptr: int = 0, sigma_ptr: int = 0):
+        _check(self._lib.ptycho_unet_forward(self._h, x_ptr, out2_ptr or None, sigma_ptr or None))
+
+    def gradients(self, x_ptr: int, target_ptr: int, sigma_t_ptr: int, lam: float, grads=None) -> float:
+        loss = ctypes.c_double()
+        _check(self._lib.ptycho_unet_gradients(self._h, x_ptr, target_ptr, sigma_t_ptr, lam, ctypes.byref(loss),
+                                               grads.ctypes.data if grads is not None else None))
+        return loss.value
+
+    def train_step(self, x_ptr: int, target_ptr: int, sigma_t_ptr: int, lam: float, lr: float,
+                   want_loss: bool = False):
+        loss = ctypes.c_double()
+        _check(self._lib.ptycho_unet_train_step(self._h, x_ptr, target_ptr, sigma_t_ptr, lam, lr,
+                                                ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def warmstart(self, intensities_ptr: int, positions_ptr: int, N: int, obj_h: int, obj_w: int,
+                  target_scale: float, object_ptr: int) -> float:
+        sigma = ctypes.c_double()
+        _check(self._lib.ptycho_warmstart(self._h, intensities_ptr, positions_ptr, N, obj_h, obj_w, target_scale,
+                                          object_ptr, ctypes.byref(sigma)))
+        return sigma.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(self._lib.ptycho_unet_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_gen_spec(d: dict) -> GenSpec:
+    g = GenSpec()
+    g.S = int(d.get("S", 128))
+    g.noise = int(d.get("noise", 1))
+    g.dose = float(d.get("dose", 200.0))
+    g.lattice_a = float(d.get("lattice_a", 16.0))
+    g.peak = float(d.get("peak", 0.1))
+    g.peak_sd = float(d.get("peak_sd", 1.5))
+    g.cutoff = float(d.get("cutoff", 6.0))
+    g.vacancy = float(d.get("vacancy", 0.05))
+    g.target_scale = float(d.get("target_scale", 0.1))
+    g.key = int(d.get("key", 0)) & ((1 << 64) - 1)
+    return g
+
+
+def generate(spec: dict, probe_ptr: int, params_ptr: int, n: int, first: int = 0, x: int = 0, counts: int = 0,
+             clean: int = 0, target: int = 0, sigma: int = 0, stream_ptr: int = 0):
+    """ptycho_generate: forward-model training patterns into the given device buffers (0 = not wanted)."""
+    g = make_gen_spec(spec)
+    _check(load().ptycho_generate(ctypes.byref(g), probe_ptr, params_ptr, n, first, x or None, counts or None,
+                                  clean or None, target or None, sigma or None, stream_ptr or None))

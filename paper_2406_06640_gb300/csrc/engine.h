@@ -70,6 +70,14 @@ struct GemmArgs {
   int mode;   // 0: D = AB^T (fp32); 1: D += AB^T (fp32); 2: Dh = act(AB^T + bias) (bf16)
   int relu;
   int* status;  // set to 1 when a bounded wait gave up
+  // implicit 3x3 convolution: row p of A is the zero-padded 3x3 neighbourhood of
+  // pixel p of the NHWC tensor A (batch x H x W x Cin), k = tap * Cin + c,
+  // tap = 3 (dy + 1) + (dx + 1); K may exceed 9 Cin (zero columns)
+  int conv, H, W, Cin;
+  // split-K (mode 0 only): blockIdx.z walks K columns [z kc, min(K, (z + 1) kc)) and stores
+  // its partial product at D + z dsplit; 1 = no split
+  int ksplit, kc;
+  size_t dsplit;
 };
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
 
@@ -114,5 +122,38 @@ cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s);
 cudaError_t launch_intensity_sums(const float* I, size_t count, double* partials, int nblocks, cudaStream_t s);
 cudaError_t launch_finish_sums(const double* partials, int nblocks, double* out2, cudaStream_t s);
 cudaError_t launch_sqrt(const float* I, float* out, size_t count, cudaStream_t s);
+
+// warm-start data generator and assembly (gen.cu)
+struct GenArgs {
+  const float2* probe;   // S x S probe
+  const float4* params;  // per pattern: (lattice rotation, origin row, origin col, blur sigma)
+  int n;                 // patterns
+  uint32_t first;        // sample index of the first pattern (Philox counter word)
+  uint32_t key_lo, key_hi;
+  float dose;            // photons / electrons per pattern
+  float a, peak, s_pk, cutoff;  // lattice constant (px), peak phase (rad), peak sd (px), peak radius (px)
+  uint32_t vac_thresh;           // a site is vacant when its Philox word is below this
+  float target_scale;    // targets are (ln |o|, arg o) / target_scale
+  int noise;             // 0: counts = the noise-free intensities
+  float* x;              // n x S x S network input log1p(counts) / 4, or nullptr
+  float* counts;         // n x S x S, or nullptr
+  float* clean;          // n x S x S dose-scaled noise-free intensities, or nullptr
+  float* target;         // n x (S/2) x (S/2) x 2, or nullptr
+  float* sigma;          // n, or nullptr
+};
+cudaError_t launch_gen(int S, const GenArgs& a, cudaStream_t s);
+size_t gen_smem_bytes(int S);
+cudaError_t launch_log_input(const float* I, float* x, size_t count, cudaStream_t s);
+struct StitchArgs {
+  const float* patches;   // N x patch x patch x 2 network outputs
+  int patch;              // patch side
+  float scale;            // patch value = exp(scale (out0 + i out1))
+  const int* tile_start;  // CSR over kObjTile x kObjTile object tiles
+  const int4* tile_pos;   // (n, corner row, corner col, 0), increasing n
+  int tiles_x, tiles_y, obj_h, obj_w;
+  float2* O;              // out: obj_h x obj_w
+};
+cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t s);
+cudaError_t launch_median(float* v, int n, int npad, double* out, cudaStream_t s);
 
 }  // namespace ptycho

@@ -5,6 +5,7 @@
 //
 //   D[M x N] (+)= A[M x K] . B[N x K]^T      A, B bf16 row-major (K contiguous)
 //   M % 128 == 0, N % 16 == 0 and 16 <= N <= 256, K % 64 == 0
+//   (optionally split along K over blockIdx.z into separate partial products)
 //
 // One CTA (128 threads) owns a 128 x N tile of D. K is walked in chunks of 64:
 // the chunk of A (128 x 64) and of B (N x 64) is copied into shared memory in
@@ -125,6 +126,26 @@ __device__ __forceinline__ void stage(uint8_t* dst, const __nv_bfloat16* src, in
   }
 }
 
+// implicit-GEMM operand: 128 rows (pixels m0 ..) x 64 columns of the 3x3
+// neighbourhood matrix of an NHWC tensor, gathered 8 channels (16 bytes) at a time
+__device__ __forceinline__ void stage_conv(uint8_t* dst, const __nv_bfloat16* X, int m0, int k0, int H, int W,
+                                           int Cin) {
+  for (int i = threadIdx.x; i < 128 * 8; i += blockDim.x) {
+    const int r = i >> 3, q = i & 7;
+    const int k = k0 + q * 8;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (k < 9 * Cin) {
+      const int tap = k / Cin, c = k - tap * Cin;
+      const int p = m0 + r;
+      const int x = p % W, y = (p / W) % H, b = p / (W * H);
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+        v = *reinterpret_cast<const uint4*>(X + (((size_t)b * H + yy) * W + xx) * Cin + c);
+    }
+    *reinterpret_cast<uint4*>(dst + (size_t)(((r >> 3) * 8 + q) * 128 + (r & 7) * 16)) = v;
+  }
+}
+
 }  // namespace
 
 // epilogue modes: 0 = store fp32 D; 1 = accumulate into fp32 D (D += A B^T);
@@ -151,12 +172,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = make_idesc(128, N);
-  const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(g.A) + (size_t)m0 * g.K;
+  const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(g.A) + (g.conv ? 0 : (size_t)m0 * g.K);
   const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(g.B) + (size_t)n0 * g.K;
   uint32_t phase = 0;
   bool ok = true;
-  for (int k0 = 0; k0 < g.K && ok; k0 += KC) {
-    stage(sA, A, 128, g.K, k0);
+  const int kbeg = g.ksplit > 1 ? (int)blockIdx.z * g.kc : 0;
+  const int kend = g.ksplit > 1 ? min(g.K, kbeg + g.kc) : g.K;
+  for (int k0 = kbeg; k0 < kend && ok; k0 += KC) {
+    if (g.conv) stage_conv(sA, A, m0, k0, g.H, g.W, g.Cin);
+    else stage(sA, A, 128, g.K, k0);
     stage(sB, B, N, g.K, k0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -166,7 +190,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
       for (int s = 0; s < KC / 16; ++s) {
         const uint64_t ad = make_desc(smem_u32(sA) + s * 256, 128, 1024);
         const uint64_t bd = make_desc(smem_u32(sB) + s * 256, 128, 1024);
-        mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+        mma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || s > 0) ? 1u : 0u);
       }
       mma_commit(&bar);
     }
@@ -194,7 +218,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
           out[j] = __float2bfloat16(x);
         }
       } else {
-        float* out = g.D + (size_t)row * g.ldd + n0 + c0;
+        float* out = g.D + (g.ksplit > 1 ? (size_t)blockIdx.z * g.dsplit : 0) + (size_t)row * g.ldd + n0 + c0;
 #pragma unroll
         for (int j = 0; j < 16; ++j) out[j] = g.mode == 1 ? out[j] + v[j] : v[j];
       }
@@ -211,13 +235,16 @@ static cudaError_t launch_n(const GemmArgs& g, cudaStream_t s) {
   const size_t smem = 128 * KC * 2 + (size_t)N * KC * 2;
   cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_bf16<N><<<dim3(g.M / 128, g.Ntot / N), 128, smem, s>>>(g);
+  k_gemm_bf16<N><<<dim3(g.M / 128, g.Ntot / N, g.ksplit > 1 ? g.ksplit : 1), 128, smem, s>>>(g);
   return cudaGetLastError();
 }
 
 // N tile chosen from the output width: the widest of 256/128/64/32/16 dividing it
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (g.M % 128 || g.K % KC || g.Ntot % 16 || g.M <= 0 || g.K <= 0 || g.Ntot <= 0) return cudaErrorInvalidValue;
+  if (g.ksplit > 1 && (g.mode != 0 || g.kc % KC || g.kc <= 0 || (long long)(g.ksplit - 1) * g.kc >= g.K ||
+                       (long long)g.ksplit * g.kc < g.K || g.ksplit > 65535))
+    return cudaErrorInvalidValue;  // every split must own at least one chunk
   if (g.Ntot % 256 == 0) return launch_n<256>(g, s);
   if (g.Ntot % 128 == 0) return launch_n<128>(g, s);
   if (g.Ntot % 64 == 0) return launch_n<64>(g, s);

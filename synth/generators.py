@@ -329,10 +329,11 @@ def cfg3_members(seed=3, count=64, M_choices=(64, 128, 256), N_range=(100, 1600)
     return out
 
 
-def _cfg4(seed, scan_side=64, M=128, obj_side=256, dose=200.0, sigma=2.0, dx=0.2e-10, step=2):
+def _cfg4(seed, scan_side=64, M=128, obj_side=256, dose=200.0, sigma=2.0, dx=0.2e-10, step=2, peak=0.1):
     r_obj, r_probe, r_scan, r_noise = _streams(seed)
     lam = electron_wavelength(300e3)
-    # hexagonal lattice of Gaussian phase peaks, 0.1 rad, sigma 0.3 A, 5% vacancies, random rotation
+    # hexagonal lattice of Gaussian phase peaks (`peak` rad, 0.1 by default), sigma 0.3 A, 5% vacancies,
+    # random rotation
     a = 3.2e-10 / dx
     s_pk = 0.3e-10 / dx
     rot = r_obj.uniform(0, np.pi / 3)
@@ -351,7 +352,7 @@ def _cfg4(seed, scan_side=64, M=128, obj_side=256, dose=200.0, sigma=2.0, dx=0.2
                 continue
             y0, y1 = max(int(p[0]) - h, 0), min(int(p[0]) + h + 1, obj_side)
             x0, x1 = max(int(p[1]) - h, 0), min(int(p[1]) + h + 1, obj_side)
-            phase[y0:y1, x0:x1] += 0.1 * np.exp(
+            phase[y0:y1, x0:x1] += peak * np.exp(
                 -((yy[y0:y1, x0:x1] - p[0]) ** 2 + (xx[y0:y1, x0:x1] - p[1]) ** 2) / (2 * s_pk * s_pk))
     O = np.exp(1j * phase)
     # defocused probe: 25 mrad aperture, 20 nm defocus
