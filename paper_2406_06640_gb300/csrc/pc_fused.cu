@@ -165,13 +165,13 @@ __device__ __forceinline__ void det_coords(int vt, int r, int& row, int& col) {
   }
 }
 
-// E consecutive outputs of a zero-padded correlation along a line of a f32
+// NO consecutive outputs of a zero-padded correlation along a line of a f32
 // buffer: out[o] = sum_d g[d] in[c0 + o + d - KH], samples outside [lo, hi)
 // read as zero; `stride` steps between consecutive samples.
-template <int M, int KH>
+template <int NO, int KH>
 __device__ __forceinline__ void blur_strip(const float* in, int base, int stride, int c0, int lo, int hi,
-                                           const float* g, float (&out)[Tile<M>::E]) {
-  constexpr int E = Tile<M>::E;
+                                           const float* g, float (&out)[NO]) {
+  constexpr int E = NO;
   constexpr int W = E + 2 * KH;
   float win[W];
 #pragma unroll
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
   using SM = FusedSmem<M, KH>;
   constexpr int E = TL::E, G = TL::G, LD = SM::LD, LDN = TL::LDN;
   constexpr int V = FusedShape<M>::V, TR = FusedShape<M>::TR;
+  constexpr int NB = E > 8 ? 8 : E;  // outputs per blur strip
   extern __shared__ __align__(16) unsigned char smem[];
   float2* cbuf = reinterpret_cast<float2*>(smem);
   float* Z = reinterpret_cast<float*>(smem);  // R for the whole tile, M x LD
@@ -293,20 +294,23 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     float2 v[V][E];
     // ---- exit wave in ROW layout
     if constexpr (TM) {
+      // every object load of this thread in flight at once (the TMEM waits below are compiler
+      // barriers: loads issued after them would expose one L2 round trip per group)
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[q][j] = On[(size_t)line[q] * a.obj_w + tp[q] + G * j];
 #pragma unroll
       for (int q = 0; q < V; ++q)
 #pragma unroll
         for (int h = 0; h < E / 4; ++h) {
           float pr[8];
           tmem_ld8(t_lane + colP + 2 * (q * E + 4 * h), pr);
-          float2 o[4];
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) o[jj] = On[(size_t)line[q] * a.obj_w + tp[q] + G * (4 * h + jj)];
           tmem_wait_ld();
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
             const int x = tp[q] + G * (4 * h + jj);
-            float2 psi = cmul(make_float2(pr[2 * jj], pr[2 * jj + 1]), o[jj]);
+            float2 psi = cmul(make_float2(pr[2 * jj], pr[2 * jj + 1]), v[q][4 * h + jj]);
             if (!NEAR && ((line[q] + x) & 1)) psi = make_float2(-psi.x, -psi.y);
             v[q][4 * h + jj] = psi;
           }
@@ -365,20 +369,21 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     }
     __syncthreads();
     // ---- (3) blur along x (columns, sigma_1) of the own rows; push the rows other ranks need as halo
-    for (int w = tid; w < nrow * (M / E); w += TR) {
-      const int lr = w % nrow, c0 = (w / nrow) * E;
+    // (strips of NB outputs: enough work items for every thread at K = 4)
+    for (int w = tid; w < nrow * (M / NB); w += TR) {
+      const int lr = w % nrow, c0 = (w / nrow) * NB;
       const int gr = r0 + lr;
-      float out[E];
-      blur_strip<M, KH>(X, lr * LD, 1, c0, 0, M, s_gx, out);
+      float out[NB];
+      blur_strip<NB, KH>(X, lr * LD, 1, c0, 0, M, s_gx, out);
 #pragma unroll
-      for (int o = 0; o < E; ++o) Yb[(lr + KH) * LD + c0 + o] = out[o];
+      for (int o = 0; o < NB; ++o) Yb[(lr + KH) * LD + c0 + o] = out[o];
       for (int q = 0; q < K; ++q) {
         if (q == rank) continue;
         const int q0 = min(M, q * RPO), q1 = min(M, q0 + RPO);
         if ((gr >= q0 - KH && gr < q0) || (gr >= q1 && gr < q1 + KH)) {
           const uint32_t base = map_rank(yb_s + (uint32_t)(((gr - q0 + KH) * LD + c0) * 4), (unsigned)q);
 #pragma unroll
-          for (int o = 0; o < E; ++o) st_cluster_f32(base + 4u * o, out[o]);
+          for (int o = 0; o < NB; ++o) st_cluster_f32(base + 4u * o, out[o]);
         }
       }
     }
@@ -387,13 +392,13 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     {
       const float* In = a.I + (size_t)n * M * M;
       const float* Sn = a.sqrtI + (size_t)n * M * M;
-      const int nstrip = (nrow + E - 1) / E;
+      const int nstrip = (nrow + NB - 1) / NB;
       for (int w = tid; w < M * nstrip; w += TR) {
-        const int col = w % M, rs = (w / M) * E;
-        float out[E];
-        blur_strip<M, KH>(Yb, col, LD, rs + KH, 0, nrow + 2 * KH, s_gy, out);
+        const int col = w % M, rs = (w / M) * NB;
+        float out[NB];
+        blur_strip<NB, KH>(Yb, col, LD, rs + KH, 0, nrow + 2 * KH, s_gy, out);
 #pragma unroll
-        for (int o = 0; o < E; ++o) {
+        for (int o = 0; o < NB; ++o) {
           const int lr = rs + o;
           if (lr >= nrow) break;
           const int gr = r0 + lr;
@@ -448,14 +453,19 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
       const int ow = ln / RPO;
       const uint32_t dst = map_rank(recv_s + (uint32_t)((rank * RPO + ln - ow * RPO) * LDN * 8), (unsigned)ow);
       if constexpr (TM) {
+        // this line's object values and (own rows) denominator partials, all loads in flight at once
+        float2 o[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) o[j] = On[(size_t)ln * a.obj_w + tp[q] + G * j];
+        const bool own = ln >= r0 && ln < r1;
+        float dold[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) dold[j] = (own && !first) ? dacc[ln * M + tp[q] + G * j] : 0.f;
 #pragma unroll
         for (int h = 0; h < E / 4; ++h) {
           float pr[8], ac[8];
           tmem_ld8(t_lane + colP + 2 * (q * E + 4 * h), pr);
           if (!first) tmem_ld8(t_lane + colA + 2 * (q * E + 4 * h), ac);
-          float2 o[4];
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) o[jj] = On[(size_t)ln * a.obj_w + tp[q] + G * (4 * h + jj)];
           tmem_wait_ld();
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
@@ -464,15 +474,12 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
             float2 psi_new = cscale(v[q][j], inv_m2);
             if (!NEAR && ((ln + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
             const float2 p = make_float2(pr[2 * jj], pr[2 * jj + 1]);
-            const float2 dpsi = csub(psi_new, cmul(p, o[jj]));
+            const float2 dpsi = csub(psi_new, cmul(p, o[j]));
             st_cluster_f2(dst + 8u * x, cconjmul(p, dpsi));
-            const float2 pc = cconjmul(o[jj], dpsi);
+            const float2 pc = cconjmul(o[j], dpsi);
             ac[2 * jj] = first ? pc.x : ac[2 * jj] + pc.x;
             ac[2 * jj + 1] = first ? pc.y : ac[2 * jj + 1] + pc.y;
-            if (ln >= r0 && ln < r1) {
-              const int qi = ln * M + x;
-              dacc[qi] = first ? cabs2(o[jj]) : dacc[qi] + cabs2(o[jj]);
-            }
+            if (own) dacc[ln * M + x] = dold[j] + cabs2(o[j]);
           }
           tmem_st8(t_lane + colA + 2 * (q * E + 4 * h), ac);
         }
