@@ -595,6 +595,9 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
 ptycho_status ptycho_error_batch(ptycho_plan_t pl, double* nrmse_last) {
   if (!pl || pl->members.empty() || !nrmse_last) return fail(PTYCHO_EINVAL, "not a batch plan or NULL output");
   PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
+  bool timed_out = false;
+  PT_CUDA(fused_timed_out(&timed_out), "read wait status");
+  if (timed_out) return fail(PTYCHO_ETIMEOUT, "a bounded device wait gave up; results are not valid");
   bool finite = true;
   for (size_t b = 0; b < pl->members.size(); ++b) {
     const ptycho_plan_s* m = pl->members[b];
@@ -613,6 +616,9 @@ ptycho_status ptycho_error(ptycho_plan_t pl, double* nrmse_last) {
   if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "batch plans report through ptycho_error_batch");
   PT_CUDA(cudaStreamSynchronize(pl->stream), "stream sync");
   if (pl->runs == 0) return fail(PTYCHO_EINVAL, "no iteration has run");
+  bool timed_out = false;
+  PT_CUDA(fused_timed_out(&timed_out), "read wait status");
+  if (timed_out) return fail(PTYCHO_ETIMEOUT, "a bounded device wait gave up; results are not valid");
   double e = 0.0;
   PT_CUDA(cudaMemcpy(&e, pl->d_errhist + (pl->runs - 1) % kErrHistory, sizeof(double), cudaMemcpyDeviceToHost),
           "copy error");

@@ -276,6 +276,9 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   if (errors && n_iter > 0)
     PS_CUDA(cudaMemcpyAsync(errors, ua.errhist, sizeof(double) * n_iter, cudaMemcpyDeviceToHost, s), "copy errors");
   PS_CUDA(cudaStreamSynchronize(s), "stream sync");
+  bool timed_out = false;
+  PS_CUDA(fused_timed_out(&timed_out), "read wait status");
+  if (timed_out) return capi_fail(PTYCHO_ETIMEOUT, "a bounded device wait gave up; results are not valid");
   capi_clear_error();
   return PTYCHO_OK;
 }

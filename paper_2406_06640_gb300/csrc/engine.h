@@ -39,6 +39,8 @@ struct FusedArgs {
 cudaError_t launch_fused(int M, const FusedArgs& a, int slots, cudaStream_t s);
 cudaError_t fused_max_slots(int M, int K, int* slots);
 size_t fused_smem_bytes(int M);
+// true if a bounded device wait of the fused kernel gave up since the last call (clears the flag; synchronous)
+cudaError_t fused_timed_out(bool* out);
 
 // staged path for M = 256 (big.cu): a chunk of C positions x K modes in the scratch W
 constexpr int kBigM = 256;

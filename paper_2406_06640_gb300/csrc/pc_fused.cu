@@ -31,6 +31,9 @@
 
 namespace ptycho {
 
+// set when a bounded device wait of the fused kernel gave up (read and cleared by fused_timed_out)
+__device__ int g_fused_timeout;
+
 __device__ __forceinline__ unsigned cluster_ctarank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -44,6 +47,41 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t addr, unsigned rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
   return r;
+}
+// ---- mbarrier + bulk (TMA) copies, waits bounded by the global timer
+constexpr unsigned long long kFusedWaitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > kFusedWaitNs) return false;
+  }
+}
+// global -> own shared memory, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 __device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
   float v;
@@ -131,7 +169,7 @@ struct FusedSmem {
   static constexpr size_t IBUF = ((size_t)max_slot_rows(M) * LD * 4 + 15) / 16 * 16;
   static constexpr size_t TWT = ((size_t)Tile<M>::G * Tile<M>::LDW * 8 + 15) / 16 * 16;  // twiddle table
   static constexpr size_t HQ = (size_t)M * 8;                                             // Fresnel factors
-  static constexpr size_t TAPS = 2 * kMaxTaps * 4 + 8;
+  static constexpr size_t TAPS = 2 * kMaxTaps * 4 + 8 + 16;  // taps, TMEM address, mbarrier (16-byte aligned)
   static constexpr size_t BYTES = CBUF + IBUF + TWT + HQ + TAPS;
   static_assert(BYTES <= 232448, "shared memory budget of one CTA");
 };
@@ -286,6 +324,16 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
   const uint32_t ibuf_s = smem_addr(ibuf), z_s = smem_addr(Z), yb_s = smem_addr(Yb), recv_s = smem_addr(recv);
   const float eps = a.eps;
   float err_s = 0.f, err_c = 0.f;  // compensated per-thread sum of (Ihat - I)^2 over own rows
+  // staging of the own rows' measured data behind Z and Yb in the exchange buffer, when it fits
+  const size_t meas_off = ((size_t)(M + nrow + 2 * KH) * LD * 4 + 15) / 16 * 16;
+  const bool pre = meas_off + (size_t)2 * nrow * M * 4 <= SM::CBUF;
+  const float* s_meas = reinterpret_cast<const float*>(smem + meas_off);
+  const uint32_t meas_s = smem_addr(smem + meas_off);
+  const uint32_t bar_s = smem_addr(s_gy + kMaxTaps) + 8u;  // after the TMEM address word; 16-byte aligned
+  uint32_t mphase = 0;
+  bool waits_ok = true;
+  if (tid == 0) mbar_init(bar_s, 1);
+  __syncthreads();
 
   for (int n = slot; n < a.N; n += nslots) {
     const bool first = (n == slot);
@@ -342,6 +390,17 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
 #pragma unroll
         for (int j = 0; j < E; ++j) v[q][j] = cscale(v[q][j], inv_m2);
     }
+    // ---- own rows of sqrt(I) and I into free shared memory (bulk copies, used in step 4); the
+    // exchange buffer is free here (the propagation ended with a CTA barrier)
+    if (pre && tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const uint32_t bytes = (uint32_t)(nrow * M * 4);
+      mbar_arrive_expect_tx(bar_s, 2u * bytes);
+      if (bytes) {
+        bulk_g2s(meas_s, a.sqrtI + ((size_t)n * M + r0) * M, bytes, bar_s);
+        bulk_g2s(meas_s + bytes, a.I + ((size_t)n * M + r0) * M, bytes, bar_s);
+      }
+    }
     // ---- (1) push |Psi_k|^2 into slot `rank` of the row owner's buffer
 #pragma unroll
     for (int q = 0; q < V; ++q)
@@ -392,6 +451,13 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     {
       const float* In = a.I + (size_t)n * M * M;
       const float* Sn = a.sqrtI + (size_t)n * M * M;
+      if (pre && waits_ok) {
+        if (!mbar_wait_bounded(bar_s, mphase)) {
+          waits_ok = false;  // report once and stop waiting; the results are flagged invalid
+          atomicExch(&g_fused_timeout, 1);
+        }
+        mphase ^= 1u;
+      }
       const int nstrip = (nrow + NB - 1) / NB;
       for (int w = tid; w < M * nstrip; w += TR) {
         const int col = w % M, rs = (w / M) * NB;
@@ -403,7 +469,8 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
           if (lr >= nrow) break;
           const int gr = r0 + lr;
           const float acc = out[o];
-          const float sq = Sn[gr * M + col];
+          const float sq = pre ? s_meas[lr * M + col] : Sn[gr * M + col];
+          const float im = pre ? s_meas[(nrow + lr) * M + col] : In[gr * M + col];
           float ihat, R;
           if (a.blur_intensity) {
             ihat = acc;
@@ -412,7 +479,7 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
             ihat = acc * acc;
             R = __fdividef(sq, acc + eps);
           }
-          const float d = ihat - In[gr * M + col];
+          const float d = ihat - im;
           const float y = fmaf(d, d, -err_c);
           const float tt = err_s + y;
           err_c = (tt - err_s) - y;
@@ -543,6 +610,18 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     }
     if (tid == 0) a.errpart[(size_t)slot * K + rank] = red[0];
   }
+}
+
+cudaError_t fused_timed_out(bool* out) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&h, g_fused_timeout, sizeof(int));
+  if (e != cudaSuccess) return e;
+  *out = h != 0;
+  if (h) {
+    const int z = 0;
+    e = cudaMemcpyToSymbol(g_fused_timeout, &z, sizeof(int));
+  }
+  return e;
 }
 
 size_t fused_smem_bytes(int M) {
