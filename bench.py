@@ -207,9 +207,14 @@ def traffic_record(kernel_tag):
 
 
 def kernel_source_hash():
+    """Hash of what the fused kernel is compiled from: fft.cuh, pc_fused.cu and its argument struct."""
     h = hashlib.sha256()
-    for f in ("fft.cuh", "pc_fused.cu", "engine.h"):
-        h.update(open(os.path.join(ROOT, "paper_2406_06640_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2406_06640_gb300", "csrc")
+    for f in ("fft.cuh", "pc_fused.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    hdr = open(os.path.join(csrc, "engine.h")).read()
+    i = hdr.find("struct FusedArgs")
+    h.update(hdr[i:hdr.find("};", i)].encode() if i >= 0 else b"")
     return h.hexdigest()
 
 
