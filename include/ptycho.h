@@ -64,6 +64,7 @@ typedef enum {
 
 enum { PTYCHO_FARFIELD = 0, PTYCHO_NEARFIELD = 1 };
 enum { PTYCHO_BLUR_AMPLITUDE = 0 /* Eq. 6 */, PTYCHO_BLUR_INTENSITY = 1 /* Eq. 2 */ };
+enum { PTYCHO_STEP_NORMALISED = 0, PTYCHO_STEP_RPIE = 1 };
 
 typedef struct {
   int32_t M;            /* probe = box = detector side, power of two, 8..256 */
@@ -85,6 +86,14 @@ typedef struct {
   int32_t n_windows;             /* number of complex-constraint windows */
   const int32_t* windows;        /* host, 2 * n_windows: [first, last], 1-based inclusive */
   int32_t start_iteration;       /* number of the first iteration (resume), >= 1 */
+  /* Step rule of the object / probe update (zero-initialised: the normalised rule above).
+   * PTYCHO_STEP_RPIE uses the regularised denominator of the rPIE family (Sec. 5, Fig. 11c)
+   *   O   += beta_obj   N_O / ((1 - a_O) D_O + a_O max D_O),
+   *   P_k += beta_probe N_P / ((1 - a_P) D_P + a_P max D_P),  a in [0, 1];
+   * a = 1 is the ePIE-style max-normalised step, a = 0 the plain normalised step without a
+   * floor. Pixels with a zero denominator are left unchanged under both rules. */
+  int32_t step_rule;             /* PTYCHO_STEP_NORMALISED (0) or PTYCHO_STEP_RPIE (1) */
+  double rpie_alpha_obj, rpie_alpha_probe;
 } ptycho_params;
 
 /* Build a plan on the current CUDA device.

@@ -80,6 +80,9 @@ class Params:
     cbar_max: float = 10.0
     windows: Sequence = ()
     start_iteration: int = 1
+    step_rule: str = "normalised"  # "normalised" | "rpie"
+    rpie_alpha_obj: float = 0.0
+    rpie_alpha_probe: float = 0.0
 
     @classmethod
     def from_dict(cls, d):
@@ -199,12 +202,25 @@ def in_window(t: int, windows) -> bool:
 # one iteration and the driver
 # ----------------------------------------------------------------------------------------
 
-def _normalised_step(beta, num, den, delta):
-    """beta num / (den + delta max den); pixels that no box reaches (den = 0) get no step."""
+def _normalised_step(beta, num, den, c_den, c_max):
+    """beta num / (c_den den + c_max max den); pixels that no box reaches (den = 0) get no step.
+
+    The normalised rule (reading 4) is (c_den, c_max) = (1, delta). The rPIE family (Sec. 5,
+    Fig. 11c) regularises the denominator as (1 - alpha) den + alpha max den, i.e.
+    (c_den, c_max) = (1 - alpha, alpha); alpha = 1 gives the ePIE-style max-normalised step."""
     out = np.zeros(num.shape, np.complex128)
     reached = den > 0
-    out[reached] = beta * num[reached] / (den[reached] + delta * den.max())
+    out[reached] = beta * num[reached] / (c_den * den[reached] + c_max * den.max())
     return out
+
+
+def step_coefficients(prm: "Params"):
+    """(c_den, c_max) of the object step and of the probe step."""
+    if prm.step_rule == "rpie":
+        return (1.0 - prm.rpie_alpha_obj, prm.rpie_alpha_obj), (1.0 - prm.rpie_alpha_probe, prm.rpie_alpha_probe)
+    if prm.step_rule != "normalised":
+        raise ValueError(f"unknown step rule {prm.step_rule!r}")
+    return (1.0, prm.delta_obj), (1.0, prm.delta_probe)
 
 
 def iteration(I: np.ndarray, positions: np.ndarray, O: np.ndarray, P: np.ndarray, prm: Params,
@@ -230,9 +246,10 @@ def iteration(I: np.ndarray, positions: np.ndarray, O: np.ndarray, P: np.ndarray
         DO[y:y + M, x:x + M] += P2
         NP += np.conj(o)[None] * dpsi
         DP += np.abs(o) ** 2
-    O_new = O + _normalised_step(prm.beta_obj, NO, DO, prm.delta_obj)
+    c_obj, c_probe = step_coefficients(prm)
+    O_new = O + _normalised_step(prm.beta_obj, NO, DO, *c_obj)
     if t >= prm.probe_update_start:
-        P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, prm.delta_probe) for k in range(K)])
+        P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, *c_probe) for k in range(K)])
     else:
         P_new = P.copy()
     if in_window(t, prm.windows):

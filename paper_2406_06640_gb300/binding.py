@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "PTYCHO_OK", 1: "PTYCHO_EINVAL", 2: "PTYCHO_ENOMEM", 3: "PTYC
                 4: "PTYCHO_EUNSUPPORTED", 5: "PTYCHO_ENUMERIC", 6: "PTYCHO_ETIMEOUT"}
 FARFIELD, NEARFIELD = 0, 1
 BLUR_AMPLITUDE, BLUR_INTENSITY = 0, 1
+STEP_NORMALISED, STEP_RPIE = 0, 1
 
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
@@ -49,6 +50,7 @@ class PtychoParams(ctypes.Structure):
         ("cbar_min", ctypes.c_double), ("cbar_max", ctypes.c_double),
         ("n_windows", ctypes.c_int32), ("windows", ctypes.POINTER(ctypes.c_int32)),
         ("start_iteration", ctypes.c_int32),
+        ("step_rule", ctypes.c_int32), ("rpie_alpha_obj", ctypes.c_double), ("rpie_alpha_probe", ctypes.c_double),
     ]
 
 
@@ -170,6 +172,12 @@ def make_params(d: dict) -> tuple:
     p.n_windows = len(wins) // 2
     p.windows = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)) if wins else None
     p.start_iteration = int(d.get("start_iteration", 1))
+    rule = d.get("step_rule", STEP_NORMALISED)
+    if isinstance(rule, str):
+        rule = {"normalised": STEP_NORMALISED, "rpie": STEP_RPIE}[rule]
+    p.step_rule = int(rule)
+    p.rpie_alpha_obj = float(d.get("rpie_alpha_obj", 0.0))
+    p.rpie_alpha_probe = float(d.get("rpie_alpha_probe", 0.0))
     return p, arr
 
 

@@ -140,7 +140,27 @@ static ptycho_status validate(const ptycho_params* p) {
     if (p->windows[2 * i] < 1 || p->windows[2 * i] > p->windows[2 * i + 1])
       return fail(PTYCHO_EINVAL, "windows must be [first, last] with 1 <= first <= last");
   if (p->start_iteration < 1) return fail(PTYCHO_EINVAL, "start_iteration must be >= 1");
+  if (p->step_rule != PTYCHO_STEP_NORMALISED && p->step_rule != PTYCHO_STEP_RPIE)
+    return fail(PTYCHO_EINVAL, "step_rule must be PTYCHO_STEP_NORMALISED or PTYCHO_STEP_RPIE");
+  if (p->step_rule == PTYCHO_STEP_RPIE &&
+      !(p->rpie_alpha_obj >= 0 && p->rpie_alpha_obj <= 1 && p->rpie_alpha_probe >= 0 && p->rpie_alpha_probe <= 1))
+    return fail(PTYCHO_EINVAL, "rPIE weights must lie in [0, 1]");
   return PTYCHO_OK;
+}
+
+// denominator coefficients of the step rule: step = beta num / (cd d + cmax max d)
+static void step_coefficients(const ptycho_params& p, UpdateArgs& u) {
+  if (p.step_rule == PTYCHO_STEP_RPIE) {
+    u.cd_obj = (float)(1.0 - p.rpie_alpha_obj);
+    u.cmax_obj = (float)p.rpie_alpha_obj;
+    u.cd_probe = (float)(1.0 - p.rpie_alpha_probe);
+    u.cmax_probe = (float)p.rpie_alpha_probe;
+  } else {
+    u.cd_obj = 1.f;
+    u.cmax_obj = (float)p.delta_obj;
+    u.cd_probe = 1.f;
+    u.cmax_probe = (float)p.delta_probe;
+  }
 }
 
 static bool is_device_pointer(const void* ptr) {
@@ -352,8 +372,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ua.errden = pl->errden;
   ua.beta_obj = (float)p.beta_obj;
   ua.beta_probe = (float)p.beta_probe;
-  ua.delta_obj = (float)p.delta_obj;
-  ua.delta_probe = (float)p.delta_probe;
+  step_coefficients(p, ua);
 
   ca.pos = d_pos;
   ca.N = N;
@@ -715,6 +734,7 @@ std::vector<int> coverage_counts(const std::vector<int2>& pos, int M, int obj_h,
   return out;
 }
 ptycho_status capi_validate(const ptycho_params* p) { return validate(p); }
+void capi_step_coefficients(const ptycho_params* p, UpdateArgs* u) { step_coefficients(*p, *u); }
 ptycho_status capi_fail(ptycho_status s, const std::string& msg) { return fail(s, msg); }
 ptycho_status capi_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 std::vector<double> capi_taps(double sigma, int h) { return taps_1d(sigma, h); }

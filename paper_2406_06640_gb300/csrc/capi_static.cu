@@ -22,6 +22,7 @@
 
 namespace ptycho {
 ptycho_status capi_validate(const ptycho_params* p);
+void capi_step_coefficients(const ptycho_params* p, UpdateArgs* u);
 ptycho_status capi_fail(ptycho_status s, const std::string& msg);
 ptycho_status capi_cuda_fail(cudaError_t e, const char* what);
 std::vector<double> capi_taps(double sigma, int h);
@@ -250,8 +251,7 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   ua.errden = h_sums[1];
   ua.beta_obj = (float)p->beta_obj;
   ua.beta_probe = (float)p->beta_probe;
-  ua.delta_obj = (float)p->delta_obj;
-  ua.delta_probe = (float)p->delta_probe;
+  capi_step_coefficients(p, &ua);
   ca.O = static_cast<float2*>(object);
   ca.pos = dpos;
   ca.N = N;

@@ -102,7 +102,8 @@ struct UpdateArgs {
   int probe_blocks;
   double* errhist; double errden;
   unsigned long long* run_counter;  // device: iterations finished; E goes to errhist[counter % kErrHistory]
-  float beta_obj, beta_probe, delta_obj, delta_probe;
+  // step = beta num / (c_d d + c_max max d): normalised rule (1, delta), rPIE rule (1 - a, a)
+  float beta_obj, beta_probe, cd_obj, cmax_obj, cd_probe, cmax_probe;
   int update_probe;
 };
 cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_obj_apply(const UpdateArgs u) {
   const int X = blockIdx.x * kObjTile + threadIdx.x;
   const int Y0 = blockIdx.y * kObjTile + threadIdx.y;
   if (X >= u.obj_w) return;
-  const float floor_d = u.delta_obj * maxd;
+  const float floor_d = u.cmax_obj * maxd;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int Y = Y0 + 8 * i;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_obj_apply(const UpdateArgs u) {
     const size_t q = (size_t)Y * u.obj_w + X;
     const float d = u.do_part[q];
     if (d > 0.f) {
-      const float w = u.beta_obj / (d + floor_d);
+      const float w = u.beta_obj / fmaf(u.cd_obj, d, floor_d);
       const float2 num = u.no_part[q];
       float2 o = u.O[q];
       o.x = fmaf(w, num.x, o.x);
@@ -257,7 +257,7 @@ __global__ void k_probe_apply(const UpdateArgs u) {
   if (p >= MM) return;
   const float d = u.dp_sum[p];
   if (d > 0.f) {
-    const float w = u.beta_probe / (d + u.delta_probe * maxd);
+    const float w = u.beta_probe / fmaf(u.cd_probe, d, u.cmax_probe * maxd);
     const size_t q = (size_t)blockIdx.y * MM + p;
     const float2 num = u.np_sum[q];
     float2 pr = u.P[q];

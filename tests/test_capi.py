@@ -70,7 +70,8 @@ def _plan_status(**over):
     (dict(sigma1=-1.0), 1), (dict(kernel_size=10), 1), (dict(kernel_size=33), 1), (dict(alpha1=1.5), 1),
     (dict(cbar_min=0.0), 1), (dict(cbar_min=2.0, cbar_max=1.0), 1), (dict(windows=[(0, 3)]), 1),
     (dict(windows=[(5, 4)]), 1), (dict(start_iteration=0), 1), (dict(delta_obj=-1.0), 1),
-    (dict(eps_mod=float("nan")), 1),
+    (dict(eps_mod=float("nan")), 1), (dict(step_rule=2), 1), (dict(step_rule="rpie", rpie_alpha_obj=1.5), 1),
+    (dict(step_rule="rpie", rpie_alpha_probe=-0.1), 1),
 ])
 def test_validation_rejects_bad_requests(over, expect):
     st, msg = _plan_status(**over)

@@ -88,6 +88,18 @@ def test_far_field_modes_intensity_blur_ragged_tiles():
     check(p, prm, 5)
 
 
+@pytest.mark.parametrize("a_obj,a_probe,n_iter", [(0.2, 0.8, 30), (1.0, 1.0, 10)])
+def test_rpie_step_rule(a_obj, a_probe, n_iter):
+    """The rPIE denominator (1 - a) D + a max D (a = 1: the ePIE-style step), same engine otherwise."""
+    p = make_problem(0)
+    check(p, dict(p.params, step_rule="rpie", rpie_alpha_obj=a_obj, rpie_alpha_probe=a_probe), n_iter)
+
+
+def test_rpie_step_rule_mixed_state_near_field():
+    p = make_problem(0, scan_side=4, obj_side=128, M=64, K=2, geometry="near", sigma=2.0)
+    check(p, dict(p.params, sigma1=2.0, sigma2=2.0, step_rule="rpie", rpie_alpha_obj=0.5, rpie_alpha_probe=0.1), 5)
+
+
 def test_near_field_two_modes():
     p = make_problem(0, scan_side=4, obj_side=128, M=64, K=2, geometry="near", sigma=2.0)
     check(p, dict(p.params, sigma1=2.0, sigma2=2.0), 5)

@@ -272,6 +272,57 @@ def test_p6_single_position_update_is_the_projection():
     assert np.max(np.abs(O * P1[0] - psi_proj)) < 1e-10 * np.max(np.abs(psi_proj))
 
 
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_p6b_rpie_single_position_closed_forms(alpha):
+    """rPIE step (Sec. 5, Fig. 11c), N = 1, K = 1, sigma = 0, object and probe steps both rPIE.
+    alpha = 0: the denominator is |P|^2 alone, so P o_new = psi' (the projection);
+    alpha = 1: the ePIE step o_new = o + conj(P) (psi' - psi) / max|P|^2 (and the same for P)."""
+    rng = _rng(13)
+    M = 16
+    O = (0.5 + rng.random((M, M))) * np.exp(1j * rng.random((M, M)))
+    P = _crandn(rng, 1, M, M)
+    I = rng.random((1, M, M)) * 10
+    prm = pe.Params(M=M, K=1, N=1, obj_h=M, obj_w=M, sigma1=0, sigma2=0, eps_mod=1e-300, step_rule="rpie",
+                    rpie_alpha_obj=alpha, rpie_alpha_probe=alpha)
+    O1, P1, _ = pe.iterate(I, np.array([[0, 0]]), O, P, prm, 1)
+    psi = P[0] * O
+    Psi = np.fft.fft2(psi)
+    psi_proj = np.fft.ifft2(np.sqrt(np.fft.ifftshift(I[0])) * np.exp(1j * np.angle(Psi)))
+    tol = 1e-10 * np.max(np.abs(psi_proj))
+    if alpha == 0.0:
+        assert np.max(np.abs(P[0] * O1 - psi_proj)) < tol
+        assert np.max(np.abs(O * P1[0] - psi_proj)) < tol
+    else:
+        d = psi_proj - psi
+        assert np.max(np.abs(O1 - (O + np.conj(P[0]) * d / np.max(np.abs(P[0]) ** 2)))) < tol
+        assert np.max(np.abs(P1[0] - (P[0] + np.conj(O) * d / np.max(np.abs(O) ** 2)))) < tol
+
+
+def test_p6c_rpie_is_a_rescaled_normalised_step_and_keeps_the_fixed_point():
+    """(1 - a) D + a max D = (1 - a) (D + a / (1 - a) max D): an rPIE step with weight a and step
+    beta equals the normalised step with delta = a / (1 - a) and step beta / (1 - a); and any rule
+    leaves consistent data fixed."""
+    rng = _rng(14)
+    M, side = 16, 28
+    O = (0.5 + rng.random((side, side))) * np.exp(1j * rng.random((side, side)))
+    P = _crandn(rng, 2, M, M)
+    pos = np.array([(0, 0), (0, 12), (12, 0), (12, 12), (6, 6)])
+    base = dict(M=M, K=2, N=len(pos), obj_h=side, obj_w=side, sigma1=1.0, sigma2=0.6, eps_mod=1e-300)
+    I = rng.random((len(pos), M, M)) * 5
+    a_o, a_p = 0.3, 0.6
+    r = pe.iterate(I, pos, O, P, pe.Params(**base, step_rule="rpie", rpie_alpha_obj=a_o, rpie_alpha_probe=a_p), 1)
+    n_o = pe.iterate(I, pos, O, P, pe.Params(**base, beta_obj=1 / (1 - a_o), delta_obj=a_o / (1 - a_o),
+                                            beta_probe=1 / (1 - a_p), delta_probe=a_p / (1 - a_p)), 1)
+    assert np.max(np.abs(r[0] - n_o[0])) < 1e-12 * np.max(np.abs(r[0]))
+    assert np.max(np.abs(r[1] - n_o[1])) < 1e-12 * np.max(np.abs(r[1]))
+    prm = pe.Params(**base, step_rule="rpie", rpie_alpha_obj=0.5, rpie_alpha_probe=1.0)
+    Ic = _consistent_data(O, P, pos, prm)
+    O1, P1, E = pe.iterate(Ic, pos, O, P, prm, 1)
+    assert np.max(np.abs(O1 - O)) < 1e-12 and np.max(np.abs(P1 - P)) < 1e-12 and E[0] < 1e-12
+    with pytest.raises(ValueError):
+        pe.iterate(I, pos, O, P, pe.Params(**base, step_rule="sequential"), 1)
+
+
 # ------------------------------------------------------------------------ P7 / P8: coherent reduction, modes
 
 def _minimal_coherent_engine(I, pos, O, P, n_iter, delta):
