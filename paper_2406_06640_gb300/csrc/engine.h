@@ -76,6 +76,10 @@ struct GemmArgs {
   // pixel p of the NHWC tensor A (batch x H x W x Cin), k = tap * Cin + c,
   // tap = 3 (dy + 1) + (dx + 1); K may exceed 9 Cin (zero columns)
   int conv, H, W, Cin;
+  // transposed implicit operand of a weight gradient: row k = tap * Cin + c of A over pixels p is
+  // XT3[dx + 1][c][p + dy W] (zero where row y + dy leaves the image; zero for k >= 9 Cin), XT3 the
+  // three x-shifted channel-major copies of the NHWC activation (Mpix pixels, W % 8 == 0)
+  int convT, Mpix;
   // split-K (mode 0 only): blockIdx.z walks K columns [z kc, min(K, (z + 1) kc)) and stores
   // its partial product at D + z dsplit; 1 = no split
   int ksplit, kc;

@@ -54,31 +54,65 @@ __global__ void k_input(const float* x, bf16* out, size_t npix) {
     out[i] = __float2bfloat16((i & 7) == 0 ? x[i >> 3] : 0.f);
 }
 
+// 8 bf16 <-> 8 floats
+__device__ __forceinline__ void bf8_to_f(const uint4& v, float (&f)[8]) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 t = __bfloat1622float2(h[i]);
+    f[2 * i] = t.x;
+    f[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ uint4 f_to_bf8(const float (&f)[8]) {
+  uint4 v;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+  return v;
+}
+
+// 2 x 2 average pooling, 8 channels (16 bytes) per thread; C % 8 == 0
 __global__ void k_avgpool2(const bf16* in, bf16* out, int n, int H, int W, int C) {
-  const size_t total = (size_t)n * (H / 2) * (W / 2) * C;
+  const int C8 = C / 8;
+  const size_t total = (size_t)n * (H / 2) * (W / 2) * C8;
+  const uint4* in4 = reinterpret_cast<const uint4*>(in);
+  uint4* out4 = reinterpret_cast<uint4*>(out);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C;
-    size_t r = i / C;
+    const int c = i % C8;
+    size_t r = i / C8;
     const int x = r % (W / 2);
     r /= (W / 2);
     const int y = r % (H / 2);
     const int b = r / (H / 2);
-    const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * C + c;
-    const float s = __bfloat162float(in[base]) + __bfloat162float(in[base + C]) +
-                    __bfloat162float(in[base + (size_t)W * C]) + __bfloat162float(in[base + (size_t)W * C + C]);
-    out[i] = __float2bfloat16(0.25f * s);
+    const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * C8 + c;
+    float a[8], t[8];
+    bf8_to_f(in4[base], a);
+    bf8_to_f(in4[base + C8], t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += t[k];
+    bf8_to_f(in4[base + (size_t)W * C8], t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += t[k];
+    bf8_to_f(in4[base + (size_t)W * C8 + C8], t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.25f * (a[k] + t[k]);
+    out4[i] = f_to_bf8(a);
   }
 }
 
-// q = [up2(a), skip]: a (n, H/2, W/2, Ca), skip (n, H, W, Cs) -> q (n, H, W, Ca + Cs)
+// q = [up2(a), skip]: a (n, H/2, W/2, Ca), skip (n, H, W, Cs) -> q (n, H, W, Ca + Cs); 8 channels per thread
 __global__ void k_up2_concat(const bf16* a, const bf16* skip, bf16* q, int n, int H, int W, int Ca, int Cs) {
-  const int Cq = Ca + Cs;
-  const size_t total = (size_t)n * H * W * Cq;
+  const int A8 = Ca / 8, S8 = Cs / 8, Q8 = A8 + S8;
+  const size_t total = (size_t)n * H * W * Q8;
+  const uint4* a4 = reinterpret_cast<const uint4*>(a);
+  const uint4* s4 = reinterpret_cast<const uint4*>(skip);
+  uint4* q4 = reinterpret_cast<uint4*>(q);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % Cq;
-    const size_t p = i / Cq;
+    const int c = i % Q8;
+    const size_t p = i / Q8;
     const int x = p % W, y = (p / W) % H, b = p / ((size_t)W * H);
-    q[i] = c < Ca ? a[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * Ca + c] : skip[p * Cs + (c - Ca)];
+    q4[i] = c < A8 ? a4[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * A8 + c] : s4[p * S8 + (c - A8)];
   }
 }
 
@@ -154,6 +188,43 @@ __global__ void k_im2colT(const bf16* X, bf16* colT, int n, int H, int W, int Ci
   }
 }
 
+// XT3[d][c][p] = X[p + d - 1][c] when pixel x + d - 1 lies in [0, W), else 0 (d = 0, 1, 2);
+// X (Mpix, Cin) NHWC; 32 pixels x 32 channels per block through shared memory
+__global__ void k_shift3T(const bf16* X, bf16* XT3, int Mpix, int W, int Cin) {
+  __shared__ bf16 tile[34][33];
+  const int p0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y * 32 + threadIdx.x; i < 34 * 32; i += 256) {
+    const int j = i / 32, c = c0 + i % 32, p = p0 - 1 + j;
+    tile[j][i % 32] = (p >= 0 && p < Mpix && c < Cin) ? X[(size_t)p * Cin + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  const int j = threadIdx.x, p = p0 + j, x = p % W;
+  for (int cc = threadIdx.y; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    if (c >= Cin || p >= Mpix) continue;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int xx = x + d - 1;
+      XT3[((size_t)d * Cin + c) * Mpix + p] = (xx >= 0 && xx < W) ? tile[j + d][cc] : __float2bfloat16(0.f);
+    }
+  }
+}
+
+// out[o] = sum over p of dYT[o][p] in a fixed order (one block per output channel)
+__global__ void k_bias_grad(const bf16* dYT, int M, float* out) {
+  __shared__ float red[256];
+  const int o = blockIdx.x;
+  float s = 0.f;
+  for (int p = threadIdx.x; p < M; p += 256) s += __bfloat162float(dYT[(size_t)o * M + p]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)o] = red[0];
+}
+
 // dst[c][r] = src[r][c], bf16, R x C
 __global__ void k_transpose(const bf16* src, bf16* dst, int R, int C) {
   __shared__ bf16 tile[32][33];
@@ -214,18 +285,21 @@ __global__ void k_loss(const float* out, const float* target, bf16* d_out, float
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0] * inv;
 }
 
-// sigma head, forward and backward, one block: g = mean_hw(a3), sigma = g . w7 + b7
-__global__ void k_sigma_head(const bf16* a3, const float* w7, const float* b7, const float* sigma_t, float lam,
-                             float* sigma, float* g, float* extra, float* gw7, float* gb7, float* loss_s, int n,
-                             int hw, int C8, int backward) {
-  __shared__ float ds[kMaxBatch];
-  for (int bc = threadIdx.x; bc < n * C8; bc += blockDim.x) {
-    const int b = bc / C8, c = bc % C8;
+// g[b][c] = mean over the hw pixels of a3[b, :, :, c]; one block per sample
+__global__ void k_sigma_pool(const bf16* a3, float* g, int hw, int C8) {
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < C8; c += blockDim.x) {
     float s = 0.f;
     for (int p = 0; p < hw; ++p) s += __bfloat162float(a3[((size_t)b * hw + p) * C8 + c]);
-    g[bc] = s / hw;
+    g[(size_t)b * C8 + c] = s / hw;
   }
-  __syncthreads();
+}
+
+// sigma head, forward and backward, one block (g from k_sigma_pool): sigma = g . w7 + b7
+__global__ void k_sigma_head(const float* w7, const float* b7, const float* sigma_t, float lam, float* sigma,
+                             const float* g, float* extra, float* gw7, float* gb7, float* loss_s, int n, int hw,
+                             int C8, int backward) {
+  __shared__ float ds[kMaxBatch];
   for (int b = threadIdx.x; b < n; b += blockDim.x) {
     float s = b7[0];
     for (int c = 0; c < C8; ++c) s += g[b * C8 + c] * w7[c];
@@ -340,7 +414,7 @@ struct ptycho_unet_s {
   // activations (bf16) and buffers
   bf16 *x, *a0, *p0, *a1, *p1, *a2, *p2, *a3, *q2, *a4, *q1, *a5;
   float *out, *g, *sigma, *extra, *loss_part, *loss_s;
-  bf16 *d_out, *dY, *dYT, *colT;
+  bf16 *d_out, *dY, *dYT, *colT, *xt3;
   float *dX, *skip1, *skip2;
   float* wpart;  // split-K partial weight gradients
   int* status;
@@ -397,6 +471,29 @@ cudaError_t gemm(ptycho_unet_s* u, const void* A, const void* B, void* D, int M,
   return launch_gemm_bf16(g, u->stream);
 }
 
+// weight-gradient contraction over the transposed shifted copies (GemmArgs::convT)
+cudaError_t gemm_wgrad_T(ptycho_unet_s* u, const Conv& L, const bf16* XT3, const bf16* dYT, float* D, int M, Split sp) {
+  GemmArgs g{};
+  g.A = reinterpret_cast<const uint16_t*>(XT3);
+  g.B = reinterpret_cast<const uint16_t*>(dYT);
+  g.D = D;
+  g.M = L.Kw;
+  g.Ntot = L.Cp;
+  g.K = M;
+  g.ldd = L.Cp;
+  g.mode = 0;
+  g.status = u->status;
+  g.ksplit = sp.ks;
+  g.kc = sp.kc;
+  g.dsplit = (size_t)L.Kw * L.Cp;
+  g.convT = 1;
+  g.Mpix = M;
+  g.H = L.H;
+  g.W = L.W;
+  g.Cin = L.Cin;
+  return launch_gemm_bf16(g, u->stream);
+}
+
 // forward of one convolution: out (n, H, W, Cp) bf16 with bias and ReLU, or fp32 without bias
 cudaError_t conv_forward(ptycho_unet_s* u, Conv& L, const bf16* in, bf16* out_bf16, float* out_f32) {
   const int M = u->nrun * L.H * L.W;
@@ -409,17 +506,21 @@ cudaError_t conv_forward(ptycho_unet_s* u, Conv& L, const bf16* in, bf16* out_bf
 cudaError_t conv_backward(ptycho_unet_s* u, Conv& L, const bf16* in, const bf16* dY, float* dX) {
   const int M = u->nrun * L.H * L.W;
   cudaStream_t s = u->stream;
-  k_im2colT<<<dim3((M + 31) / 32, L.Kw / 32), dim3(32, 8), 0, s>>>(in, u->colT, u->nrun, L.H, L.W, L.Cin, L.Kw);
   k_transpose<<<dim3((M + 31) / 32, (L.Cp + 31) / 32), dim3(32, 8), 0, s>>>(dY, u->dYT, M, L.Cp);
   const Split sp = wgrad_split(L.Kw, L.Cp, M);
+  const bool shifted = L.W % 8 == 0;  // transposed shifted copies (else the explicit neighbourhood matrix)
   cudaError_t e;
-  if (sp.ks > 1) {
-    e = gemm(u, u->colT, u->dYT, u->wpart, L.Kw, L.Cp, M, L.Cp, 0, nullptr, 0, nullptr, sp);
-    if (e != cudaSuccess) return e;
-    k_sum_splits<<<grid_for((size_t)L.Kw * L.Cp), 256, 0, s>>>(u->wpart, sp.ks, (size_t)L.Kw * L.Cp, L.gT);
-  } else {
-    e = gemm(u, u->colT, u->dYT, L.gT, L.Kw, L.Cp, M, L.Cp, 0, nullptr, 0, nullptr);
-  }
+  if (shifted)
+    k_shift3T<<<dim3(M / 32, (L.Cin + 31) / 32), dim3(32, 8), 0, s>>>(in, u->xt3, M, L.W, L.Cin);
+  else
+    k_im2colT<<<dim3((M + 31) / 32, L.Kw / 32), dim3(32, 8), 0, s>>>(in, u->colT, u->nrun, L.H, L.W, L.Cin, L.Kw);
+  float* D = sp.ks > 1 ? u->wpart : L.gT;
+  if (shifted) e = gemm_wgrad_T(u, L, u->xt3, u->dYT, D, M, sp);
+  else e = gemm(u, u->colT, u->dYT, D, L.Kw, L.Cp, M, L.Cp, 0, nullptr, 0, nullptr, sp);
+  if (e != cudaSuccess) return e;
+  if (sp.ks > 1) k_sum_splits<<<grid_for((size_t)L.Kw * L.Cp), 256, 0, s>>>(u->wpart, sp.ks, (size_t)L.Kw * L.Cp, L.gT);
+  // bias gradient (row 9 Cin of gT); the explicit matrix's row of ones already produced it
+  if (shifted) k_bias_grad<<<L.Cp, 256, 0, s>>>(u->dYT, M, L.gT + (size_t)9 * L.Cin * L.Cp);
   if (e != cudaSuccess || !dX) return e;
   Conv R = L;  // the data gradient gathers dY with Cp channels
   R.Cin = L.Cp;
@@ -444,15 +545,15 @@ static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev) {
         u->L[i].Kd);
   cudaError_t e;
   if ((e = conv_forward(u, u->L[0], u->x, u->a0, nullptr)) != cudaSuccess) return e;
-  k_avgpool2<<<grid_for(npx * C / 4), 256, 0, s>>>(u->a0, u->p0, n, S, S, C);
+  k_avgpool2<<<grid_for(npx * C / 32), 256, 0, s>>>(u->a0, u->p0, n, S, S, C);
   if ((e = conv_forward(u, u->L[1], u->p0, u->a1, nullptr)) != cudaSuccess) return e;
-  k_avgpool2<<<grid_for(npx * C / 8), 256, 0, s>>>(u->a1, u->p1, n, S / 2, S / 2, 2 * C);
+  k_avgpool2<<<grid_for(npx * C / 64), 256, 0, s>>>(u->a1, u->p1, n, S / 2, S / 2, 2 * C);
   if ((e = conv_forward(u, u->L[2], u->p1, u->a2, nullptr)) != cudaSuccess) return e;
-  k_avgpool2<<<grid_for(npx * C / 16), 256, 0, s>>>(u->a2, u->p2, n, S / 4, S / 4, 4 * C);
+  k_avgpool2<<<grid_for(npx * C / 128), 256, 0, s>>>(u->a2, u->p2, n, S / 4, S / 4, 4 * C);
   if ((e = conv_forward(u, u->L[3], u->p2, u->a3, nullptr)) != cudaSuccess) return e;
-  k_up2_concat<<<grid_for(npx * 12 * C / 16), 256, 0, s>>>(u->a3, u->a2, u->q2, n, S / 4, S / 4, 8 * C, 4 * C);
+  k_up2_concat<<<grid_for(npx * 12 * C / 128), 256, 0, s>>>(u->a3, u->a2, u->q2, n, S / 4, S / 4, 8 * C, 4 * C);
   if ((e = conv_forward(u, u->L[4], u->q2, u->a4, nullptr)) != cudaSuccess) return e;
-  k_up2_concat<<<grid_for(npx * 6 * C / 4), 256, 0, s>>>(u->a4, u->a1, u->q1, n, S / 2, S / 2, 4 * C, 2 * C);
+  k_up2_concat<<<grid_for(npx * 6 * C / 32), 256, 0, s>>>(u->a4, u->a1, u->q1, n, S / 2, S / 2, 4 * C, 2 * C);
   if ((e = conv_forward(u, u->L[5], u->q1, u->a5, nullptr)) != cudaSuccess) return e;
   if ((e = conv_forward(u, u->L[6], u->a5, nullptr, u->out)) != cudaSuccess) return e;
   const int Mo = n * (S / 2) * (S / 2);
@@ -466,7 +567,8 @@ static cudaError_t unet_backward(ptycho_unet_s* u, const float* target, const fl
   const int n = u->nrun, S = u->S, C = u->C;
   const int Mo = n * (S / 2) * (S / 2);
   k_loss<<<64, 256, 0, s>>>(u->out, target, u->d_out, u->loss_part, Mo);
-  k_sigma_head<<<1, kMaxBatch, 0, s>>>(u->a3, u->w7, u->b7, sigma_t, lam, u->sigma, u->g, u->extra, u->gw7, u->gb7,
+  k_sigma_pool<<<n, 256, 0, s>>>(u->a3, u->g, (S / 8) * (S / 8), 8 * C);
+  k_sigma_head<<<1, kMaxBatch, 0, s>>>(u->w7, u->b7, sigma_t, lam, u->sigma, u->g, u->extra, u->gw7, u->gb7,
                                   u->loss_s, n, (S / 8) * (S / 8), 8 * C, 1);
   cudaError_t e;
   // head and a5
@@ -494,7 +596,8 @@ static cudaError_t unet_backward(ptycho_unet_s* u, const float* target, const fl
 static cudaError_t unet_infer(ptycho_unet_s* u, const float* x, float* out2, float* sigma, int nvalid) {
   cudaError_t e = unet_forward(u, x);
   if (e != cudaSuccess) return e;
-  k_sigma_head<<<1, kMaxBatch, 0, u->stream>>>(u->a3, u->w7, u->b7, nullptr, 0.f, u->sigma, u->g, u->extra, u->gw7,
+  k_sigma_pool<<<u->nrun, 256, 0, u->stream>>>(u->a3, u->g, (u->S / 8) * (u->S / 8), 8 * u->C);
+  k_sigma_head<<<1, kMaxBatch, 0, u->stream>>>(u->w7, u->b7, nullptr, 0.f, u->sigma, u->g, u->extra, u->gw7,
                                                u->gb7, u->loss_s, u->nrun, (u->S / 8) * (u->S / 8), 8 * u->C, 0);
   const int Mo = nvalid * (u->S / 2) * (u->S / 2);
   if (out2) k_extract2<<<grid_for((size_t)Mo * 2), 256, 0, u->stream>>>(u->out, out2, Mo);
@@ -555,6 +658,9 @@ ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t s
       ((size_t)batch * (S / 8) * (S / 8)) % 128)
     return capi_fail(PTYCHO_EINVAL, "need 16 <= S <= 512, S % 16 == 0, C % 16 == 0, C <= 64, 1 <= batch <= 1024 and "
                                     "batch (S/8)^2 % 128 == 0");
+  // the largest activation (batch x S^2 x max(8, 1.5 C) elements) must be indexable by int
+  if ((double)batch * S * S * std::max(8.0, 1.5 * C) >= 2147483647.0)
+    return capi_fail(PTYCHO_EINVAL, "batch x S^2 x channels exceeds 2^31 elements");
   ptycho_unet_s* u = new (std::nothrow) ptycho_unet_s();
   if (!u) return capi_fail(PTYCHO_ENOMEM, "host allocation failed");
   u->S = S;
@@ -567,7 +673,7 @@ ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t s
   const int ci_t[7] = {1, C, 2 * C, 4 * C, 12 * C, 6 * C, 2 * C};
   const int co[7] = {C, 2 * C, 4 * C, 8 * C, 4 * C, 2 * C, 2};
   const int hs[7] = {S, S / 2, S / 4, S / 8, S / 4, S / 2, S / 2};
-  size_t colT_max = 0, wpart_max = 0;
+  size_t colT_max = 0, xt3_max = 0, wpart_max = 0;
   auto fail_alloc = [&](cudaError_t e) {
     const ptycho_status st = capi_cuda_fail(e, "unet allocation");
     delete u;
@@ -593,7 +699,8 @@ ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t s
         (e = u->alloc(&L.wb, (size_t)L.Cp * L.Kf)) != cudaSuccess ||
         (e = u->alloc(&L.wr, (size_t)L.Cin * L.Kd)) != cudaSuccess)
       return fail_alloc(e);
-    colT_max = std::max(colT_max, (size_t)L.Kw * batch * hs[i] * hs[i]);
+    if (hs[i] % 8) colT_max = std::max(colT_max, (size_t)L.Kw * batch * hs[i] * hs[i]);
+    else xt3_max = std::max(xt3_max, (size_t)3 * L.Cin * batch * hs[i] * hs[i]);
     const Split sp = wgrad_split(L.Kw, L.Cp, batch * hs[i] * hs[i]);
     wpart_max = std::max(wpart_max, sp.ks > 1 ? (size_t)sp.ks * L.Kw * L.Cp : (size_t)0);
     // He initialisation of the true weights (channels beyond the true counts stay zero)
@@ -639,6 +746,7 @@ ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t s
   UA(dY, px * C);
   UA(dYT, px * C);
   UA(colT, colT_max);
+  UA(xt3, xt3_max);
   UA(dX, std::max(px * C, px * 6 * C / 4));
   UA(skip1, px * 2 * C / 4);
   UA(skip2, px * 4 * C / 16);

@@ -7,15 +7,17 @@
 //   M % 128 == 0, N % 16 == 0 and 16 <= N <= 256, K % 64 == 0
 //   (optionally split along K over blockIdx.z into separate partial products)
 //
-// One CTA (128 threads) owns a 128 x N tile of D. K is walked in chunks of 64:
-// the chunk of A (128 x 64) and of B (N x 64) is copied into shared memory in
+// One CTA (256 threads) owns a 128 x N tile of D. K is walked in chunks of 64,
+// each copied by cp.async (16 bytes per copy) into one of S pipeline stages in
 // the no-swizzle K-major core-matrix layout (a core matrix = 8 rows x 16 bytes;
 // core matrix (row group g, k group q) at byte (g * 8 + q) * 128, so the
-// K-direction stride is 128 B and the row-group stride 1024 B); one thread
-// issues four tcgen05.mma.kind::f16 (K = 16 each) into the TMEM accumulator and
-// commits them to an mbarrier, which the CTA waits on before the next chunk
-// overwrites shared memory. The epilogue reads TMEM (each warp its 32 lanes =
-// 32 rows) and applies bias / ReLU / bf16 conversion as requested.
+// K-direction stride is 128 B and the row-group stride 1024 B). One thread
+// issues four tcgen05.mma.kind::f16 (K = 16 each) per chunk into the TMEM
+// accumulator and commits them to that stage's mbarrier; the copies of the next
+// S - 1 chunks are in flight meanwhile, and a stage is refilled only after its
+// mbarrier reports the MMAs reading it done. The epilogue reads TMEM (each warp
+// a 32-lane quarter and every other group of 16 columns) and applies bias /
+// ReLU / bf16 conversion as requested.
 //
 // Every mbarrier wait is bounded (wall-clock limit via %globaltimer): on
 // timeout the kernel raises *status, waits once more (bounded), frees TMEM and
@@ -117,46 +119,127 @@ __device__ __forceinline__ void tm_ld16(uint32_t taddr, float (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// copy rows x 64 bf16 from a K-contiguous matrix into the core-matrix layout
-__device__ __forceinline__ void stage(uint8_t* dst, const __nv_bfloat16* src, int rows, int ld, int k0) {
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int kThreads = 256;                       // 8 warps: copies shared by all, epilogue by column halves
+constexpr int kRowsPerThread = 128 * 8 / kThreads;  // A rows each thread copies per chunk (fixed q)
+
+// rows x 64 bf16 of a K-contiguous matrix into the core-matrix layout, 16 bytes per async copy
+__device__ __forceinline__ void stage(uint32_t dst, const __nv_bfloat16* src, int rows, int ld, int k0) {
   for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
     const int r = i >> 3, q = i & 7;
-    const uint4 v = *reinterpret_cast<const uint4*>(src + (size_t)r * ld + k0 + q * 8);
-    *reinterpret_cast<uint4*>(dst + (size_t)(((r >> 3) * 8 + q) * 128 + (r & 7) * 16)) = v;
+    cp_async16(dst + (uint32_t)(((r >> 3) * 8 + q) * 128 + (r & 7) * 16), src + (size_t)r * ld + k0 + q * 8, 16u);
   }
 }
 
+// pixel coordinates of the A rows this thread copies: row r_t = (tid >> 3) + 32 t
+struct ConvRows {
+  int off[kRowsPerThread];  // ((b H + y) W + x) Cin
+  int y[kRowsPerThread], x[kRowsPerThread];
+};
+__device__ __forceinline__ ConvRows conv_rows(int m0, int H, int W, int Cin) {
+  ConvRows c;
+#pragma unroll
+  for (int t = 0; t < kRowsPerThread; ++t) {
+    const int p = m0 + (threadIdx.x >> 3) + (kThreads / 8) * t;
+    const int x = p % W, y = (p / W) % H, b = p / (W * H);
+    c.y[t] = y;
+    c.x[t] = x;
+    c.off[t] = ((b * H + y) * W + x) * Cin;
+  }
+  return c;
+}
+
 // implicit-GEMM operand: 128 rows (pixels m0 ..) x 64 columns of the 3x3
-// neighbourhood matrix of an NHWC tensor, gathered 8 channels (16 bytes) at a time
-__device__ __forceinline__ void stage_conv(uint8_t* dst, const __nv_bfloat16* X, int m0, int k0, int H, int W,
-                                           int Cin) {
-  for (int i = threadIdx.x; i < 128 * 8; i += blockDim.x) {
-    const int r = i >> 3, q = i & 7;
-    const int k = k0 + q * 8;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (k < 9 * Cin) {
-      const int tap = k / Cin, c = k - tap * Cin;
-      const int p = m0 + r;
-      const int x = p % W, y = (p / W) % H, b = p / (W * H);
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-        v = *reinterpret_cast<const uint4*>(X + (((size_t)b * H + yy) * W + xx) * Cin + c);
-    }
-    *reinterpret_cast<uint4*>(dst + (size_t)(((r >> 3) * 8 + q) * 128 + (r & 7) * 16)) = v;
+// neighbourhood matrix of an NHWC tensor, gathered 8 channels (16 bytes) at a
+// time; taps outside the image and columns beyond 9 Cin are zero-filled
+__device__ __forceinline__ void stage_conv(uint32_t dst, const __nv_bfloat16* X, const ConvRows& cr, int k0, int H,
+                                           int W, int Cin) {
+  const int q = threadIdx.x & 7;
+  const int k = k0 + q * 8;
+  const bool inK = k < 9 * Cin;
+  const int tap = inK ? k / Cin : 0;
+  const int c = k - tap * Cin;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int shift = (dy * W + dx) * Cin + c;
+#pragma unroll
+  for (int t = 0; t < kRowsPerThread; ++t) {
+    const int r = (threadIdx.x >> 3) + (kThreads / 8) * t;
+    const int yy = cr.y[t] + dy, xx = cr.x[t] + dx;
+    const bool in = inK && yy >= 0 && yy < H && xx >= 0 && xx < W;
+    cp_async16(dst + (uint32_t)(((r >> 3) * 8 + q) * 128 + (r & 7) * 16), in ? X + cr.off[t] + shift : X,
+               in ? 16u : 0u);
+  }
+}
+
+// rows of the transposed operand this thread copies (fixed across the K loop over pixels)
+struct ConvTRows {
+  size_t off[kRowsPerThread];  // ((dx + 1) Cin + c) Mpix
+  int dy[kRowsPerThread];
+  bool valid[kRowsPerThread];
+};
+__device__ __forceinline__ ConvTRows convT_rows(int m0, int Cin, int Mpix) {
+  ConvTRows c;
+#pragma unroll
+  for (int t = 0; t < kRowsPerThread; ++t) {
+    const int k = m0 + (threadIdx.x >> 3) + (kThreads / 8) * t;
+    c.valid[t] = k < 9 * Cin;
+    const int tap = c.valid[t] ? k / Cin : 4, ch = k - tap * Cin;
+    c.dy[t] = tap / 3 - 1;
+    c.off[t] = ((size_t)(tap % 3) * Cin + (c.valid[t] ? ch : 0)) * Mpix;
+  }
+  return c;
+}
+// 128 rows (k) x 64 pixels (p0 ..) of the transposed operand; the 8 pixels of one 16-byte
+// copy share an image row because W % 8 == 0
+__device__ __forceinline__ void stage_convT(uint32_t dst, const __nv_bfloat16* XT3, const ConvTRows& cr, int p0,
+                                            int H, int W) {
+  const int q = threadIdx.x & 7;
+  const int p = p0 + q * 8;
+  const int y = (p / W) % H;
+#pragma unroll
+  for (int t = 0; t < kRowsPerThread; ++t) {
+    const int r = (threadIdx.x >> 3) + (kThreads / 8) * t;
+    const int yy = y + cr.dy[t];
+    const bool in = cr.valid[t] && yy >= 0 && yy < H;
+    cp_async16(dst + (uint32_t)(((r >> 3) * 8 + q) * 128 + (r & 7) * 16),
+               in ? XT3 + cr.off[t] + p + (ptrdiff_t)cr.dy[t] * W : XT3, in ? 16u : 0u);
   }
 }
 
 }  // namespace
 
+// pipeline depth: stages of (A chunk, B chunk) in shared memory
+template <int N>
+struct GemmStages {
+  static constexpr int S = N >= 128 ? 3 : 4;  // <= 96 KB below N = 256: two CTAs per SM
+  static constexpr size_t A_BYTES = 128 * KC * 2, B_BYTES = (size_t)N * KC * 2;
+  static constexpr size_t STAGE = A_BYTES + B_BYTES;
+  static constexpr size_t SMEM = S * STAGE;
+};
+
 // epilogue modes: 0 = store fp32 D; 1 = accumulate into fp32 D (D += A B^T);
 // 2 = bf16 out = act(D + bias[n]) with act = ReLU when `relu`
+//
+// K pipeline: chunk i is copied (cp.async) into stage i % S while the MMAs of
+// the chunks before it run; before stage s is refilled, the CTA waits on the
+// mbarrier that the MMAs reading it committed to (bounded). One thread issues
+// the MMAs after a CTA barrier that follows every thread's wait for its own
+// copies of that chunk.
 template <int N>
-__global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_bf16(const GemmArgs g) {
+  using ST = GemmStages<N>;
+  constexpr int S = ST::S;
   constexpr uint32_t NCOLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint8_t* sA = smem;                  // 128 x 64 bf16 = 16 KB
-  uint8_t* sB = smem + 128 * KC * 2;   // N x 64 bf16
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[S];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * 128;
@@ -164,7 +247,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
 
   if (warp == 0) tm_alloc(&s_tmem, NCOLS);
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    for (int i = 0; i < S; ++i) mbar_init(&bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -172,41 +255,68 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = make_idesc(128, N);
-  const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(g.A) + (g.conv ? 0 : (size_t)m0 * g.K);
+  const __nv_bfloat16* A =
+      reinterpret_cast<const __nv_bfloat16*>(g.A) + ((g.conv || g.convT) ? 0 : (size_t)m0 * g.K);
   const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(g.B) + (size_t)n0 * g.K;
-  uint32_t phase = 0;
-  bool ok = true;
   const int kbeg = g.ksplit > 1 ? (int)blockIdx.z * g.kc : 0;
   const int kend = g.ksplit > 1 ? min(g.K, kbeg + g.kc) : g.K;
-  for (int k0 = kbeg; k0 < kend && ok; k0 += KC) {
-    if (g.conv) stage_conv(sA, A, m0, k0, g.H, g.W, g.Cin);
-    else stage(sA, A, 128, g.K, k0);
-    stage(sB, B, N, g.K, k0);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int s = 0; s < KC / 16; ++s) {
-        const uint64_t ad = make_desc(smem_u32(sA) + s * 256, 128, 1024);
-        const uint64_t bd = make_desc(smem_u32(sB) + s * 256, 128, 1024);
-        mma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || s > 0) ? 1u : 0u);
+  const int nk = (kend - kbeg) / KC;
+  const uint32_t base = smem_u32(smem);
+  ConvRows cr{};
+  if (g.conv) cr = conv_rows(m0, g.H, g.W, g.Cin);
+  ConvTRows ctr{};
+  if (g.convT) ctr = convT_rows(m0, g.Cin, g.Mpix);
+  bool ok = true;
+  for (int i = 0; i < nk + S - 1 && ok; ++i) {
+    if (i < nk) {
+      const int st = i % S;
+      if (i >= S)  // the MMAs of chunk i - S read this stage
+        ok = __syncthreads_and(mbar_wait_bounded(&bar[st], (uint32_t)((i / S - 1) & 1)) ? 1 : 0) != 0;
+      if (ok) {
+        const uint32_t sa = base + (uint32_t)(st * ST::STAGE), sb = sa + (uint32_t)ST::A_BYTES;
+        const int k0 = kbeg + i * KC;
+        if (g.conv) stage_conv(sa, A, cr, k0, g.H, g.W, g.Cin);
+        else if (g.convT) stage_convT(sa, A, ctr, k0, g.H, g.W);
+        else stage(sa, A, 128, g.K, k0);
+        stage(sb, B, N, g.K, k0);
       }
-      mma_commit(&bar);
     }
-    ok = __syncthreads_and(mbar_wait_bounded(&bar, phase) ? 1 : 0) != 0;  // CTA-uniform outcome
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    cp_async_commit();  // one group per step (possibly empty) keeps the group count aligned
+    const int j = i - (S - 1);
+    if (j >= 0 && ok) {
+      cp_async_wait<S - 1>();  // this thread's copies of chunk j have landed
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int st = j % S;
+        const uint32_t sa = base + (uint32_t)(st * ST::STAGE), sb = sa + (uint32_t)ST::A_BYTES;
+#pragma unroll
+        for (int s = 0; s < KC / 16; ++s) {
+          const uint64_t ad = make_desc(sa + s * 256, 128, 1024);
+          const uint64_t bd = make_desc(sb + s * 256, 128, 1024);
+          mma_bf16(tmem, ad, bd, idesc, (j > 0 || s > 0) ? 1u : 0u);
+        }
+        mma_commit(&bar[st]);
+      }
+    }
   }
+  cp_async_wait<0>();
+  // the last chunk's commit covers every MMA issued before it
+  if (ok && nk > 0)
+    ok = __syncthreads_and(mbar_wait_bounded(&bar[(nk - 1) % S], (uint32_t)(((nk - 1) / S) & 1)) ? 1 : 0) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!ok) {
     if (tid == 0) atomicExch(g.status, 1);
-    mbar_wait_bounded(&bar, phase ^ 1u);  // give the MMAs in flight a bounded chance to finish
+    // give the MMAs in flight a bounded chance to finish before TMEM is released
+    for (int st = 0; st < S; ++st) mbar_wait_bounded(&bar[st], 0u), mbar_wait_bounded(&bar[st], 1u);
   } else {
-    // epilogue: warp w owns rows 32 w .. 32 w + 31 (TMEM lanes), 16 columns per load
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    // epilogue: warp w owns rows 32 (w % 4) .. + 31 (its TMEM lane quarter) and every other
+    // group of 16 columns, starting at 16 (w / 4)
+    const int row = m0 + (warp & 3) * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    for (int c0 = (warp >> 2) * 16; c0 < N; c0 += 32) {
       float v[16];
       tm_ld16(tl + c0, v);
       if (g.mode == 2) {
@@ -232,16 +342,17 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g) {
 
 template <int N>
 static cudaError_t launch_n(const GemmArgs& g, cudaStream_t s) {
-  const size_t smem = 128 * KC * 2 + (size_t)N * KC * 2;
+  const size_t smem = GemmStages<N>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gemm_bf16<N><<<dim3(g.M / 128, g.Ntot / N, g.ksplit > 1 ? g.ksplit : 1), 128, smem, s>>>(g);
+  k_gemm_bf16<N><<<dim3(g.M / 128, g.Ntot / N, g.ksplit > 1 ? g.ksplit : 1), kThreads, smem, s>>>(g);
   return cudaGetLastError();
 }
 
 // N tile chosen from the output width: the widest of 256/128/64/32/16 dividing it
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (g.M % 128 || g.K % KC || g.Ntot % 16 || g.M <= 0 || g.K <= 0 || g.Ntot <= 0) return cudaErrorInvalidValue;
+  if (g.convT && (g.W % 8 || g.Mpix != g.K || g.conv)) return cudaErrorInvalidValue;
   if (g.ksplit > 1 && (g.mode != 0 || g.kc % KC || g.kc <= 0 || (long long)(g.ksplit - 1) * g.kc >= g.K ||
                        (long long)g.ksplit * g.kc < g.K || g.ksplit > 65535))
     return cudaErrorInvalidValue;  // every split must own at least one chunk
