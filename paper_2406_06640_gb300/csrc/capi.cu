@@ -53,6 +53,9 @@ std::vector<double> taps_1d(double sigma, int h) {
 
 }  // namespace
 
+// positions per chunk of a work-queue launch (each chunk has its own probe / error partials)
+constexpr int kQueueChunk = 16;
+
 struct ptycho_plan_s {
   ptycho_params p{};
   std::vector<int32_t> windows;
@@ -74,9 +77,24 @@ struct ptycho_plan_s {
   std::vector<cudaStream_t> branch;
   std::vector<cudaEvent_t> branch_ev;
   std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
+  std::vector<std::vector<FusedArgs*>> graph_descs;  // per graph: each class's device argument array
   cudaStream_t origin = nullptr;          // capture / replay stream of a batch plan
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int chunk = 0;
+  // batch member drained by a work-queue launch: number of position chunks (its partial count)
+  int parts = 0;
+  // batch plans: one work-queue launch per shape class (M, K, geometry, kernel width class)
+  struct QueueClass {
+    int M = 0, K = 0, near = 0, kh = 0;
+    std::vector<int> members;  // batch member indices, in order
+    int4* d_chunks = nullptr;
+    int nchunks = 0;
+    int* d_queue = nullptr;
+    int slots = 0;
+    int chunk_len = 0;
+  };
+  std::vector<QueueClass> qclasses;
+  std::vector<char> queued;  // per member: drained by its class's work-queue launch
   double* d_errhist = nullptr;
   // profiling: event pairs around the fused kernel
   bool profiling = false;
@@ -204,6 +222,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
     if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
     pl->slots = std::min(max_slots, N);
   }
+  if (pl->parts > 0) pl->slots = pl->parts;  // partials per position chunk (work-queue batch member)
 
   // ---- buffers
   FusedArgs& fa = pl->fa;
@@ -482,6 +501,20 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
   return PTYCHO_OK;
 }
 
+// The update part of iteration t (object / probe steps, complex constraint) of a batch member whose
+// per-position work ran in its class's work-queue launch.
+static ptycho_status enqueue_update(ptycho_plan_s* pl, void* object, void* probe, long long t, cudaStream_t s) {
+  UpdateArgs ua = pl->ua;
+  ConstraintArgs ca = pl->ca;
+  ua.O = static_cast<float2*>(object);
+  ua.P = static_cast<float2*>(probe);
+  ca.O = static_cast<float2*>(object);
+  ua.update_probe = t >= pl->p.probe_update_start;
+  PT_CUDA(launch_update(ua, s), "update launch");
+  if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
+  return PTYCHO_OK;
+}
+
 ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_t n_iter) {
   if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
   if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "batch plans run through ptycho_iterate_batch");
@@ -516,6 +549,33 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
     delete pl;
     return cuda_fail(e, "cudaGetDevice");
   }
+  // shape classes of the work-queue launches: members with M in {32, 64, 128} sharing K, geometry
+  // and kernel width class are drained together; the others keep their own launches
+  std::vector<int> member_class(B, -1);
+  for (int b = 0; b < B; ++b) {
+    const ptycho_params& q = *params[b];
+    if (!fused_queue_supported(q.M)) continue;
+    const int kh = (q.kernel_size - 1) / 2 == 5 ? 5 : 15;
+    const int near = q.geometry == PTYCHO_NEARFIELD ? 1 : 0;
+    int ci = -1;
+    for (size_t c = 0; c < pl->qclasses.size(); ++c) {
+      const auto& qc = pl->qclasses[c];
+      if (qc.M == q.M && qc.K == q.K && qc.near == near && qc.kh == kh) ci = (int)c;
+    }
+    if (ci < 0) {
+      ptycho_plan_s::QueueClass qc;
+      qc.M = q.M;
+      qc.K = q.K;
+      qc.near = near;
+      qc.kh = kh;
+      qc.chunk_len = kQueueChunk;
+      pl->qclasses.push_back(qc);
+      ci = (int)pl->qclasses.size() - 1;
+    }
+    pl->qclasses[ci].members.push_back(b);
+    member_class[b] = ci;
+  }
+  pl->queued.assign(B, 0);
   for (int b = 0; b < B; ++b) {
     ptycho_status st = PTYCHO_OK;
     ptycho_plan_s* m = new (std::nothrow) ptycho_plan_s();
@@ -528,6 +588,11 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       m->stream = pl->stream;
       m->iter = params[b]->start_iteration;
       m->device = pl->device;
+      if (member_class[b] >= 0) {
+        const int L = pl->qclasses[member_class[b]].chunk_len;
+        m->parts = (m->p.N + L - 1) / L;
+        pl->queued[b] = 1;
+      }
       st = build_plan(m, intensities[b], positions[b]);
     }
     if (st != PTYCHO_OK) {
@@ -536,6 +601,24 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       delete pl;
       return fail(st, msg);
     }
+  }
+  // chunk lists: (member position in its class, first position, end, partial index), members in order
+  for (auto& qc : pl->qclasses) {
+    std::vector<int4> chunks;
+    for (size_t j = 0; j < qc.members.size(); ++j) {
+      const ptycho_plan_s* m = pl->members[qc.members[j]];
+      for (int c = 0; c < m->parts; ++c)
+        chunks.push_back(make_int4((int)j, c * qc.chunk_len, std::min(m->p.N, (c + 1) * qc.chunk_len), c));
+    }
+    qc.nchunks = (int)chunks.size();
+    int max_slots = 0;
+    PT_CUDA(pl->alloc(&qc.d_chunks, chunks.size()), "alloc chunk list");
+    PT_CUDA(pl->alloc(&qc.d_queue, 1), "alloc work counter");
+    PT_CUDA(cudaMemcpy(qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice),
+            "copy chunk list");
+    PT_CUDA(fused_queue_max_slots(qc.M, qc.K, &max_slots), "occupancy of the work-queue kernel");
+    if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
+    qc.slots = std::min(max_slots, qc.nchunks);
   }
   const int S = std::min(B, 8);
   pl->branch.resize(S);
@@ -572,12 +655,46 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
     for (auto& g : pl->graphs)
       if (g.first == key) exec = g.second;
     if (!exec) {
+      // each class's per-problem arguments with this call's object / probe pointers (kept with the graph)
+      std::vector<FusedArgs*> descs;
+      for (const auto& qc : pl->qclasses) {
+        std::vector<FusedArgs> h;
+        for (int b : qc.members) {
+          FusedArgs f = pl->members[b]->fa;
+          f.O = static_cast<const float2*>(objects[b]);
+          f.P = static_cast<const float2*>(probes[b]);
+          h.push_back(f);
+        }
+        FusedArgs* d = nullptr;
+        PT_CUDA(pl->alloc(&d, h.size()), "alloc work-queue arguments");
+        PT_CUDA(cudaMemcpy(d, h.data(), sizeof(FusedArgs) * h.size(), cudaMemcpyHostToDevice), "copy arguments");
+        descs.push_back(d);
+      }
       PT_CUDA(cudaStreamBeginCapture(pl->origin, cudaStreamCaptureModeRelaxed), "begin capture");
       ptycho_status st = PTYCHO_OK;
       cudaError_t ce = cudaEventRecord(pl->branch_ev[S], pl->origin);
       for (int j = 0; j < S && ce == cudaSuccess; ++j) ce = cudaStreamWaitEvent(pl->branch[j], pl->branch_ev[S], 0);
+      int br = 0;
+      // one persistent work-queue launch per class, then its members' updates on the same branch
+      for (size_t c = 0; c < pl->qclasses.size() && ce == cudaSuccess && st == PTYCHO_OK; ++c) {
+        const auto& qc = pl->qclasses[c];
+        cudaStream_t bs = pl->branch[br++ % S];
+        ce = cudaMemsetAsync(qc.d_queue, 0, sizeof(int), bs);
+        FusedArgs fa = pl->members[qc.members[0]]->fa;
+        fa.probs = descs[c];
+        fa.chunks = qc.d_chunks;
+        fa.nchunks = qc.nchunks;
+        fa.queue = qc.d_queue;
+        fa.kh = qc.kh;
+        if (ce == cudaSuccess) ce = launch_fused_queue(qc.M, fa, qc.slots, bs);
+        for (size_t j = 0; j < qc.members.size() && ce == cudaSuccess && st == PTYCHO_OK; ++j) {
+          const int b = qc.members[j];
+          st = enqueue_update(pl->members[b], objects[b], probes[b], pl->members[b]->iter, bs);
+        }
+      }
       for (int b = 0; b < B && ce == cudaSuccess && st == PTYCHO_OK; ++b)
-        st = enqueue_iteration(pl->members[b], objects[b], probes[b], pl->members[b]->iter, pl->branch[b % S]);
+        if (!pl->queued[b])
+          st = enqueue_iteration(pl->members[b], objects[b], probes[b], pl->members[b]->iter, pl->branch[br++ % S]);
       for (int j = 0; j < S && ce == cudaSuccess && st == PTYCHO_OK; ++j) {
         ce = cudaEventRecord(pl->branch_ev[j], pl->branch[j]);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(pl->origin, pl->branch_ev[j], 0);
@@ -597,6 +714,7 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
       cudaGraphDestroy(graph);
       PT_CUDA(ie, "instantiate the batch graph");
       pl->graphs.emplace_back(key, exec);
+      pl->graph_descs.push_back(descs);
     }
     PT_CUDA(cudaEventRecord(pl->ev_in, pl->stream), "event");
     PT_CUDA(cudaStreamWaitEvent(pl->origin, pl->ev_in, 0), "wait");

@@ -33,11 +33,23 @@ struct FusedArgs {
   float2* pacc;         // out: per-slot probe numerator partials, slots x K x M x M (accumulated)
   float* dacc;          // out: per-slot probe denominator partials, slots x M x M (accumulated)
   double* errpart;      // out: per-CTA FP64 error numerators, slots x K
+  // work-queue launches over several problems of one shape (M, K, geometry, blur kernel width):
+  // chunk c = (problem index into probs, first position, end position, partial index); partials
+  // (pacc, dacc, errpart) are indexed by the chunk's partial index instead of the slot
+  const FusedArgs* probs;  // device, one entry per problem; unused by single-problem launches
+  const int4* chunks;
+  int nchunks;
+  int* queue;  // device counter, zero before the launch
 };
 
 // fused kernel launch; returns the number of slots (co-resident clusters) used
 cudaError_t launch_fused(int M, const FusedArgs& a, int slots, cudaStream_t s);
 cudaError_t fused_max_slots(int M, int K, int* slots);
+// work-queue launch (M = 32, 64, 128): `slots` persistent clusters drain a.chunks through a.queue;
+// a.K, a.near_field, a.kh (kernel width class) and a.tw are those of every problem in a.probs
+cudaError_t launch_fused_queue(int M, const FusedArgs& a, int slots, cudaStream_t s);
+cudaError_t fused_queue_max_slots(int M, int K, int* slots);
+bool fused_queue_supported(int M);
 size_t fused_smem_bytes(int M);
 // true if a bounded device wait of the fused kernel gave up since the last call (clears the flag; synchronous)
 cudaError_t fused_timed_out(bool* out);

@@ -97,6 +97,9 @@ __device__ __forceinline__ float2 ld_cluster_f2(uint32_t addr) {
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 __device__ __forceinline__ void st_cluster_f2(uint32_t addr, float2 v) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
@@ -171,7 +174,9 @@ struct FusedSmem {
   static constexpr size_t HQ = (size_t)M * 8;                                             // Fresnel factors
   static constexpr size_t TAPS = 2 * kMaxTaps * 4 + 8 + 16;  // taps, TMEM address, mbarrier (16-byte aligned)
   static constexpr size_t BYTES = CBUF + IBUF + TWT + HQ + TAPS;
-  static_assert(BYTES <= 232448, "shared memory budget of one CTA");
+  // queued launches: the current problem's arguments and the chunk index handed out by rank 0
+  static constexpr size_t DESC = (sizeof(FusedArgs) + 15) / 16 * 16 + 16;
+  static_assert(BYTES + DESC <= 232448, "shared memory budget of one CTA");
 };
 
 // lines per thread: the 128 x 128 tile runs on 512 threads with two lines each
@@ -240,8 +245,8 @@ __device__ __forceinline__ void blur_strip(const float* in, int base, int stride
   }
 }
 
-template <int M, bool NEAR, int KH>
-__global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const FusedArgs a) {
+template <int M, bool NEAR, int KH, bool QUEUED>
+__global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const FusedArgs a_in) {
   using TL = Tile<M>;
   using SM = FusedSmem<M, KH>;
   constexpr int E = TL::E, G = TL::G, LD = SM::LD, LDN = TL::LDN;
@@ -260,35 +265,23 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
   float* s_gy = s_gx + kMaxTaps;
 
   const int tid = threadIdx.x;
-  const int K = a.K;
+  const int K = a_in.K;
   const int rank = (int)cluster_ctarank();
   const int slot = blockIdx.x / K;
   const int nslots = gridDim.x / K;
 
-  // twiddle table s_tw[t * (E + 1) + k2] = W_M^(t k2), t < G, from the host table W_M^m
+  // twiddle table s_tw[t * (E + 1) + k2] = W_M^(t k2), t < G, from the host table W_M^m (same for every
+  // problem of a launch: one M)
   for (int i = tid; i < G * TL::LDW; i += TR) {
     const int t = i / TL::LDW, k2 = i % TL::LDW;
-    s_tw[i] = k2 < E ? a.tw[(t * k2) % M] : make_float2(0.f, 0.f);
+    s_tw[i] = k2 < E ? a_in.tw[(t * k2) % M] : make_float2(0.f, 0.f);
   }
-  if constexpr (NEAR)
-    for (int i = tid; i < M; i += TR) s_h[i] = a.hq[i];
-  // taps centred at index KH; zero outside the requested kernel
-  for (int i = tid; i < 2 * KH + 1; i += TR) {
-    const int d = i - KH;
-    const bool in = d >= -a.kh && d <= a.kh;
-    s_gx[i] = in ? a.gx[d + a.kh] : 0.f;
-    s_gy[i] = in ? a.gy[d + a.kh] : 0.f;
-  }
-  __syncthreads();
-
   int line[V], tp[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     line[v] = (tid + v * TR) / G;
     tp[v] = (tid + v * TR) % G;
   }
-  const float2* Pk = a.P + (size_t)rank * M * M;
-  float2* pacc = a.pacc + ((size_t)slot * K + rank) * M * M;
   // ---- TMEM: columns [colP, colP + 2 V E) hold P_k, [colA, colA + 2 V E) the probe numerator
   constexpr bool TM = FusedShape<M>::TMEM;
   uint32_t t_lane = 0, colP = 0, colA = 0;
@@ -302,27 +295,11 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
     t_lane = *s_tmem + ((uint32_t)(32 * (warp % 4)) << 16);
     colP = (uint32_t)((warp / 4) * FusedShape<M>::COLS_PER_THREAD);
     colA = colP + 2 * V * E;
-#pragma unroll
-    for (int q = 0; q < V; ++q)
-#pragma unroll
-      for (int h = 0; h < E / 8; ++h) {
-        float pr[16];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const float2 p = Pk[line[q] * M + tp[q] + G * (8 * h + jj)];
-          pr[2 * jj] = p.x;
-          pr[2 * jj + 1] = p.y;
-        }
-        tmem_st16(t_lane + colP + 2 * (q * E + 8 * h), pr);
-      }
-    tmem_wait_st();
   }
-  float* dacc = a.dacc + (size_t)slot * M * M;
   const int RPO = (M + K - 1) / K;  // rows per owner
   const int r0 = min(M, rank * RPO), r1 = min(M, r0 + RPO), nrow = r1 - r0;
   const float inv_m2 = 1.0f / (float)(M * M);
   const uint32_t ibuf_s = smem_addr(ibuf), z_s = smem_addr(Z), yb_s = smem_addr(Yb), recv_s = smem_addr(recv);
-  const float eps = a.eps;
   float err_s = 0.f, err_c = 0.f;  // compensated per-thread sum of (Ihat - I)^2 over own rows
   // staging of the own rows' measured data behind Z and Yb in the exchange buffer, when it fits
   const size_t meas_off = ((size_t)(M + nrow + 2 * KH) * LD * 4 + 15) / 16 * 16;
@@ -335,8 +312,41 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
   if (tid == 0) mbar_init(bar_s, 1);
   __syncthreads();
 
-  for (int n = slot; n < a.N; n += nslots) {
-    const bool first = (n == slot);
+  // ---- per problem (one unit of work): Fresnel factors, taps, this rank's probe mode into TMEM.
+  // Called between CTA barriers.
+  auto setup_unit = [&](const FusedArgs& a) {
+    if constexpr (NEAR)
+      for (int i = tid; i < M; i += TR) s_h[i] = a.hq[i];
+    // taps centred at index KH; zero outside the requested kernel
+    for (int i = tid; i < 2 * KH + 1; i += TR) {
+      const int d = i - KH;
+      const bool in = d >= -a.kh && d <= a.kh;
+      s_gx[i] = in ? a.gx[d + a.kh] : 0.f;
+      s_gy[i] = in ? a.gy[d + a.kh] : 0.f;
+    }
+    if constexpr (TM) {
+      const float2* Pk = a.P + (size_t)rank * M * M;
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+#pragma unroll
+        for (int h = 0; h < E / 8; ++h) {
+          float pr[16];
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const float2 p = Pk[line[q] * M + tp[q] + G * (8 * h + jj)];
+            pr[2 * jj] = p.x;
+            pr[2 * jj + 1] = p.y;
+          }
+          tmem_st16(t_lane + colP + 2 * (q * E + 8 * h), pr);
+        }
+      tmem_wait_st();
+    }
+  };
+
+  // ---- one scan position n of problem a; `first` starts this unit's probe partials
+  auto run_position = [&](const FusedArgs& a, int n, bool first, float2* pacc, float* dacc) {
+    const float2* Pk = a.P + (size_t)rank * M * M;
+    const float eps = a.eps;
     const int2 pn = a.pos[n];
     const float2* On = a.O + (size_t)pn.x * a.obj_w + pn.y;
     float2 v[V][E];
@@ -580,27 +590,24 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
       }
     }
     __syncthreads();  // the next position reuses the exchange buffer
-  }
-  // ---- probe-numerator partial from TMEM to global, then release TMEM
-  if constexpr (TM) {
+  };
+
+  // ---- end of a unit: probe-numerator partial from TMEM to global; per-CTA FP64 error
+  // numerator (the compensated FP32 thread sums, added in thread order) into partial `part`
+  auto finish_unit = [&](const FusedArgs& a, float2* pacc, int part) {
+    if constexpr (TM) {
 #pragma unroll
-    for (int q = 0; q < V; ++q)
+      for (int q = 0; q < V; ++q)
 #pragma unroll
-      for (int h = 0; h < E / 4; ++h) {
-        float ac[8];
-        tmem_ld8(t_lane + colA + 2 * (q * E + 4 * h), ac);
-        tmem_wait_ld();
+        for (int h = 0; h < E / 4; ++h) {
+          float ac[8];
+          tmem_ld8(t_lane + colA + 2 * (q * E + 4 * h), ac);
+          tmem_wait_ld();
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          pacc[line[q] * M + tp[q] + G * (4 * h + jj)] = make_float2(ac[2 * jj], ac[2 * jj + 1]);
-      }
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    if (tid / 32 == 0) tmem_dealloc(*s_tmem, FusedShape<M>::TMEM_COLS);
-  }
-  // ---- per-CTA FP64 error numerator: the compensated FP32 thread sums, added in thread order
-  {
+          for (int jj = 0; jj < 4; ++jj)
+            pacc[line[q] * M + tp[q] + G * (4 * h + jj)] = make_float2(ac[2 * jj], ac[2 * jj + 1]);
+        }
+    }
     double* red = reinterpret_cast<double*>(smem);
     red[tid] = (double)err_s - (double)err_c;
     __syncthreads();
@@ -608,7 +615,50 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
       if (tid < w) red[tid] += red[tid + w];
       __syncthreads();
     }
-    if (tid == 0) a.errpart[(size_t)slot * K + rank] = red[0];
+    if (tid == 0) a.errpart[(size_t)part * K + rank] = red[0];
+    err_s = 0.f;
+    err_c = 0.f;
+    __syncthreads();  // red aliases the exchange buffer
+  };
+
+  if constexpr (!QUEUED) {
+    // one problem: cluster `slot` takes positions slot, slot + slots, ... and owns partial `slot`
+    setup_unit(a_in);
+    __syncthreads();
+    float2* pacc = a_in.pacc + ((size_t)slot * K + rank) * M * M;
+    float* dacc = a_in.dacc + (size_t)slot * M * M;
+    for (int n = slot; n < a_in.N; n += nslots) run_position(a_in, n, n == slot, pacc, dacc);
+    finish_unit(a_in, pacc, slot);
+  } else {
+    // work queue over every problem of this launch: chunk (problem, first position, end, partial);
+    // rank 0 takes the next chunk index and hands it to every rank of the cluster
+    FusedArgs* s_desc = reinterpret_cast<FusedArgs*>(smem + SM::BYTES);
+    int* s_item = reinterpret_cast<int*>(smem + SM::BYTES + SM::DESC - 16);
+    for (;;) {
+      if (rank == 0 && tid == 0) {
+        const int c = atomicAdd(a_in.queue, 1);
+        for (int q = 0; q < K; ++q) st_cluster_s32(map_rank(smem_addr(s_item), (unsigned)q), c);
+      }
+      cluster_sync_all();
+      const int c = *s_item;
+      if (c >= a_in.nchunks) break;
+      const int4 ch = a_in.chunks[c];
+      const int* src = reinterpret_cast<const int*>(a_in.probs + ch.x);
+      for (int i = tid; i < (int)(sizeof(FusedArgs) / 4); i += TR) reinterpret_cast<int*>(s_desc)[i] = src[i];
+      __syncthreads();
+      setup_unit(*s_desc);
+      __syncthreads();
+      float2* pacc = s_desc->pacc + ((size_t)ch.w * K + rank) * M * M;
+      float* dacc = s_desc->dacc + (size_t)ch.w * M * M;
+      for (int n = ch.y; n < ch.z; ++n) run_position(*s_desc, n, n == ch.y, pacc, dacc);
+      finish_unit(*s_desc, pacc, ch.w);
+    }
+  }
+  if constexpr (TM) {
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (tid / 32 == 0) tmem_dealloc(*s_tmem, FusedShape<M>::TMEM_COLS);
   }
 }
 
@@ -635,12 +685,12 @@ size_t fused_smem_bytes(int M) {
   }
 }
 
-template <int M, int KH>
+template <int M, int KH, bool QUEUED = false>
 static cudaLaunchConfig_t fused_config(const FusedArgs& a, int slots, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(slots * a.K));
   cfg.blockDim = dim3(FusedShape<M>::TR);
-  cfg.dynamicSmemBytes = FusedSmem<M, KH>::BYTES;
+  cfg.dynamicSmemBytes = FusedSmem<M, KH>::BYTES + (QUEUED ? FusedSmem<M, KH>::DESC : 0);
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)a.K;
@@ -651,13 +701,14 @@ static cudaLaunchConfig_t fused_config(const FusedArgs& a, int slots, cudaStream
   return cfg;
 }
 
-template <int M, bool NEAR, int KH>
+template <int M, bool NEAR, int KH, bool QUEUED = false>
 static cudaError_t launch_kh(const FusedArgs& a, int slots, cudaStream_t s) {
-  auto kern = pc_fused_kernel<M, NEAR, KH>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M, KH>::BYTES);
+  auto kern = pc_fused_kernel<M, NEAR, KH, QUEUED>;
+  const size_t bytes = FusedSmem<M, KH>::BYTES + (QUEUED ? FusedSmem<M, KH>::DESC : 0);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = fused_config<M, KH>(a, slots, s, attr);
+  cudaLaunchConfig_t cfg = fused_config<M, KH, QUEUED>(a, slots, s, attr);
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
@@ -671,7 +722,7 @@ static cudaError_t launch_t(const FusedArgs& a, int slots, cudaStream_t s) {
 // co-resident clusters, taken for the largest shared-memory variant (KH = 15)
 template <int M>
 static cudaError_t max_slots_t(int K, int* slots) {
-  auto kern = pc_fused_kernel<M, false, 15>;
+  auto kern = pc_fused_kernel<M, false, 15, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M, 15>::BYTES);
   if (e != cudaSuccess) return e;
   FusedArgs a = {};
@@ -703,6 +754,51 @@ cudaError_t fused_max_slots(int M, int K, int* slots) {
     case 32: return max_slots_t<32>(K, slots);
     case 64: return max_slots_t<64>(K, slots);
     case 128: return max_slots_t<128>(K, slots);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+
+// ---- work-queue launches (batches of problems sharing M, K, geometry and kernel width class)
+template <int M, bool NEAR>
+static cudaError_t launch_queue_t(const FusedArgs& a, int slots, cudaStream_t s) {
+  return a.kh == 5 ? launch_kh<M, NEAR, 5, true>(a, slots, s) : launch_kh<M, NEAR, 15, true>(a, slots, s);
+}
+
+bool fused_queue_supported(int M) { return M == 32 || M == 64 || M == 128; }
+
+cudaError_t launch_fused_queue(int M, const FusedArgs& a, int slots, cudaStream_t s) {
+  if (!a.probs || !a.chunks || !a.queue || a.nchunks < 0) return cudaErrorInvalidValue;
+  const bool nf = a.near_field != 0;
+  switch (M) {
+    case 32: return nf ? launch_queue_t<32, true>(a, slots, s) : launch_queue_t<32, false>(a, slots, s);
+    case 64: return nf ? launch_queue_t<64, true>(a, slots, s) : launch_queue_t<64, false>(a, slots, s);
+    case 128: return nf ? launch_queue_t<128, true>(a, slots, s) : launch_queue_t<128, false>(a, slots, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int M>
+static cudaError_t queue_slots_t(int K, int* slots) {
+  auto kern = pc_fused_kernel<M, false, 15, true>;
+  const size_t bytes = FusedSmem<M, 15>::BYTES + FusedSmem<M, 15>::DESC;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  FusedArgs a = {};
+  a.K = K;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = fused_config<M, 15, true>(a, 1, 0, attr);
+  int n = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+  *slots = n;
+  return e;
+}
+
+cudaError_t fused_queue_max_slots(int M, int K, int* slots) {
+  switch (M) {
+    case 32: return queue_slots_t<32>(K, slots);
+    case 64: return queue_slots_t<64>(K, slots);
+    case 128: return queue_slots_t<128>(K, slots);
     default: return cudaErrorInvalidValue;
   }
 }

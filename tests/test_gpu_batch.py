@@ -1,9 +1,13 @@
 """GPU: batched reconstructions of uneven sizes (ptycho_plan_batch / ptycho_iterate_batch).
 
-Each problem in a batch is an independent reconstruction; replaying the
-batch's CUDA graph must give exactly the result of running every problem
-through its own plan (same kernels, fixed reduction orders), across graph
-re-use and call splits, and therefore the oracle's result within 1e-4.
+Members with M in {32, 64, 128} are drained by one persistent work-queue launch per
+shape class (M, K, geometry, kernel width): chunks of 16 positions from every
+problem of the class, each chunk with its own probe / error partials summed in
+chunk order. Their results therefore differ from a single plan's (partials per
+slot) only by the FP32 summation order -- compared within 1e-5 -- and match the
+oracle within the 1e-4 bar; reruns of a batch are bitwise identical (the chunk a
+cluster takes does not change the arithmetic). Other members (M = 8, 16, 256)
+keep their own launches and match single plans exactly.
 """
 import numpy as np
 import pytest
@@ -57,18 +61,52 @@ def test_batch_matches_individual_plans_and_oracle():
     batch.iterate(objs, prbs, 1)
     batch.iterate(objs, prbs, n_iter - 1)
     E = batch.errors()
+    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)  # noqa: E731
     for b, (O1, P1, E1) in enumerate(single):
-        assert np.array_equal(objs[b].cpu().numpy(), O1), b
-        assert np.array_equal(prbs[b].cpu().numpy(), P1), b
-        assert E[b] == E1, b
+        Ob, Pb = objs[b].cpu().numpy(), prbs[b].cpu().numpy()
+        if probs[b][0].params["M"] == 256:  # own launches: the single plan's arithmetic exactly
+            assert np.array_equal(Ob, O1) and np.array_equal(Pb, P1) and E[b] == E1, b
+        else:
+            assert rel(Ob, O1) < 1e-5 and rel(Pb, P1) < 1e-5 and abs(E[b] - E1) / E1 < 1e-5, b
     batch.close()
-    # oracle on two members
-    for b in (0, 4):
+    # oracle on every member but the large one
+    for b in (0, 1, 2, 4):
         prob, prm = probs[b]
         Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), n_iter)
-        rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)  # noqa: E731
-        assert rel(single[b][0], Oo) < 1e-4 and rel(single[b][1], Po) < 1e-4
-        assert abs(single[b][2] - Eo[-1]) / Eo[-1] < 1e-4
+        assert rel(objs[b].cpu().numpy(), Oo) < 1e-4 and rel(prbs[b].cpu().numpy(), Po) < 1e-4, b
+        assert abs(E[b] - Eo[-1]) / Eo[-1] < 1e-4, b
+
+
+def _run_batch(dev, probs, n_iter):
+    from paper_2406_06640_gb300.engine import ReconstructionBatch
+
+    tens = [_tensors(dev, prob) for prob, _ in probs]
+    batch = ReconstructionBatch([(prm, t[0], prob.positions) for (prob, prm), t in zip(probs, tens)])
+    objs, prbs = [t[1] for t in tens], [t[2] for t in tens]
+    batch.iterate(objs, prbs, n_iter)
+    E = batch.errors()
+    batch.close()
+    return [o.cpu().numpy() for o in objs], [p.cpu().numpy() for p in prbs], E
+
+
+def test_work_queue_shares_chunks_across_problems_and_is_deterministic():
+    """Six problems of one class (M 64, K 2, far field, 11 x 11 kernel) of uneven N, including
+    N < 16 and N not a multiple of 16, drained by one launch: oracle parity for each, and two
+    runs bitwise equal."""
+    dev = torch.device("cuda:0")
+    probs = []
+    for i, side in enumerate((2, 3, 4, 5, 6, 7)):
+        p = make_problem(0, scan_side=side, obj_side=64 + 10 * side + 16, M=64, K=2, sigma=1.0 + 0.1 * i)
+        probs.append((p, dict(p.params, sigma1=1.0 + 0.1 * i, sigma2=1.0 + 0.1 * i)))
+    n_iter = 3
+    O1, P1, E1 = _run_batch(dev, probs, n_iter)
+    O2, P2, E2 = _run_batch(dev, probs, n_iter)
+    for b in range(len(probs)):
+        assert np.array_equal(O1[b], O2[b]) and np.array_equal(P1[b], P2[b]) and E1[b] == E2[b], b
+    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)  # noqa: E731
+    for b, (prob, prm) in enumerate(probs):
+        Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), n_iter)
+        assert rel(O1[b], Oo) < 1e-4 and rel(P1[b], Po) < 1e-4 and abs(E1[b] - Eo[-1]) / Eo[-1] < 1e-4, b
 
 
 def test_batch_rejects_single_plan_calls():
