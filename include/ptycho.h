@@ -148,6 +148,24 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
 ptycho_status ptycho_iterate_batch(ptycho_plan_t plan, void* const* objects, void* const* probes, int32_t n_iter);
 ptycho_status ptycho_error_batch(ptycho_plan_t plan, double* nrmse_last);
 
+/* Work-queue batching: problems with M in {32, 64, 128} sharing K, geometry and
+ * kernel width class (11 x 11 or any other size) are drained by one persistent
+ * launch per class; each chunk of L consecutive positions keeps its own probe and
+ * error partials, summed in chunk order (results do not depend on which cluster
+ * took a chunk). L is chosen per class by an autotuner the first time a batch
+ * plan of that class is built on a device in the process: it times the class's
+ * launch for L = 8, 16, 32, 64 on the device and keeps the fastest (cached per
+ * device, M, K, geometry and kernel width class).
+ * ptycho_set_batch_chunk fixes L for every later ptycho_plan_batch (8, 16, 32 or
+ * 64; 0 restores tuning), e.g. for bitwise-reproducible runs across processes:
+ * different L give the same result up to the FP32 order of the partial sums. */
+ptycho_status ptycho_set_batch_chunk(int32_t chunk_len);
+/* Describe the work-queue classes of a batch plan: for each of the first
+ * max_classes classes, 8 int32 (M, K, near field, kernel width class 5 or 15,
+ * members, chunk length, chunks, persistent clusters) into out; *count = the
+ * number of classes. */
+ptycho_status ptycho_batch_classes(ptycho_plan_t plan, int32_t max_classes, int32_t* out, int32_t* count);
+
 /* Tensor-core GEMM used by the warm-start network (the paper has no learned
  * component; this is the contraction under its 3x3 convolutions):
  *   D[M x N] = A[M x K] . B[N x K]^T      (accumulate != 0: D += A . B^T)

@@ -23,7 +23,7 @@ STEP_NORMALISED, STEP_RPIE = 0, 1
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
-            "ptycho_version", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
+            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
             "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
             "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart")
 
@@ -109,6 +109,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_iterate_batch.restype = st
     lib.ptycho_error_batch.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.ptycho_error_batch.restype = st
+    lib.ptycho_set_batch_chunk.argtypes = [ctypes.c_int32]
+    lib.ptycho_set_batch_chunk.restype = st
+    lib.ptycho_batch_classes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32)]
+    lib.ptycho_batch_classes.restype = st
     lib.ptycho_last_error.argtypes = []
     lib.ptycho_last_error.restype = ctypes.c_char_p
     lib.ptycho_version.argtypes = []
@@ -258,6 +263,15 @@ class BatchPlan:
         pp = (ctypes.c_void_p * self.B)(*probe_ptrs)
         _check(load().ptycho_iterate_batch(self._h, op, pp, int(n_iter)))
 
+    def classes(self) -> list:
+        """Work-queue classes: dicts with M, K, near, kh, members, chunk_len, chunks, slots."""
+        n = ctypes.c_int32()
+        _check(load().ptycho_batch_classes(self._h, 0, None, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * (8 * max(n.value, 1)))()
+        _check(load().ptycho_batch_classes(self._h, n.value, buf, ctypes.byref(n)))
+        keys = ("M", "K", "near", "kh", "members", "chunk_len", "chunks", "slots")
+        return [dict(zip(keys, buf[8 * c:8 * c + 8])) for c in range(n.value)]
+
     def errors(self) -> list:
         out = (ctypes.c_double * self.B)()
         _check(load().ptycho_error_batch(self._h, out))
@@ -355,3 +369,8 @@ def generate(spec: dict, probe_ptr: int, params_ptr: int, n: int, first: int = 0
     g = make_gen_spec(spec)
     _check(load().ptycho_generate(ctypes.byref(g), probe_ptr, params_ptr, n, first, x or None, counts or None,
                                   clean or None, target or None, sigma or None, stream_ptr or None))
+
+
+def set_batch_chunk(chunk_len: int):
+    """Fix the positions per work-queue chunk of later batch plans (8, 16, 32, 64; 0 = autotune)."""
+    _check(load().ptycho_set_batch_chunk(chunk_len))

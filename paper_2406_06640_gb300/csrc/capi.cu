@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "engine.h"
@@ -53,8 +56,16 @@ std::vector<double> taps_1d(double sigma, int h) {
 
 }  // namespace
 
-// positions per chunk of a work-queue launch (each chunk has its own probe / error partials)
-constexpr int kQueueChunk = 16;
+// positions per chunk of a work-queue launch (each chunk has its own probe / error partials):
+// candidates of the autotuner, smallest first (partial buffers are sized for the smallest)
+constexpr int kChunkCandidates[] = {8, 16, 32, 64};
+constexpr int kQueueChunkMin = 8;
+
+// autotuner cache: chunk length per (device, M, K, geometry, kernel width class), and an optional
+// caller-fixed chunk length (0: tune)
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
+int g_fixed_chunk = 0;
 
 struct ptycho_plan_s {
   ptycho_params p{};
@@ -530,6 +541,109 @@ ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_
   return PTYCHO_OK;
 }
 
+// Chunk list of a class for chunk length L: (member position in the class, first position, end,
+// partial index), members in order; sets each member's partial count (<= what its buffers hold).
+static std::vector<int4> chunk_list(ptycho_plan_s* pl, ptycho_plan_s::QueueClass& qc, int L) {
+  std::vector<int4> chunks;
+  for (size_t j = 0; j < qc.members.size(); ++j) {
+    const ptycho_plan_s* m = pl->members[qc.members[j]];
+    const int parts = (m->p.N + L - 1) / L;
+    for (int c = 0; c < parts; ++c) chunks.push_back(make_int4((int)j, c * L, std::min(m->p.N, (c + 1) * L), c));
+  }
+  return chunks;
+}
+
+static void st_apply_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueClass& qc, int L, int max_slots) {
+  const std::vector<int4> chunks = chunk_list(pl, qc, L);
+  qc.chunk_len = L;
+  qc.nchunks = (int)chunks.size();
+  qc.slots = std::min(max_slots, qc.nchunks);
+  cudaMemcpy(qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice);
+  for (int b : qc.members) {
+    ptycho_plan_s* m = pl->members[b];
+    m->parts = (m->p.N + L - 1) / L;
+    m->slots = m->parts;
+    m->ua.slots = m->parts;
+    m->ua.nerr = m->parts * m->p.K;
+  }
+}
+
+// Autotuner: time the class's work-queue launch for every candidate chunk length (object and probe
+// read from scratch buffers of ones; the launch writes only per-position contributions and
+// partials, which the first real iteration overwrites) and keep the fastest. Best of three
+// launches after one warm-up, CUDA events on the plan's stream.
+static ptycho_status tune_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueClass& qc, int max_slots, int* best) {
+  cudaStream_t s = pl->stream;
+  size_t obj_max = 1, probe_max = 1;
+  for (int b : qc.members) {
+    const ptycho_params& p = pl->members[b]->p;
+    obj_max = std::max(obj_max, (size_t)p.obj_h * p.obj_w);
+    probe_max = std::max(probe_max, (size_t)p.K * p.M * p.M);
+  }
+  float2 *d_o, *d_p;
+  FusedArgs* d_desc;
+  PT_CUDA(pl->alloc(&d_o, obj_max), "alloc tuning object");
+  PT_CUDA(pl->alloc(&d_p, probe_max), "alloc tuning probe");
+  PT_CUDA(pl->alloc(&d_desc, qc.members.size()), "alloc tuning arguments");
+  {
+    std::vector<float2> ones(std::max(obj_max, probe_max), make_float2(1.f, 0.f));
+    PT_CUDA(cudaMemcpy(d_o, ones.data(), sizeof(float2) * obj_max, cudaMemcpyHostToDevice), "tuning object");
+    PT_CUDA(cudaMemcpy(d_p, ones.data(), sizeof(float2) * probe_max, cudaMemcpyHostToDevice), "tuning probe");
+    std::vector<FusedArgs> h;
+    for (int b : qc.members) {
+      FusedArgs f = pl->members[b]->fa;
+      f.O = d_o;
+      f.P = d_p;
+      h.push_back(f);
+    }
+    PT_CUDA(cudaMemcpy(d_desc, h.data(), sizeof(FusedArgs) * h.size(), cudaMemcpyHostToDevice), "tuning arguments");
+  }
+  cudaEvent_t e0, e1;
+  PT_CUDA(cudaEventCreate(&e0), "event");
+  PT_CUDA(cudaEventCreate(&e1), "event");
+  float best_ms = 1e30f;
+  *best = kChunkCandidates[0];
+  ptycho_status st = PTYCHO_OK;
+  for (int L : kChunkCandidates) {
+    const std::vector<int4> chunks = chunk_list(pl, qc, L);
+    cudaError_t ce = cudaMemcpy(qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice);
+    FusedArgs fa = pl->members[qc.members[0]]->fa;
+    fa.probs = d_desc;
+    fa.chunks = qc.d_chunks;
+    fa.nchunks = (int)chunks.size();
+    fa.queue = qc.d_queue;
+    fa.kh = qc.kh;
+    const int slots = std::min(max_slots, fa.nchunks);
+    float t_best = 1e30f;
+    for (int r = 0; r < 4 && ce == cudaSuccess; ++r) {
+      ce = cudaMemsetAsync(qc.d_queue, 0, sizeof(int), s);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+      if (ce == cudaSuccess) ce = launch_fused_queue(qc.M, fa, slots, s);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce == cudaSuccess && r > 0) t_best = std::min(t_best, ms);
+    }
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ce, "autotuner launch");
+      break;
+    }
+    if (t_best < best_ms) {
+      best_ms = t_best;
+      *best = L;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == PTYCHO_OK) {
+    bool timed_out = false;
+    PT_CUDA(fused_timed_out(&timed_out), "read wait status");
+    if (timed_out) return fail(PTYCHO_ETIMEOUT, "a bounded device wait gave up while tuning");
+  }
+  return st;
+}
+
 ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, const float* const* intensities,
                                 const int32_t* const* positions, void* cuda_stream, ptycho_plan_t* out) {
   if (!out) return fail(PTYCHO_EINVAL, "out is NULL");
@@ -568,7 +682,7 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       qc.K = q.K;
       qc.near = near;
       qc.kh = kh;
-      qc.chunk_len = kQueueChunk;
+      qc.chunk_len = kQueueChunkMin;
       pl->qclasses.push_back(qc);
       ci = (int)pl->qclasses.size() - 1;
     }
@@ -602,23 +716,31 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       return fail(st, msg);
     }
   }
-  // chunk lists: (member position in its class, first position, end, partial index), members in order
+  // chunk lists, sized for the smallest chunk length (the most chunks); the autotuner then picks the
+  // length per class and the lists and partial counts are rebuilt for it
   for (auto& qc : pl->qclasses) {
-    std::vector<int4> chunks;
-    for (size_t j = 0; j < qc.members.size(); ++j) {
-      const ptycho_plan_s* m = pl->members[qc.members[j]];
-      for (int c = 0; c < m->parts; ++c)
-        chunks.push_back(make_int4((int)j, c * qc.chunk_len, std::min(m->p.N, (c + 1) * qc.chunk_len), c));
-    }
-    qc.nchunks = (int)chunks.size();
+    int max_chunks = 0;
+    for (int b : qc.members) max_chunks += pl->members[b]->parts;
     int max_slots = 0;
-    PT_CUDA(pl->alloc(&qc.d_chunks, chunks.size()), "alloc chunk list");
+    PT_CUDA(pl->alloc(&qc.d_chunks, (size_t)max_chunks), "alloc chunk list");
     PT_CUDA(pl->alloc(&qc.d_queue, 1), "alloc work counter");
-    PT_CUDA(cudaMemcpy(qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice),
-            "copy chunk list");
     PT_CUDA(fused_queue_max_slots(qc.M, qc.K, &max_slots), "occupancy of the work-queue kernel");
     if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
-    qc.slots = std::min(max_slots, qc.nchunks);
+    const std::tuple<int, int, int, int, int> key{pl->device, qc.M, qc.K, qc.near, qc.kh};
+    int L = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      if (g_fixed_chunk > 0) L = g_fixed_chunk;
+      else if (g_tune_cache.count(key)) L = g_tune_cache[key];
+    }
+    if (L == 0) {
+      ptycho_status st = tune_chunk_length(pl, qc, max_slots, &L);
+      if (st != PTYCHO_OK) return st;
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_cache[key] = L;
+    }
+    st_apply_chunk_length(pl, qc, L, max_slots);
+    PT_CUDA(cudaGetLastError(), "chunk list");
   }
   const int S = std::min(B, 8);
   pl->branch.resize(S);
@@ -725,6 +847,26 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
       m->iter++;
       m->runs++;
     }
+  }
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_set_batch_chunk(int32_t chunk_len) {
+  if (chunk_len != 0 && chunk_len != 8 && chunk_len != 16 && chunk_len != 32 && chunk_len != 64)
+    return fail(PTYCHO_EINVAL, "chunk length must be 0 (autotune), 8, 16, 32 or 64");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_fixed_chunk = chunk_len;
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_batch_classes(ptycho_plan_t pl, int32_t max_classes, int32_t* out, int32_t* count) {
+  if (!pl || pl->members.empty() || !count || max_classes < 0 || (max_classes > 0 && !out))
+    return fail(PTYCHO_EINVAL, "not a batch plan or bad output");
+  *count = (int32_t)pl->qclasses.size();
+  for (int c = 0; c < std::min<int>(max_classes, *count); ++c) {
+    const auto& qc = pl->qclasses[c];
+    const int32_t v[8] = {qc.M, qc.K, qc.near, qc.kh, (int32_t)qc.members.size(), qc.chunk_len, qc.nchunks, qc.slots};
+    std::memcpy(out + 8 * c, v, sizeof(v));
   }
   return PTYCHO_OK;
 }

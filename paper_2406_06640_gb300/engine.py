@@ -96,5 +96,9 @@ class ReconstructionBatch:
     def errors(self) -> list:
         return self._plan.errors()
 
+    def classes(self) -> list:
+        """The work-queue classes of this batch (shape, members, tuned chunk length, ...)."""
+        return self._plan.classes()
+
     def close(self):
         self._plan.close()

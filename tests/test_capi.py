@@ -106,3 +106,10 @@ def test_batch_validation_names_the_problem():
     assert lib.ptycho_plan_batch(2, arr, ip, pp, None, ctypes.byref(h)) == 1
     assert lib.ptycho_last_error().decode().startswith("problem 1:")
     assert lib.ptycho_plan_batch(0, arr, ip, pp, None, ctypes.byref(h)) == 1
+
+
+def test_batch_chunk_setting_is_validated():
+    lib = pg.load()
+    assert lib.ptycho_set_batch_chunk(7) == 1
+    assert lib.ptycho_set_batch_chunk(-8) == 1
+    assert lib.ptycho_set_batch_chunk(0) == 0

@@ -122,3 +122,38 @@ def test_batch_rejects_single_plan_calls():
     batch.iterate([O], [P], 1)
     assert len(batch.errors()) == 1
     batch.close()
+
+
+def test_autotuner_picks_a_chunk_length_caches_it_and_can_be_fixed():
+    import paper_2406_06640_gb300 as pg
+    from paper_2406_06640_gb300.engine import ReconstructionBatch
+
+    dev = torch.device("cuda:0")
+    probs = []
+    for i, side in enumerate((5, 6)):
+        p = make_problem(0, scan_side=side, obj_side=64 + 10 * side + 16, M=64, K=1, geometry="near", sigma=1.2)
+        probs.append((p, dict(p.params, sigma1=1.2, sigma2=1.2, kernel_size=7)))
+
+    def classes():
+        tens = [_tensors(dev, prob) for prob, _ in probs]
+        batch = ReconstructionBatch([(prm, t[0], prob.positions) for (prob, prm), t in zip(probs, tens)])
+        out = batch.classes()
+        batch.close()
+        return out
+
+    first = classes()
+    assert len(first) == 1 and first[0]["members"] == 2 and first[0]["M"] == 64 and first[0]["kh"] == 15
+    assert first[0]["chunk_len"] in (8, 16, 32, 64)
+    n = sum(-(-prob.N // first[0]["chunk_len"]) for prob, _ in probs)
+    assert first[0]["chunks"] == n and 1 <= first[0]["slots"] <= n
+    assert classes()[0]["chunk_len"] == first[0]["chunk_len"]  # cached for this shape class
+    pg.set_batch_chunk(32)
+    try:
+        assert classes()[0]["chunk_len"] == 32
+        O, P, E = _run_batch(dev, probs, 2)
+    finally:
+        pg.set_batch_chunk(0)
+    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)  # noqa: E731
+    for b, (prob, prm) in enumerate(probs):
+        Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), 2)
+        assert rel(O[b], Oo) < 1e-4 and rel(P[b], Po) < 1e-4 and abs(E[b] - Eo[-1]) / Eo[-1] < 1e-4, b
