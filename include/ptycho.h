@@ -160,6 +160,16 @@ ptycho_status ptycho_error_batch(ptycho_plan_t plan, double* nrmse_last);
  * 64; 0 restores tuning), e.g. for bitwise-reproducible runs across processes:
  * different L give the same result up to the FP32 order of the partial sums. */
 ptycho_status ptycho_set_batch_chunk(int32_t chunk_len);
+/* Staged path (M = 256): positions per chunk of the staged passes (their scratch
+ * holds chunk x K x M^2 complex values, so the chunk decides how much of it stays
+ * in L2). Chosen per (device, M, K, geometry, kernel width class) by timing one
+ * pass over all positions for 4, 8, 16 and 32 when the first such plan is built
+ * in the process, then cached. ptycho_set_staged_chunk fixes it for later plans
+ * (4, 8, 16 or 32; 0 restores tuning); the probe partials are per position of a
+ * chunk, so different chunks change only the FP32 order of their sums.
+ * ptycho_staged_chunk returns a plan's chunk (0 for M <= 128). */
+ptycho_status ptycho_set_staged_chunk(int32_t chunk);
+int32_t ptycho_staged_chunk(ptycho_plan_t plan);
 /* Describe the work-queue classes of a batch plan: for each of the first
  * max_classes classes, 8 int32 (M, K, near field, kernel width class 5 or 15,
  * members, chunk length, chunks, persistent clusters) into out; *count = the

@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     make_gen_spec,
     make_params,
     set_batch_chunk,
+    set_staged_chunk,
     version,
 )
 

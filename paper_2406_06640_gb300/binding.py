@@ -23,7 +23,7 @@ STEP_NORMALISED, STEP_RPIE = 0, 1
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
-            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
+            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
             "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
             "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart")
 
@@ -111,6 +111,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_error_batch.restype = st
     lib.ptycho_set_batch_chunk.argtypes = [ctypes.c_int32]
     lib.ptycho_set_batch_chunk.restype = st
+    lib.ptycho_set_staged_chunk.argtypes = [ctypes.c_int32]
+    lib.ptycho_set_staged_chunk.restype = st
+    lib.ptycho_staged_chunk.argtypes = [P]
+    lib.ptycho_staged_chunk.restype = ctypes.c_int32
     lib.ptycho_batch_classes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32)]
     lib.ptycho_batch_classes.restype = st
@@ -220,6 +224,9 @@ class Plan:
         c = ctypes.c_int32()
         _check(load().ptycho_profile_read(self._h, ctypes.byref(ms), ctypes.byref(c)))
         return ms.value, c.value
+
+    def staged_chunk(self) -> int:
+        return int(load().ptycho_staged_chunk(self._h))
 
     def launches_per_iteration(self, in_window: bool) -> int:
         return int(load().ptycho_launches_per_iteration(self._h, 1 if in_window else 0))
@@ -374,3 +381,8 @@ def generate(spec: dict, probe_ptr: int, params_ptr: int, n: int, first: int = 0
 def set_batch_chunk(chunk_len: int):
     """Fix the positions per work-queue chunk of later batch plans (8, 16, 32, 64; 0 = autotune)."""
     _check(load().ptycho_set_batch_chunk(chunk_len))
+
+
+def set_staged_chunk(chunk: int):
+    """Fix the positions per chunk of the staged M = 256 passes of later plans (4, 8, 16, 32; 0 = autotune)."""
+    _check(load().ptycho_set_staged_chunk(chunk))

@@ -66,6 +66,10 @@ constexpr int kQueueChunkMin = 8;
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
 int g_fixed_chunk = 0;
+// staged path (M = 256): positions per chunk of the staged passes, same key, and its fixed value
+constexpr int kStagedCandidates[] = {4, 8, 16, 32};
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_staged;
+int g_fixed_staged = 0;
 
 struct ptycho_plan_s {
   ptycho_params p{};
@@ -201,6 +205,59 @@ static bool is_device_pointer(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Autotuner of the staged path (M = 256): positions per chunk of the staged passes, timed on the
+// device for each candidate over one pass of all positions (object and probe from scratch buffers
+// of ones -- the passes only read them; they write the scratch, contributions and partials, which
+// the first real iteration overwrites), best of two after a warm-up.
+static ptycho_status tune_staged_chunk(ptycho_plan_s* pl, int* best) {
+  cudaStream_t s = pl->stream;
+  const ptycho_params& p = pl->p;
+  const size_t MM = (size_t)p.M * p.M;
+  float2 *d_o, *d_p;
+  PT_CUDA(pl->alloc(&d_o, (size_t)p.obj_h * p.obj_w), "alloc tuning object");
+  PT_CUDA(pl->alloc(&d_p, (size_t)p.K * MM), "alloc tuning probe");
+  {
+    std::vector<float2> ones(std::max((size_t)p.obj_h * p.obj_w, (size_t)p.K * MM), make_float2(1.f, 0.f));
+    PT_CUDA(cudaMemcpy(d_o, ones.data(), sizeof(float2) * p.obj_h * p.obj_w, cudaMemcpyHostToDevice), "tuning data");
+    PT_CUDA(cudaMemcpy(d_p, ones.data(), sizeof(float2) * p.K * MM, cudaMemcpyHostToDevice), "tuning data");
+  }
+  BigArgs ba = pl->ba;
+  ba.O = d_o;
+  ba.P = d_p;
+  cudaEvent_t e0, e1;
+  PT_CUDA(cudaEventCreate(&e0), "event");
+  PT_CUDA(cudaEventCreate(&e1), "event");
+  float best_ms = 1e30f;
+  *best = std::min(p.N, kStagedCandidates[0]);
+  cudaError_t ce = cudaSuccess;
+  for (int cand : kStagedCandidates) {
+    const int c = std::min(cand, pl->chunk);
+    if (cand > kStagedCandidates[0] && c != cand) break;  // larger candidates than N add nothing
+    float t_best = 1e30f;
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
+      ce = cudaEventRecord(e0, s);
+      for (int n0 = 0; n0 < p.N && ce == cudaSuccess; n0 += c) {
+        ba.n0 = n0;
+        ce = launch_big_chunk(ba, std::min(c, p.N - n0), s);
+      }
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce == cudaSuccess && r > 0) t_best = std::min(t_best, ms);
+    }
+    if (ce != cudaSuccess) break;
+    if (t_best < best_ms) {
+      best_ms = t_best;
+      *best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_fail(ce, "autotuner launch");
+  return PTYCHO_OK;
+}
+
 static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, const int32_t* positions) {
   const ptycho_params& p = pl->p;
   const int M = p.M, K = p.K, N = p.N;
@@ -225,7 +282,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   // the staged path (M = 256), whose per-slot partials are summed in slot order
   pl->big = M > 128;
   if (pl->big) {
-    pl->chunk = std::min(N, 16);
+    pl->chunk = std::min(N, kStagedCandidates[3]);  // buffers for the largest candidate; tuned below
     pl->slots = pl->chunk;
   } else {
     int max_slots = 0;
@@ -444,6 +501,24 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ba.errpart = d_errpart;
 
   PT_CUDA(cudaStreamSynchronize(s), "plan sync");
+  if (pl->big) {
+    const std::tuple<int, int, int, int, int> key{pl->device, M, K, fa.near_field, kh == 5 ? 5 : 15};
+    int c = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      if (g_fixed_staged > 0) c = g_fixed_staged;
+      else if (g_tune_staged.count(key)) c = g_tune_staged[key];
+    }
+    if (c == 0) {
+      ptycho_status st = tune_staged_chunk(pl, &c);
+      if (st != PTYCHO_OK) return st;
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_staged[key] = c;
+    }
+    pl->chunk = std::min(c, pl->chunk);  // a chunk holds at most N positions; buffers hold the largest
+    pl->slots = pl->chunk;
+    pl->ua.slots = pl->chunk;
+  }
   return PTYCHO_OK;
 }
 
@@ -858,6 +933,16 @@ ptycho_status ptycho_set_batch_chunk(int32_t chunk_len) {
   g_fixed_chunk = chunk_len;
   return PTYCHO_OK;
 }
+
+ptycho_status ptycho_set_staged_chunk(int32_t chunk) {
+  if (chunk != 0 && chunk != 4 && chunk != 8 && chunk != 16 && chunk != 32)
+    return fail(PTYCHO_EINVAL, "staged chunk must be 0 (autotune), 4, 8, 16 or 32");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_fixed_staged = chunk;
+  return PTYCHO_OK;
+}
+
+int32_t ptycho_staged_chunk(ptycho_plan_t pl) { return (pl && pl->big) ? pl->chunk : 0; }
 
 ptycho_status ptycho_batch_classes(ptycho_plan_t pl, int32_t max_classes, int32_t* out, int32_t* count) {
   if (!pl || pl->members.empty() || !count || max_classes < 0 || (max_classes > 0 && !out))

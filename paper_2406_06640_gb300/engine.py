@@ -60,6 +60,10 @@ class Reconstruction:
     def launches_per_iteration(self, in_window: bool) -> int:
         return self._plan.launches_per_iteration(in_window)
 
+    def staged_chunk(self) -> int:
+        """Positions per chunk of the staged M = 256 passes (0 for M <= 128)."""
+        return self._plan.staged_chunk()
+
     def close(self):
         self._plan.close()
 

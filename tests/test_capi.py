@@ -113,3 +113,5 @@ def test_batch_chunk_setting_is_validated():
     assert lib.ptycho_set_batch_chunk(7) == 1
     assert lib.ptycho_set_batch_chunk(-8) == 1
     assert lib.ptycho_set_batch_chunk(0) == 0
+    assert lib.ptycho_set_staged_chunk(12) == 1
+    assert lib.ptycho_set_staged_chunk(0) == 0

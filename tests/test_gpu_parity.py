@@ -132,6 +132,29 @@ def test_m256_far_field_two_chunks_wide_kernel():
     check(p, prm, 2)
 
 
+@pytest.mark.parametrize("chunk", [0, 4, 32])
+def test_m256_staged_chunk_sizes(chunk):
+    """The staged path at a tuned (0) or fixed chunk size: 20 positions (five chunks of 4, one of 20),
+    near field, two modes."""
+    import paper_2406_06640_gb300 as pg
+    from paper_2406_06640_gb300.engine import Reconstruction
+
+    p = make_problem(0, scan_side=5, obj_side=400, M=256, K=2, geometry="near", sigma=1.5)
+    p.positions = p.positions[:20].copy()
+    p.I = p.I[:20].copy()
+    prm = dict(p.params, N=20, sigma1=1.5, sigma2=1.5)
+    pg.set_staged_chunk(chunk)
+    try:
+        check(p, prm, 2)
+        dev = _dev()
+        rec = Reconstruction(prm, torch.from_numpy(p.I).to(dev), p.positions)
+        got = rec.staged_chunk()
+        rec.close()
+    finally:
+        pg.set_staged_chunk(0)
+    assert got in (4, 8, 16, 20) if chunk == 0 else got == min(chunk, 20)
+
+
 def test_config2_full_size_one_iteration():
     """Full configuration 2 (near field F = 10, M = 256, K = 8, 256 positions, 1024^2 object)."""
     p = make_problem(2)
