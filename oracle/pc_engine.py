@@ -51,6 +51,8 @@ from typing import Sequence
 import numpy as np
 from scipy import signal
 
+from . import philox
+
 A_MIN = 1e-6
 PHI_FLOOR = 1e-30
 
@@ -83,6 +85,8 @@ class Params:
     step_rule: str = "normalised"  # "normalised" | "rpie"
     rpie_alpha_obj: float = 0.0
     rpie_alpha_probe: float = 0.0
+    minibatch: int = 0  # 0: every position in one simultaneous step; B >= 1: batches of B positions
+    order_seed: int = 0  # key of the batch partition and of each iteration's visiting order
 
     @classmethod
     def from_dict(cls, d):
@@ -223,24 +227,24 @@ def step_coefficients(prm: "Params"):
     return (1.0, prm.delta_obj), (1.0, prm.delta_probe)
 
 
-def iteration(I: np.ndarray, positions: np.ndarray, O: np.ndarray, P: np.ndarray, prm: Params,
-              t: int, eps: float, g: np.ndarray):
-    """One simultaneous pc-engine iteration. Returns (O_new, P_new, E_t) in complex128."""
+def _batch_step(I, positions, idx, O, P, prm: Params, t: int, eps: float, g):
+    """The simultaneous normalised step over the positions idx (Fig. 1 boxes 1 and 2 for each,
+    then one update of O and P from the old O and P). Returns (O_new, P_new, [error numerators])."""
     M, K = prm.M, prm.K
     NO = np.zeros(O.shape, np.complex128)
     DO = np.zeros(O.shape, np.float64)
     NP = np.zeros(P.shape, np.complex128)
     DP = np.zeros((M, M), np.float64)
     P2 = np.sum(np.abs(P) ** 2, axis=0)
-    errnum, errden = [], []
-    for n, (y, x) in enumerate(positions):
+    errnum = []
+    for n in idx:
+        y, x = positions[n]
         o = O[y:y + M, x:x + M]
         psi = P * o[None]
         Psi = propagate_forward(psi, prm)
-        Psi_new, Ihat = modulus(Psi, I[n].astype(np.float64), g, eps, prm.blur_domain)
         In = I[n].astype(np.float64)
+        Psi_new, Ihat = modulus(Psi, In, g, eps, prm.blur_domain)
         errnum.append(math.fsum(((Ihat - In) ** 2).ravel()))
-        errden.append(math.fsum((In ** 2).ravel()))
         dpsi = propagate_backward(Psi_new, prm) - psi
         NO[y:y + M, x:x + M] += np.sum(np.conj(P) * dpsi, axis=0)
         DO[y:y + M, x:x + M] += P2
@@ -252,10 +256,42 @@ def iteration(I: np.ndarray, positions: np.ndarray, O: np.ndarray, P: np.ndarray
         P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, *c_probe) for k in range(K)])
     else:
         P_new = P.copy()
+    return O_new, P_new, errnum
+
+
+def batches(N: int, prm: Params):
+    """Partition of the positions into batches of prm.minibatch (reading 11b): consecutive groups of
+    a Philox permutation of 0..N-1 (stream 3); one batch of every position when minibatch is 0."""
+    if prm.minibatch <= 0 or prm.minibatch >= N:
+        return [np.arange(N)]
+    perm = philox.permutation(N, prm.order_seed, 3, 0)
+    return [perm[b:b + prm.minibatch] for b in range(0, N, prm.minibatch)]
+
+
+def visit_order(nb: int, prm: Params, t: int):
+    """Order in which iteration t visits the batches: a Philox permutation (stream 4, counter t)."""
+    return philox.permutation(nb, prm.order_seed, 4, t) if nb > 1 else np.arange(nb)
+
+
+def iteration(I: np.ndarray, positions: np.ndarray, O: np.ndarray, P: np.ndarray, prm: Params,
+              t: int, eps: float, g: np.ndarray, parts=None):
+    """One pc-engine iteration. Returns (O_new, P_new, E_t) in complex128.
+
+    Without mini-batches: one simultaneous step over every position. With batches (the paper's
+    sequential pc-ePIE of Fig. 1 for batches of one position): the batches are visited in the
+    iteration's order, each step starting from the object and probe the previous one left; the
+    complex constraint (inside its windows) follows the last batch, over every box; E_t sums the
+    error numerators of all positions, each at the state its batch saw."""
+    parts = batches(len(positions), prm) if parts is None else parts
+    errnum = []
+    for b in visit_order(len(parts), prm, t):
+        O, P, en = _batch_step(I, positions, parts[b], O, P, prm, t, eps, g)
+        errnum += en
     if in_window(t, prm.windows):
-        O_new = complex_constraint(O_new, positions, prm)
+        O = complex_constraint(O, positions, prm)
+    errden = [math.fsum((I[n].astype(np.float64) ** 2).ravel()) for n in range(len(positions))]
     E = math.sqrt(math.fsum(errnum) / math.fsum(errden))
-    return O_new, P_new, E
+    return O, P, E
 
 
 def iterate(I, positions, O, P, prm: Params, n_iter: int):
@@ -270,8 +306,9 @@ def iterate(I, positions, O, P, prm: Params, n_iter: int):
     eps = prm.eps_mod if prm.eps_mod > 0 else default_eps(I)
     g = gaussian_kernel(prm.kernel_size, prm.sigma1, prm.sigma2)
     errors = []
+    parts = batches(len(positions), prm)
     for i in range(n_iter):
         t = prm.start_iteration + i
-        O, P, E = iteration(I, positions, O, P, prm, t, eps, g)
+        O, P, E = iteration(I, positions, O, P, prm, t, eps, g, parts)
         errors.append(E)
     return O, P, np.array(errors)

@@ -33,30 +33,8 @@ import numpy as np
 
 from .pc_engine import Params, blur, propagate_forward
 
-_M0, _M1 = 0xD2511F53, 0xCD9E8D57
-_W0, _W1 = 0x9E3779B9, 0xBB67AE85
+from .philox import key_words, philox4x32_10  # noqa: F401  (re-exported)
 _MASK = 0xFFFFFFFF
-
-
-def philox4x32_10(counter, key):
-    """counter: (..., 4) uint32-valued array; key: (2,) or (..., 2). Returns (..., 4) uint64 words < 2^32."""
-    c = np.array(counter, dtype=np.uint64) & _MASK
-    k = np.broadcast_to(np.array(key, dtype=np.uint64) & _MASK, c.shape[:-1] + (2,)).copy()
-    c0, c1, c2, c3 = (c[..., i].copy() for i in range(4))
-    k0, k1 = k[..., 0].copy(), k[..., 1].copy()
-    for _ in range(10):
-        p0 = np.uint64(_M0) * c0          # < 2^64: exact in uint64
-        p1 = np.uint64(_M1) * c2
-        hi0, lo0 = p0 >> np.uint64(32), p0 & np.uint64(_MASK)
-        hi1, lo1 = p1 >> np.uint64(32), p1 & np.uint64(_MASK)
-        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
-        k0 = (k0 + np.uint64(_W0)) & np.uint64(_MASK)
-        k1 = (k1 + np.uint64(_W1)) & np.uint64(_MASK)
-    return np.stack([c0, c1, c2, c3], axis=-1)
-
-
-def key_words(key64: int):
-    return (key64 & _MASK, (key64 >> 32) & _MASK)
 
 
 def vacancy_threshold(vacancy: float) -> int:

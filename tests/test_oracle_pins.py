@@ -323,6 +323,72 @@ def test_p6c_rpie_is_a_rescaled_normalised_step_and_keeps_the_fixed_point():
         pe.iterate(I, pos, O, P, pe.Params(**base, step_rule="sequential"), 1)
 
 
+# ------------------------------------------------------------------------ mini-batch (sequential) engine
+
+def test_philox_permutation():
+    from oracle import philox
+
+    a = philox.permutation(10, 99, 4, 1)
+    assert sorted(a.tolist()) == list(range(10))
+    assert np.array_equal(a, philox.permutation(10, 99, 4, 1))
+    assert not np.array_equal(a, philox.permutation(10, 99, 4, 2))
+    assert not np.array_equal(a, philox.permutation(10, 98, 4, 1))
+    # every position lands in exactly one batch
+    prm = pe.Params(M=8, K=1, N=23, obj_h=8, obj_w=8, minibatch=5, order_seed=3)
+    parts = pe.batches(23, prm)
+    assert [len(b) for b in parts] == [5, 5, 5, 5, 3]
+    assert sorted(np.concatenate(parts).tolist()) == list(range(23))
+
+
+def test_minibatch_of_one_is_textbook_epie():
+    """Batches of one position with the rPIE weight 1 on both steps are the ePIE engine (Fig. 1 with
+    sigma = 0, K = 1): for each position in the iteration's order, psi' = the projection of P o,
+    o += conj(P) (psi' - psi) / max|P|^2, P += conj(o_old) (psi' - psi) / max|o_old|^2."""
+    rng = _rng(21)
+    M, side = 16, 28
+    O0 = (0.5 + rng.random((side, side))) * np.exp(1j * rng.random((side, side)))
+    P0 = _crandn(rng, 1, M, M)
+    pos = np.array([(0, 0), (0, 12), (12, 0), (12, 12), (6, 6)])
+    I = rng.random((len(pos), M, M)) * 10
+    prm = pe.Params(M=M, K=1, N=len(pos), obj_h=side, obj_w=side, sigma1=0, sigma2=0, eps_mod=1e-300,
+                    step_rule="rpie", rpie_alpha_obj=1.0, rpie_alpha_probe=1.0, minibatch=1, order_seed=5)
+    O1, P1, E1 = pe.iterate(I, pos, O0, P0, prm, 2)
+    O, P = O0.copy(), P0[0].copy()
+    parts = pe.batches(len(pos), prm)
+    for t in (1, 2):
+        for b in pe.visit_order(len(parts), prm, t):
+            n = int(parts[b][0])
+            y, x = pos[n]
+            o = O[y:y + M, x:x + M].copy()
+            psi = P * o
+            Psi = np.fft.fftshift(np.fft.fft2(psi))
+            Psi_p = np.sqrt(np.fft.fftshift(np.fft.ifftshift(I[n]))) * Psi / np.abs(Psi)
+            d = np.fft.ifft2(np.fft.ifftshift(Psi_p)) - psi
+            O[y:y + M, x:x + M] = o + np.conj(P) * d / np.max(np.abs(P) ** 2)
+            P = P + np.conj(o) * d / np.max(np.abs(o) ** 2)
+    assert np.max(np.abs(O1 - O)) < 1e-10 * np.max(np.abs(O))
+    assert np.max(np.abs(P1[0] - P)) < 1e-10 * np.max(np.abs(P))
+
+
+def test_minibatch_of_all_positions_is_the_simultaneous_step_and_keeps_the_fixed_point():
+    rng = _rng(22)
+    M, side = 16, 28
+    O = (0.5 + rng.random((side, side))) * np.exp(1j * rng.random((side, side)))
+    P = _crandn(rng, 2, M, M)
+    pos = np.array([(0, 0), (0, 12), (12, 0), (12, 12), (6, 6)])
+    base = dict(M=M, K=2, N=len(pos), obj_h=side, obj_w=side, sigma1=1.0, sigma2=0.6, eps_mod=1e-300)
+    I = rng.random((len(pos), M, M)) * 5
+    a = pe.iterate(I, pos, O, P, pe.Params(**base), 2)
+    b = pe.iterate(I, pos, O, P, pe.Params(**base, minibatch=len(pos), order_seed=9), 2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    c = pe.iterate(I, pos, O, P, pe.Params(**base, minibatch=2, order_seed=9), 2)
+    assert np.max(np.abs(c[0] - a[0])) > 1e-6  # batches change the result
+    prm = pe.Params(**base, minibatch=2, order_seed=9)
+    Ic = _consistent_data(O, P, pos, prm)
+    O1, P1, E = pe.iterate(Ic, pos, O, P, prm, 2)
+    assert np.max(np.abs(O1 - O)) < 1e-12 and np.max(np.abs(P1 - P)) < 1e-12 and max(E) < 1e-12
+
+
 # ------------------------------------------------------------------------ P7 / P8: coherent reduction, modes
 
 def _minimal_coherent_engine(I, pos, O, P, n_iter, delta):
