@@ -94,6 +94,16 @@ typedef struct {
    * floor. Pixels with a zero denominator are left unchanged under both rules. */
   int32_t step_rule;             /* PTYCHO_STEP_NORMALISED (0) or PTYCHO_STEP_RPIE (1) */
   double rpie_alpha_obj, rpie_alpha_probe;
+  /* Mini-batch (sequential) engine, the paper's pc-ePIE of Fig. 1 for minibatch = 1: 0 (default)
+   * or >= N runs every position in one simultaneous step. Otherwise the positions are split into
+   * batches of `minibatch` by a Philox4x32-10 permutation keyed by order_seed (ptycho_permutation
+   * with stream 3, t = 0, consecutive groups), and iteration t visits the batches in the order of
+   * ptycho_permutation(batches, order_seed, 4, t); each batch takes one step of the rule above over
+   * its own positions, from the object and probe the previous batch left. The complex constraint
+   * (inside its windows) follows the last batch; E_t sums every position's error numerator at the
+   * state its batch saw. M <= 128 only; not available in batch plans or ptycho_iterate_static. */
+  int32_t minibatch;
+  uint64_t order_seed;
 } ptycho_params;
 
 /* Build a plan on the current CUDA device.
@@ -306,6 +316,12 @@ ptycho_status ptycho_generate(const ptycho_gen_spec* spec, const void* probe, co
 ptycho_status ptycho_warmstart(ptycho_unet_t net, const float* intensities, const int32_t* positions, int32_t N,
                                int32_t obj_h, int32_t obj_w, double target_scale, void* object_out,
                                double* sigma_out);
+
+/* The Philox permutation of 0..n-1 a mini-batch plan uses (Fisher-Yates: for i = n-1 .. 1,
+ * j = (w (i + 1)) >> 32 with w the first word of Philox4x32-10((i, t, stream, 5), key = seed
+ * as two 32-bit words, low first); out: host, n int32. For reproducing a plan's batches (stream 3,
+ * t = 0) and visiting order (stream 4, iteration t). */
+ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32_t t, int32_t* out);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ptycho_last_error(void);

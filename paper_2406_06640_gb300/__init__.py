@@ -20,6 +20,7 @@ from .binding import (  # noqa: F401
     load,
     make_gen_spec,
     make_params,
+    permutation,
     set_batch_chunk,
     set_staged_chunk,
     version,

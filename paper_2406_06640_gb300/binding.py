@@ -23,7 +23,7 @@ STEP_NORMALISED, STEP_RPIE = 0, 1
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
-            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
+            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_permutation", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
             "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
             "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart")
 
@@ -51,6 +51,7 @@ class PtychoParams(ctypes.Structure):
         ("n_windows", ctypes.c_int32), ("windows", ctypes.POINTER(ctypes.c_int32)),
         ("start_iteration", ctypes.c_int32),
         ("step_rule", ctypes.c_int32), ("rpie_alpha_obj", ctypes.c_double), ("rpie_alpha_probe", ctypes.c_double),
+        ("minibatch", ctypes.c_int32), ("order_seed", ctypes.c_uint64),
     ]
 
 
@@ -111,6 +112,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_error_batch.restype = st
     lib.ptycho_set_batch_chunk.argtypes = [ctypes.c_int32]
     lib.ptycho_set_batch_chunk.restype = st
+    lib.ptycho_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)]
+    lib.ptycho_permutation.restype = st
     lib.ptycho_set_staged_chunk.argtypes = [ctypes.c_int32]
     lib.ptycho_set_staged_chunk.restype = st
     lib.ptycho_staged_chunk.argtypes = [P]
@@ -187,6 +191,8 @@ def make_params(d: dict) -> tuple:
     p.step_rule = int(rule)
     p.rpie_alpha_obj = float(d.get("rpie_alpha_obj", 0.0))
     p.rpie_alpha_probe = float(d.get("rpie_alpha_probe", 0.0))
+    p.minibatch = int(d.get("minibatch", 0))
+    p.order_seed = int(d.get("order_seed", 0)) & ((1 << 64) - 1)
     return p, arr
 
 
@@ -386,3 +392,10 @@ def set_batch_chunk(chunk_len: int):
 def set_staged_chunk(chunk: int):
     """Fix the positions per chunk of the staged M = 256 passes of later plans (4, 8, 16, 32; 0 = autotune)."""
     _check(load().ptycho_set_staged_chunk(chunk))
+
+
+def permutation(n: int, seed: int, stream: int, t: int) -> list:
+    """ptycho_permutation: the Philox permutation of 0..n-1 that mini-batch plans use."""
+    out = (ctypes.c_int32 * max(n, 1))()
+    _check(load().ptycho_permutation(n, seed & ((1 << 64) - 1), stream, t, out))
+    return list(out[:n])

@@ -71,6 +71,36 @@ constexpr int kStagedCandidates[] = {4, 8, 16, 32};
 std::map<std::tuple<int, int, int, int, int>, int> g_tune_staged;
 int g_fixed_staged = 0;
 
+// Philox4x32-10 on the host (Salmon et al., SC'11) and the Fisher-Yates permutation of 0..n-1 that
+// mini-batch plans draw their batches (stream 3, t = 0) and visiting orders (stream 4, t) from:
+// for i = n-1 .. 1, j = (w (i + 1)) >> 32 with w the first word of Philox((i, t, stream, 5), seed).
+static uint32_t philox_first_word(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key) {
+  uint32_t k0 = (uint32_t)(key & 0xffffffffu), k1 = (uint32_t)(key >> 32);
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c0;
+}
+
+static std::vector<int> philox_permutation(int n, uint64_t seed, uint32_t stream, uint32_t t) {
+  std::vector<int> a(std::max(n, 0));
+  for (int i = 0; i < n; ++i) a[i] = i;
+  for (int i = n - 1; i >= 1; --i) {
+    const uint32_t w = philox_first_word((uint32_t)i, t, stream, 5u, seed);
+    const int j = (int)(((uint64_t)w * (uint64_t)(i + 1)) >> 32);
+    std::swap(a[i], a[j]);
+  }
+  return a;
+}
+
 struct ptycho_plan_s {
   ptycho_params p{};
   std::vector<int32_t> windows;
@@ -98,6 +128,11 @@ struct ptycho_plan_s {
   int chunk = 0;
   // batch member drained by a work-queue launch: number of position chunks (its partial count)
   int parts = 0;
+  // mini-batch engine: batch size (0: off), number of batches, per-batch tile lists (nb x (tiles + 1)
+  // offsets into one entry array), running FP64 error of the current iteration
+  int mb = 0, nb = 1, tiles = 0;
+  int* d_starts = nullptr;
+  double* d_err_acc = nullptr;
   // batch plans: one work-queue launch per shape class (M, K, geometry, kernel width class)
   struct QueueClass {
     int M = 0, K = 0, near = 0, kh = 0;
@@ -173,6 +208,9 @@ static ptycho_status validate(const ptycho_params* p) {
     if (p->windows[2 * i] < 1 || p->windows[2 * i] > p->windows[2 * i + 1])
       return fail(PTYCHO_EINVAL, "windows must be [first, last] with 1 <= first <= last");
   if (p->start_iteration < 1) return fail(PTYCHO_EINVAL, "start_iteration must be >= 1");
+  if (p->minibatch < 0) return fail(PTYCHO_EINVAL, "minibatch must be >= 0");
+  if (p->minibatch > 0 && p->minibatch < p->N && p->M > 128)
+    return fail(PTYCHO_EUNSUPPORTED, "the mini-batch engine handles M <= 128");
   if (p->step_rule != PTYCHO_STEP_NORMALISED && p->step_rule != PTYCHO_STEP_RPIE)
     return fail(PTYCHO_EINVAL, "step_rule must be PTYCHO_STEP_NORMALISED or PTYCHO_STEP_RPIE");
   if (p->step_rule == PTYCHO_STEP_RPIE &&
@@ -277,6 +315,17 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
       return fail(PTYCHO_EINVAL, "position " + std::to_string(n) + " puts its box outside the object");
   }
   if (!is_device_pointer(intensities)) return fail(PTYCHO_EINVAL, "intensities must be a device pointer");
+  // ---- mini-batch engine: positions (and below, their patterns) stored in the order of the batch
+  // partition, so batch b is the contiguous range [b mb, min(N, (b + 1) mb))
+  std::vector<int> order;
+  if (p.minibatch > 0 && p.minibatch < N) {
+    pl->mb = p.minibatch;
+    pl->nb = (N + pl->mb - 1) / pl->mb;
+    order = philox_permutation(N, p.order_seed, 3u, 0u);
+    std::vector<int2> perm(N);
+    for (int i = 0; i < N; ++i) perm[i] = pl->h_pos[order[i]];
+    pl->h_pos = perm;
+  }
 
   // ---- slots: co-resident clusters of the fused kernel (M <= 128), or the position chunk of
   // the staged path (M = 256), whose per-slot partials are summed in slot order
@@ -300,7 +349,15 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   int2* d_pos;
   PT_CUDA(pl->alloc(&d_I, (size_t)N * MM), "alloc intensities");
   PT_CUDA(pl->alloc(&d_pos, (size_t)N), "alloc positions");
-  PT_CUDA(cudaMemcpyAsync(d_I, intensities, sizeof(float) * N * MM, cudaMemcpyDeviceToDevice, s), "copy intensities");
+  if (order.empty()) {
+    PT_CUDA(cudaMemcpyAsync(d_I, intensities, sizeof(float) * N * MM, cudaMemcpyDeviceToDevice, s),
+            "copy intensities");
+  } else {
+    for (int i = 0; i < N; ++i)
+      PT_CUDA(cudaMemcpyAsync(d_I + (size_t)i * MM, intensities + (size_t)order[i] * MM, sizeof(float) * MM,
+                              cudaMemcpyDeviceToDevice, s),
+              "copy intensities");
+  }
   PT_CUDA(cudaMemcpyAsync(d_pos, pl->h_pos.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, s), "copy positions");
 
   // plan-time FP64 sums: sum I (for eps), sum I^2 (error denominator), bad values
@@ -360,17 +417,23 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
 
   // object tiles and their position lists (increasing n)
   const int tx = (p.obj_w + kObjTile - 1) / kObjTile, ty = (p.obj_h + kObjTile - 1) / kObjTile;
-  std::vector<std::vector<int>> lists((size_t)tx * ty);
-  for (int n = 0; n < N; ++n) {
-    const int2 q = pl->h_pos[n];
-    for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
-      for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
-  }
-  std::vector<int> start((size_t)tx * ty + 1, 0);
+  // one list per batch (the whole scan when there are no mini-batches), offsets into one entry array
+  pl->tiles = tx * ty;
+  const int bsize = pl->mb > 0 ? pl->mb : N;
+  std::vector<int> start;
   std::vector<int4> flat;
-  for (size_t i = 0; i < lists.size(); ++i) {
-    start[i + 1] = start[i] + (int)lists[i].size();
-    for (int n : lists[i]) flat.push_back(make_int4(n, pl->h_pos[n].x, pl->h_pos[n].y, 0));
+  for (int b = 0; b < pl->nb; ++b) {
+    std::vector<std::vector<int>> lists((size_t)tx * ty);
+    for (int n = b * bsize; n < std::min(N, (b + 1) * bsize); ++n) {
+      const int2 q = pl->h_pos[n];
+      for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
+        for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
+    }
+    for (size_t i = 0; i < lists.size(); ++i) {
+      start.push_back((int)flat.size());
+      for (int n : lists[i]) flat.push_back(make_int4(n, pl->h_pos[n].x, pl->h_pos[n].y, 0));
+    }
+    start.push_back((int)flat.size());
   }
   int* d_start;
   int4* d_list;
@@ -379,6 +442,9 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(cudaMemcpy(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice), "copy tiles");
   if (!flat.empty())
     PT_CUDA(cudaMemcpy(d_list, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice), "copy tiles");
+  pl->d_starts = d_start;
+  PT_CUDA(pl->alloc(&pl->d_err_acc, 1), "alloc error accumulator");
+  PT_CUDA(cudaMemset(pl->d_err_acc, 0, sizeof(double)), "clear error accumulator");
 
   const size_t plane = (size_t)p.obj_h * p.obj_w;
   float2* d_no;
@@ -574,6 +640,37 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
       ba.n0 = n0;
       PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, pl->p.N - n0), s), "staged pass launch");
     }
+  } else if (pl->mb > 0) {
+    // mini-batch engine: the batches in this iteration's order, each a fused launch over its own
+    // positions followed by its update; the error accumulates over the batches
+    const size_t MM = (size_t)pl->p.M * pl->p.M;
+    const std::vector<int> visit = philox_permutation(pl->nb, pl->p.order_seed, 4u, (uint32_t)t);
+    ua.update_probe = t >= pl->p.probe_update_start;
+    for (int j = 0; j < pl->nb; ++j) {
+      const int b = visit[j];
+      const int s0 = b * pl->mb, len = std::min(pl->mb, pl->p.N - s0);
+      FusedArgs fb = fa;
+      fb.I = fa.I + (size_t)s0 * MM;
+      fb.sqrtI = fa.sqrtI + (size_t)s0 * MM;
+      fb.pos = fa.pos + s0;
+      fb.N = len;
+      fb.cn = fa.cn + (size_t)s0 * MM;
+      const int slots = std::min(pl->slots, len);
+      PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
+      UpdateArgs ub = ua;
+      ub.tile_start = pl->d_starts + (size_t)b * (pl->tiles + 1);
+      ub.slots = slots;
+      ub.nerr = slots * pl->p.K;
+      ub.err_mode = j + 1 < pl->nb ? 1 : 2;
+      ub.err_acc = pl->d_err_acc;
+      PT_CUDA(launch_update(ub, s), "update launch");
+    }
+    if (pl->profiling) {
+      PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], s), "profile event");
+      pl->prof_count++;
+    }
+    if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
+    return PTYCHO_OK;
   } else {
     PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, s), "fused kernel launch");
   }
@@ -728,6 +825,8 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
     ptycho_status st = validate(params[b]);
     if (st == PTYCHO_OK && (!intensities[b] || !positions[b]))
       st = fail(PTYCHO_EINVAL, "intensities and positions must be non-NULL");
+    if (st == PTYCHO_OK && params[b]->minibatch > 0 && params[b]->minibatch < params[b]->N)
+      st = fail(PTYCHO_EUNSUPPORTED, "mini-batch problems run through ptycho_plan");
     if (st != PTYCHO_OK) return fail(st, "problem " + std::to_string(b) + ": " + g_last_error);
   }
   ptycho_plan_s* pl = new (std::nothrow) ptycho_plan_s();
@@ -1048,7 +1147,15 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
     const int chunks = (pl->p.N + pl->chunk - 1) / pl->chunk;
     fft = chunks * (pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5);
   }
+  if (pl->mb > 0) fft = pl->nb * 6 - 5;  // per batch: the fused kernel and the 5 update kernels
   return fft + 5 + (in_window ? 6 : 0);
+}
+
+ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32_t t, int32_t* out) {
+  if (n < 0 || (n > 0 && !out)) return fail(PTYCHO_EINVAL, "need n >= 0 and an output array");
+  const std::vector<int> a = philox_permutation(n, seed, (uint32_t)stream, (uint32_t)t);
+  for (int i = 0; i < n; ++i) out[i] = a[i];
+  return PTYCHO_OK;
 }
 
 const char* ptycho_last_error(void) { return g_last_error.c_str(); }

@@ -118,6 +118,10 @@ struct UpdateArgs {
   int probe_blocks;
   double* errhist; double errden;
   unsigned long long* run_counter;  // device: iterations finished; E goes to errhist[counter % kErrHistory]
+  // error of a launch: 0 finishes E from this launch's partials; 1 adds them to *err_acc (a batch
+  // of a mini-batch iteration); 2 adds them and finishes E from the total, clearing *err_acc
+  int err_mode;
+  double* err_acc;
   // step = beta num / (c_d d + c_max max d): normalised rule (1, delta), rPIE rule (1 - a, a)
   float beta_obj, beta_probe, cd_obj, cmax_obj, cd_probe, cmax_probe;
   int update_probe;

@@ -247,9 +247,15 @@ __global__ void k_probe_apply(const UpdateArgs u) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     double e = 0.0;
     for (int s = 0; s < u.nerr; ++s) e += u.errpart[s];
-    const unsigned long long r = *u.run_counter;
-    u.errhist[r % kErrHistory] = sqrt(e / u.errden);
-    *u.run_counter = r + 1;
+    if (u.err_mode != 0) e += *u.err_acc;
+    if (u.err_mode == 1) {
+      *u.err_acc = e;
+    } else {
+      const unsigned long long r = *u.run_counter;
+      u.errhist[r % kErrHistory] = sqrt(e / u.errden);
+      *u.run_counter = r + 1;
+      if (u.err_mode == 2) *u.err_acc = 0.0;
+    }
   }
   if (!u.update_probe) return;
   const int MM = u.M * u.M;

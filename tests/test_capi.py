@@ -71,7 +71,8 @@ def _plan_status(**over):
     (dict(cbar_min=0.0), 1), (dict(cbar_min=2.0, cbar_max=1.0), 1), (dict(windows=[(0, 3)]), 1),
     (dict(windows=[(5, 4)]), 1), (dict(start_iteration=0), 1), (dict(delta_obj=-1.0), 1),
     (dict(eps_mod=float("nan")), 1), (dict(step_rule=2), 1), (dict(step_rule="rpie", rpie_alpha_obj=1.5), 1),
-    (dict(step_rule="rpie", rpie_alpha_probe=-0.1), 1),
+    (dict(step_rule="rpie", rpie_alpha_probe=-0.1), 1), (dict(minibatch=-1), 1),
+    (dict(M=256, obj_h=300, obj_w=300, minibatch=2), 4),
 ])
 def test_validation_rejects_bad_requests(over, expect):
     st, msg = _plan_status(**over)
@@ -115,3 +116,11 @@ def test_batch_chunk_setting_is_validated():
     assert lib.ptycho_set_batch_chunk(0) == 0
     assert lib.ptycho_set_staged_chunk(12) == 1
     assert lib.ptycho_set_staged_chunk(0) == 0
+
+
+@pytest.mark.parametrize("n,seed,stream,t", [(1, 0, 3, 0), (2, 5, 3, 0), (37, 123456789012345, 4, 7),
+                                             (100, 2 ** 64 - 1, 3, 0), (9, 42, 4, 4096)])
+def test_host_permutation_matches_the_oracle(n, seed, stream, t):
+    from oracle import philox
+
+    assert pg.permutation(n, seed, stream, t) == philox.permutation(n, seed, stream, t).tolist()
