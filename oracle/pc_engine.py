@@ -85,6 +85,7 @@ class Params:
     step_rule: str = "normalised"  # "normalised" | "rpie"
     rpie_alpha_obj: float = 0.0
     rpie_alpha_probe: float = 0.0
+    engine: str = "pie"  # "pie": the step of reading 4 / 10b / 10c; "dm": pc-DM (reading 10d)
     minibatch: int = 0  # 0: every position in one simultaneous step; B >= 1: batches of B positions
     order_seed: int = 0  # key of the batch partition and of each iteration's visiting order
 
@@ -259,6 +260,43 @@ def _batch_step(I, positions, idx, O, P, prm: Params, t: int, eps: float, g):
     return O_new, P_new, errnum
 
 
+def iteration_dm(I, positions, O, P, psi, prm: Params, t: int, eps: float, g):
+    """One pc-DM iteration (reading 10d; difference map of Thibault et al. with the pc intensity model
+    of Fig. 1 box 1 in its modulus projection). psi: exit-wave state, (N, K, M, M), updated in place.
+    Per position: psi_ov = P o_n, chi = 2 psi_ov - psi_n, psi_n <- psi_n + Pi_F(chi) - psi_ov; then the
+    overlap projection as one normalised step with dpsi = psi_n - psi_ov. E_t from Pi_F's input."""
+    M, K = prm.M, prm.K
+    NO = np.zeros(O.shape, np.complex128)
+    DO = np.zeros(O.shape, np.float64)
+    NP = np.zeros(P.shape, np.complex128)
+    DP = np.zeros((M, M), np.float64)
+    P2 = np.sum(np.abs(P) ** 2, axis=0)
+    errnum, errden = [], []
+    for n, (y, x) in enumerate(positions):
+        o = O[y:y + M, x:x + M]
+        psi_ov = P * o[None]
+        chi = 2.0 * psi_ov - psi[n]
+        In = I[n].astype(np.float64)
+        Chi_new, Ihat = modulus(propagate_forward(chi, prm), In, g, eps, prm.blur_domain)
+        errnum.append(math.fsum(((Ihat - In) ** 2).ravel()))
+        errden.append(math.fsum((In ** 2).ravel()))
+        psi[n] = psi[n] + propagate_backward(Chi_new, prm) - psi_ov
+        dpsi = psi[n] - psi_ov
+        NO[y:y + M, x:x + M] += np.sum(np.conj(P) * dpsi, axis=0)
+        DO[y:y + M, x:x + M] += P2
+        NP += np.conj(o)[None] * dpsi
+        DP += np.abs(o) ** 2
+    c_obj, c_probe = step_coefficients(prm)
+    O_new = O + _normalised_step(prm.beta_obj, NO, DO, *c_obj)
+    if t >= prm.probe_update_start:
+        P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, *c_probe) for k in range(K)])
+    else:
+        P_new = P.copy()
+    if in_window(t, prm.windows):
+        O_new = complex_constraint(O_new, positions, prm)
+    return O_new, P_new, math.sqrt(math.fsum(errnum) / math.fsum(errden))
+
+
 def batches(N: int, prm: Params):
     """Partition of the positions into batches of prm.minibatch (reading 11b): consecutive groups of
     a Philox permutation of 0..N-1 (stream 3); one batch of every position when minibatch is 0."""
@@ -306,6 +344,16 @@ def iterate(I, positions, O, P, prm: Params, n_iter: int):
     eps = prm.eps_mod if prm.eps_mod > 0 else default_eps(I)
     g = gaussian_kernel(prm.kernel_size, prm.sigma1, prm.sigma2)
     errors = []
+    if prm.engine == "dm":
+        # exit-wave state of pc-DM, started at the overlap estimate
+        psi = np.stack([P * O[y:y + prm.M, x:x + prm.M][None] for (y, x) in positions])
+        for i in range(n_iter):
+            t = prm.start_iteration + i
+            O, P, E = iteration_dm(I, positions, O, P, psi, prm, t, eps, g)
+            errors.append(E)
+        return O, P, np.array(errors)
+    if prm.engine != "pie":
+        raise ValueError(f"unknown engine {prm.engine!r}")
     parts = batches(len(positions), prm)
     for i in range(n_iter):
         t = prm.start_iteration + i

@@ -389,6 +389,66 @@ def test_minibatch_of_all_positions_is_the_simultaneous_step_and_keeps_the_fixed
     assert np.max(np.abs(O1 - O)) < 1e-12 and np.max(np.abs(P1 - P)) < 1e-12 and max(E) < 1e-12
 
 
+# ------------------------------------------------------------------------ pc-DM engine
+
+def test_dm_fixed_point_and_single_position_projection():
+    rng = _rng(31)
+    M, side = 16, 28
+    O = (0.5 + rng.random((side, side))) * np.exp(1j * rng.random((side, side)))
+    P = _crandn(rng, 2, M, M)
+    pos = np.array([(0, 0), (0, 12), (12, 0), (12, 12), (6, 6)])
+    prm = pe.Params(M=M, K=2, N=len(pos), obj_h=side, obj_w=side, sigma1=1.0, sigma2=0.6, eps_mod=1e-300,
+                    engine="dm")
+    Ic = _consistent_data(O, P, pos, prm)
+    O1, P1, E = pe.iterate(Ic, pos, O, P, prm, 3)
+    assert np.max(np.abs(O1 - O)) < 1e-12 and np.max(np.abs(P1 - P)) < 1e-12 and max(E) < 1e-12
+    # one position, one mode, no blur, no floor: the first DM step is the projection (P o_new = psi')
+    O = (0.5 + rng.random((M, M))) * np.exp(1j * rng.random((M, M)))
+    P = _crandn(rng, 1, M, M)
+    I = rng.random((1, M, M)) * 10
+    prm = pe.Params(M=M, K=1, N=1, obj_h=M, obj_w=M, sigma1=0, sigma2=0, delta_obj=0.0, delta_probe=0.0,
+                    eps_mod=1e-300, engine="dm", probe_update_start=10 ** 9)
+    O1, _, _ = pe.iterate(I, np.array([[0, 0]]), O, P, prm, 1)
+    Psi = np.fft.fft2(P[0] * O)
+    proj = np.fft.ifft2(np.sqrt(np.fft.ifftshift(I[0])) * np.exp(1j * np.angle(Psi)))
+    assert np.max(np.abs(P[0] * O1 - proj)) < 1e-10 * np.max(np.abs(proj))
+
+
+def test_dm_with_a_fixed_probe_is_textbook_difference_map():
+    """Probe fixed, no floor, sigma = 0, K = 1: the overlap projection is exact in one step, so pc-DM is
+    the difference map: O = sum conj(P) psi_n / sum |P|^2 over the covering boxes, then
+    psi_n <- psi_n + Pi_F(2 P o_n - psi_n) - P o_n, starting from psi_n = P o_n."""
+    rng = _rng(32)
+    M, side = 16, 30
+    O0 = (0.5 + rng.random((side, side))) * np.exp(1j * rng.random((side, side)))
+    P = _crandn(rng, 1, M, M)
+    pos = np.array([(0, 0), (0, 14), (14, 0), (14, 14), (7, 7)])
+    I = rng.random((len(pos), M, M)) * 10
+    prm = pe.Params(M=M, K=1, N=len(pos), obj_h=side, obj_w=side, sigma1=0, sigma2=0, delta_obj=0.0,
+                    eps_mod=1e-300, engine="dm", probe_update_start=10 ** 9)
+    O1, _, _ = pe.iterate(I, pos, O0, P, prm, 3)
+
+    def proj_f(chi, In):
+        X = np.fft.fftshift(np.fft.fft2(chi))
+        return np.fft.ifft2(np.fft.ifftshift(np.sqrt(In) * X / np.abs(X)))
+
+    O = O0.copy()
+    psi = [P[0] * O[y:y + M, x:x + M] for y, x in pos]
+    for _ in range(3):
+        new_psi = []
+        for n, (y, x) in enumerate(pos):
+            ov = P[0] * O[y:y + M, x:x + M]
+            new_psi.append(psi[n] + proj_f(2 * ov - psi[n], I[n]) - ov)
+        psi = new_psi
+        num = np.zeros_like(O)
+        den = np.zeros(O.shape)
+        for n, (y, x) in enumerate(pos):
+            num[y:y + M, x:x + M] += np.conj(P[0]) * psi[n]
+            den[y:y + M, x:x + M] += np.abs(P[0]) ** 2
+        O = np.where(den > 0, num / np.where(den > 0, den, 1), O)
+    assert np.max(np.abs(O1 - O)) < 1e-10 * np.max(np.abs(O))
+
+
 # ------------------------------------------------------------------------ P7 / P8: coherent reduction, modes
 
 def _minimal_coherent_engine(I, pos, O, P, n_iter, delta):
