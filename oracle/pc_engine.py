@@ -263,8 +263,10 @@ def _batch_step(I, positions, idx, O, P, prm: Params, t: int, eps: float, g):
 def iteration_dm(I, positions, O, P, psi, prm: Params, t: int, eps: float, g):
     """One pc-DM iteration (reading 10d; difference map of Thibault et al. with the pc intensity model
     of Fig. 1 box 1 in its modulus projection). psi: exit-wave state, (N, K, M, M), updated in place.
-    Per position: psi_ov = P o_n, chi = 2 psi_ov - psi_n, psi_n <- psi_n + Pi_F(chi) - psi_ov; then the
-    overlap projection as one normalised step with dpsi = psi_n - psi_ov. E_t from Pi_F's input."""
+    Per position: psi_ov = P o_n, chi = 2 psi_ov - psi_n, psi_n <- psi_n + Pi_F(chi) - psi_ov. Then the
+    overlap projection, alternating: the object takes one normalised step with dpsi = psi_n - psi_ov,
+    then the probe one from the new object, sum conj(o'_n) (psi_n - P o'_n) over sum |o'_n|^2.
+    E_t is the estimate's error: the pc model of psi_ov against I_n."""
     M, K = prm.M, prm.K
     NO = np.zeros(O.shape, np.complex128)
     DO = np.zeros(O.shape, np.float64)
@@ -277,18 +279,21 @@ def iteration_dm(I, positions, O, P, psi, prm: Params, t: int, eps: float, g):
         psi_ov = P * o[None]
         chi = 2.0 * psi_ov - psi[n]
         In = I[n].astype(np.float64)
-        Chi_new, Ihat = modulus(propagate_forward(chi, prm), In, g, eps, prm.blur_domain)
+        _, Ihat = modulus(propagate_forward(psi_ov, prm), In, g, eps, prm.blur_domain)
         errnum.append(math.fsum(((Ihat - In) ** 2).ravel()))
         errden.append(math.fsum((In ** 2).ravel()))
+        Chi_new, _ = modulus(propagate_forward(chi, prm), In, g, eps, prm.blur_domain)
         psi[n] = psi[n] + propagate_backward(Chi_new, prm) - psi_ov
         dpsi = psi[n] - psi_ov
         NO[y:y + M, x:x + M] += np.sum(np.conj(P) * dpsi, axis=0)
         DO[y:y + M, x:x + M] += P2
-        NP += np.conj(o)[None] * dpsi
-        DP += np.abs(o) ** 2
     c_obj, c_probe = step_coefficients(prm)
     O_new = O + _normalised_step(prm.beta_obj, NO, DO, *c_obj)
     if t >= prm.probe_update_start:
+        for n, (y, x) in enumerate(positions):
+            o = O_new[y:y + M, x:x + M]
+            NP += np.conj(o)[None] * (psi[n] - P * o[None])
+            DP += np.abs(o) ** 2
         P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, *c_probe) for k in range(K)])
     else:
         P_new = P.copy()

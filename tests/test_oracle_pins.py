@@ -414,6 +414,25 @@ def test_dm_fixed_point_and_single_position_projection():
     assert np.max(np.abs(P[0] * O1 - proj)) < 1e-10 * np.max(np.abs(proj))
 
 
+def test_dm_probe_step_uses_the_new_object_and_error_is_the_estimates():
+    """The probe step follows the object step (alternating projections): with one position, no blur
+    and no floors, after one iteration o_new P_new = the projection (both factors fit psi' exactly);
+    E of the first iteration is the NRMSE of P o_n itself (psi starts at P o_n)."""
+    rng = _rng(33)
+    M = 16
+    O = (0.5 + rng.random((M, M))) * np.exp(1j * rng.random((M, M)))
+    P = _crandn(rng, 1, M, M)
+    I = rng.random((1, M, M)) * 10
+    prm = pe.Params(M=M, K=1, N=1, obj_h=M, obj_w=M, sigma1=0, sigma2=0, delta_obj=0.0, delta_probe=0.0,
+                    eps_mod=1e-300, engine="dm")
+    O1, P1, E = pe.iterate(I, np.array([[0, 0]]), O, P, prm, 1)
+    Psi = np.fft.fft2(P[0] * O)
+    proj = np.fft.ifft2(np.sqrt(np.fft.ifftshift(I[0])) * np.exp(1j * np.angle(Psi)))
+    assert np.max(np.abs(P1[0] * O1 - proj)) < 1e-10 * np.max(np.abs(proj))
+    model = np.abs(np.fft.fftshift(Psi)) ** 2
+    assert abs(E[0] - np.sqrt(np.sum((model - I[0]) ** 2) / np.sum(I[0] ** 2))) < 1e-12
+
+
 def test_dm_with_a_fixed_probe_is_textbook_difference_map():
     """Probe fixed, no floor, sigma = 0, K = 1: the overlap projection is exact in one step, so pc-DM is
     the difference map: O = sum conj(P) psi_n / sum |P|^2 over the covering boxes, then
