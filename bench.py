@@ -210,7 +210,7 @@ def kernel_source_hash():
     """Hash of what the fused kernel is compiled from: fft.cuh, pc_fused.cu and its argument struct."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_06640_gb300", "csrc")
-    for f in ("fft.cuh", "pc_fused.cu"):
+    for f in ("fft.cuh", "pc_fused_kernel.cuh", "pc_fused.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     hdr = open(os.path.join(csrc, "engine.h")).read()
     i = hdr.find("struct FusedArgs")

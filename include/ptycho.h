@@ -65,6 +65,7 @@ typedef enum {
 enum { PTYCHO_FARFIELD = 0, PTYCHO_NEARFIELD = 1 };
 enum { PTYCHO_BLUR_AMPLITUDE = 0 /* Eq. 6 */, PTYCHO_BLUR_INTENSITY = 1 /* Eq. 2 */ };
 enum { PTYCHO_STEP_NORMALISED = 0, PTYCHO_STEP_RPIE = 1 };
+enum { PTYCHO_ENGINE_PIE = 0, PTYCHO_ENGINE_DM = 1 };
 
 typedef struct {
   int32_t M;            /* probe = box = detector side, power of two, 8..256 */
@@ -104,6 +105,14 @@ typedef struct {
    * state its batch saw. M <= 128 only; not available in batch plans or ptycho_iterate_static. */
   int32_t minibatch;
   uint64_t order_seed;
+  /* Engine: PTYCHO_ENGINE_PIE (0, default) takes the steps above from dpsi = Pi_F(P o_n) - P o_n;
+   * PTYCHO_ENGINE_DM (1) is pc-DM (Sec. 4.5, the difference map with the pc intensity model): the
+   * plan keeps an exit wave psi_{n,k} per position and mode (N K M^2 complex, started at P_k o_n
+   * when the plan first iterates), each position forms chi = 2 P_k o_n - psi_{n,k}, runs it through
+   * the propagation and the pc modulus step, sets psi_{n,k} <- psi_{n,k} + Pi_F(chi) - P_k o_n,
+   * and O and P take the step of the chosen rule with dpsi = psi_{n,k} - P_k o_n (the overlap
+   * projection); E_t is evaluated on chi. M <= 128, without mini-batches, single plans only. */
+  int32_t engine;
 } ptycho_params;
 
 /* Build a plan on the current CUDA device.

@@ -6,6 +6,8 @@ ABI of include/ptycho.h; `binding` marshals arguments with ctypes and
 """
 from .binding import (  # noqa: F401
     BLUR_AMPLITUDE,
+    ENGINE_DM,
+    ENGINE_PIE,
     BLUR_INTENSITY,
     EXPORTED,
     FARFIELD,

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "PTYCHO_OK", 1: "PTYCHO_EINVAL", 2: "PTYCHO_ENOMEM", 3: "PTYC
 FARFIELD, NEARFIELD = 0, 1
 BLUR_AMPLITUDE, BLUR_INTENSITY = 0, 1
 STEP_NORMALISED, STEP_RPIE = 0, 1
+ENGINE_PIE, ENGINE_DM = 0, 1
 
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
@@ -51,7 +52,7 @@ class PtychoParams(ctypes.Structure):
         ("n_windows", ctypes.c_int32), ("windows", ctypes.POINTER(ctypes.c_int32)),
         ("start_iteration", ctypes.c_int32),
         ("step_rule", ctypes.c_int32), ("rpie_alpha_obj", ctypes.c_double), ("rpie_alpha_probe", ctypes.c_double),
-        ("minibatch", ctypes.c_int32), ("order_seed", ctypes.c_uint64),
+        ("minibatch", ctypes.c_int32), ("order_seed", ctypes.c_uint64), ("engine", ctypes.c_int32),
     ]
 
 
@@ -193,6 +194,10 @@ def make_params(d: dict) -> tuple:
     p.rpie_alpha_probe = float(d.get("rpie_alpha_probe", 0.0))
     p.minibatch = int(d.get("minibatch", 0))
     p.order_seed = int(d.get("order_seed", 0)) & ((1 << 64) - 1)
+    eng = d.get("engine", ENGINE_PIE)
+    if isinstance(eng, str):
+        eng = {"pie": ENGINE_PIE, "dm": ENGINE_DM}[eng]
+    p.engine = int(eng)
     return p, arr
 
 

@@ -133,6 +133,9 @@ struct ptycho_plan_s {
   int mb = 0, nb = 1, tiles = 0;
   int* d_starts = nullptr;
   double* d_err_acc = nullptr;
+  // pc-DM: exit-wave state, and whether the next iteration starts it at P o_n
+  float2* d_psi = nullptr;
+  bool dm_fresh = true;
   // batch plans: one work-queue launch per shape class (M, K, geometry, kernel width class)
   struct QueueClass {
     int M = 0, K = 0, near = 0, kh = 0;
@@ -183,7 +186,7 @@ static ptycho_status validate(const ptycho_params* p) {
   if (!is_pow2(p->M) || p->M < 8 || p->M > 512) return fail(PTYCHO_EINVAL, "M must be a power of two in [8, 512]");
   if (p->M > 256) return fail(PTYCHO_EUNSUPPORTED, "M > 256 is not handled by this build");
   if (p->K < 1) return fail(PTYCHO_EINVAL, "K must be >= 1");
-  if (p->K > 8) return fail(PTYCHO_EUNSUPPORTED, "K > 8 probe modes is not handled by this build");
+  if (p->K > kMaxModes) return fail(PTYCHO_EUNSUPPORTED, "K > 8 probe modes is not handled by this build");
   if (p->N < 1) return fail(PTYCHO_EINVAL, "N must be >= 1");
   if (p->obj_h < p->M || p->obj_w < p->M) return fail(PTYCHO_EINVAL, "object must be at least M x M");
   if (p->geometry != PTYCHO_FARFIELD && p->geometry != PTYCHO_NEARFIELD) return fail(PTYCHO_EINVAL, "bad geometry");
@@ -209,6 +212,10 @@ static ptycho_status validate(const ptycho_params* p) {
       return fail(PTYCHO_EINVAL, "windows must be [first, last] with 1 <= first <= last");
   if (p->start_iteration < 1) return fail(PTYCHO_EINVAL, "start_iteration must be >= 1");
   if (p->minibatch < 0) return fail(PTYCHO_EINVAL, "minibatch must be >= 0");
+  if (p->engine != PTYCHO_ENGINE_PIE && p->engine != PTYCHO_ENGINE_DM)
+    return fail(PTYCHO_EINVAL, "engine must be PTYCHO_ENGINE_PIE or PTYCHO_ENGINE_DM");
+  if (p->engine == PTYCHO_ENGINE_DM && (p->M > 128 || (p->minibatch > 0 && p->minibatch < p->N)))
+    return fail(PTYCHO_EUNSUPPORTED, "pc-DM handles M <= 128 without mini-batches");
   if (p->minibatch > 0 && p->minibatch < p->N && p->M > 128)
     return fail(PTYCHO_EUNSUPPORTED, "the mini-batch engine handles M <= 128");
   if (p->step_rule != PTYCHO_STEP_NORMALISED && p->step_rule != PTYCHO_STEP_RPIE)
@@ -443,6 +450,10 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   if (!flat.empty())
     PT_CUDA(cudaMemcpy(d_list, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice), "copy tiles");
   pl->d_starts = d_start;
+  if (p.engine == PTYCHO_ENGINE_DM) {
+    PT_CUDA(pl->alloc(&pl->d_psi, (size_t)N * K * MM), "alloc exit-wave state");
+    pl->ua.dm_psi = pl->d_psi;
+  }
   PT_CUDA(pl->alloc(&pl->d_err_acc, 1), "alloc error accumulator");
   PT_CUDA(cudaMemset(pl->d_err_acc, 0, sizeof(double)), "clear error accumulator");
 
@@ -671,6 +682,11 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
     }
     if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
     return PTYCHO_OK;
+  } else if (pl->d_psi) {
+    fa.psi = pl->d_psi;
+    fa.dm_init = pl->dm_fresh ? 1 : 0;
+    PT_CUDA(launch_fused_dm(pl->p.M, fa, pl->slots, s), "pc-DM kernel launch");
+    pl->dm_fresh = false;
   } else {
     PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, s), "fused kernel launch");
   }
@@ -827,6 +843,8 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       st = fail(PTYCHO_EINVAL, "intensities and positions must be non-NULL");
     if (st == PTYCHO_OK && params[b]->minibatch > 0 && params[b]->minibatch < params[b]->N)
       st = fail(PTYCHO_EUNSUPPORTED, "mini-batch problems run through ptycho_plan");
+    if (st == PTYCHO_OK && params[b]->engine == PTYCHO_ENGINE_DM)
+      st = fail(PTYCHO_EUNSUPPORTED, "pc-DM problems run through ptycho_plan");
     if (st != PTYCHO_OK) return fail(st, "problem " + std::to_string(b) + ": " + g_last_error);
   }
   ptycho_plan_s* pl = new (std::nothrow) ptycho_plan_s();

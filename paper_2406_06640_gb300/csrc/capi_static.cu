@@ -89,8 +89,8 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   if (st != PTYCHO_OK) return st;
   if (!intensities || !positions || !object || !probe) return capi_fail(PTYCHO_EINVAL, "NULL argument");
   if (n_iter < 0 || n_iter > kErrHistory) return capi_fail(PTYCHO_EINVAL, "n_iter must lie in [0, 4096]");
-  if (p->minibatch > 0 && p->minibatch < p->N)
-    return capi_fail(PTYCHO_EUNSUPPORTED, "the mini-batch engine runs through ptycho_plan");
+  if ((p->minibatch > 0 && p->minibatch < p->N) || p->engine == PTYCHO_ENGINE_DM)
+    return capi_fail(PTYCHO_EUNSUPPORTED, "the mini-batch and pc-DM engines run through ptycho_plan");
   if (!capi_is_device_pointer(intensities)) return capi_fail(PTYCHO_EINVAL, "intensities must be a device pointer");
   if (p->M > 128) return capi_fail(PTYCHO_EUNSUPPORTED, "the static entry point handles M <= 128");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

@@ -10,6 +10,7 @@ namespace ptycho {
 
 constexpr int kMaxTaps = 31;        // largest odd Gaussian kernel side accepted (Eq. 7 support)
 constexpr int kObjTile = 32;        // object tile side of the gather kernels
+constexpr int kMaxModes = 8;        // probe modes K handled (one cluster rank per mode)
 constexpr int kObjSplit = 8;        // position groups per object tile (partial sums, fixed order)
 constexpr int kErrHistory = 4096;   // ring of per-iteration errors kept on the device
 
@@ -40,6 +41,9 @@ struct FusedArgs {
   const int4* chunks;
   int nchunks;
   int* queue;  // device counter, zero before the launch
+  // pc-DM launches: exit-wave state N x K x M x M (updated in place); dm_init: start it at P o_n
+  float2* psi;
+  int dm_init;
 };
 
 // fused kernel launch; returns the number of slots (co-resident clusters) used
@@ -49,6 +53,9 @@ cudaError_t fused_max_slots(int M, int K, int* slots);
 // a.K, a.near_field, a.kh (kernel width class) and a.tw are those of every problem in a.probs
 cudaError_t launch_fused_queue(int M, const FusedArgs& a, int slots, cudaStream_t s);
 cudaError_t fused_queue_max_slots(int M, int K, int* slots);
+// pc-DM launch (single problem, M <= 128): as launch_fused with the exit-wave state a.psi
+cudaError_t launch_fused_dm(int M, const FusedArgs& a, int slots, cudaStream_t s);
+cudaError_t fused_dm_timed_out(bool* out);
 bool fused_queue_supported(int M);
 size_t fused_smem_bytes(int M);
 // true if a bounded device wait of the fused kernel gave up since the last call (clears the flag; synchronous)
@@ -125,6 +132,9 @@ struct UpdateArgs {
   // step = beta num / (c_d d + c_max max d): normalised rule (1, delta), rPIE rule (1 - a, a)
   float beta_obj, beta_probe, cd_obj, cmax_obj, cd_probe, cmax_probe;
   int update_probe;
+  // pc-DM: exit-wave state (N x K x M x M). When set, the probe step follows the object step and is
+  // taken from the new object and this state (alternating overlap projection)
+  const float2* dm_psi;
 };
 cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);
 

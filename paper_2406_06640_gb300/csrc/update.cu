@@ -123,6 +123,38 @@ __global__ void k_probe_gather(const UpdateArgs u) {
   if (threadIdx.x == 0) u.blk_max_p[blockIdx.x] = smax[0];
 }
 
+// ------------------------------------------------------------------ pc-DM probe partials
+// After the object step: slot s sums, over positions n = s, s + slots, ..., conj(o'_n)(psi_n,k - P_k o'_n)
+// into pacc[s][k] and |o'_n|^2 into dacc[s] (o'_n: the new object under position n). grid
+// (ceil(M^2 / 256), slots); one thread per probe pixel and every mode, so o'_n is read once
+__global__ void k_dm_probe_partials(const UpdateArgs u) {
+  const int MM = u.M * u.M;
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p >= MM) return;
+  const int s = blockIdx.y;
+  const int row = p / u.M, col = p % u.M;
+  float2 pk[kMaxModes], acc[kMaxModes];
+#pragma unroll
+  for (int k = 0; k < kMaxModes; ++k) {
+    pk[k] = k < u.K ? u.P[(size_t)k * MM + p] : make_float2(0.f, 0.f);
+    acc[k] = make_float2(0.f, 0.f);
+  }
+  float d = 0.f;
+  for (int n = s; n < u.N; n += u.slots) {
+    const int2 r = u.pos[n];
+    const float2 o = u.O[(size_t)(r.x + row) * u.obj_w + r.y + col];
+    d += cabs2(o);
+    const float2* ps = u.dm_psi + (size_t)n * u.K * MM + p;
+#pragma unroll
+    for (int k = 0; k < kMaxModes; ++k)
+      if (k < u.K) acc[k] = cadd(acc[k], cconjmul(o, csub(ps[(size_t)k * MM], cmul(pk[k], o))));
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxModes; ++k)
+    if (k < u.K) const_cast<float2*>(u.pacc)[((size_t)s * u.K + k) * MM + p] = acc[k];
+  const_cast<float*>(u.dacc)[(size_t)s * MM + p] = d;
+}
+
 // ------------------------------------------------------------------ object: per-tile gather of the contributions
 // grid (tiles_x, tiles_y, kObjSplit), block 32 x 8; thread (tx, ty) owns pixels (Y0 + ty + 8 i, X0 + tx)
 __global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
@@ -276,11 +308,22 @@ __global__ void k_probe_apply(const UpdateArgs u) {
 cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s) {
   const int MM = u.M * u.M;
   const int pb = (MM + 255) / 256;
-  k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+  if (u.dm_psi) {
+    // the |P|^2 map for the object step only (no partials: the probe sums follow the object step)
+    UpdateArgs u0 = u;
+    u0.slots = 0;
+    k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u0);
+  } else {
+    k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+  }
   const dim3 tb(32, 8);
   k_obj_gather<<<dim3(u.tiles_x, u.tiles_y, kObjSplit), tb, 0, s>>>(u);
   k_obj_finalize<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
   k_obj_apply<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
+  if (u.dm_psi && u.update_probe) {
+    k_dm_probe_partials<<<dim3(pb, u.slots), 256, 0, s>>>(u);
+    k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+  }
   k_probe_apply<<<dim3(pb, u.K), 256, 0, s>>>(u);
   return cudaGetLastError();
 }

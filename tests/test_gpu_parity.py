@@ -120,6 +120,44 @@ def test_minibatch_engine_near_field_modes_window():
                   step_rule="rpie", rpie_alpha_obj=0.3, rpie_alpha_probe=0.3), 3)
 
 
+def test_pc_dm_engine():
+    """pc-DM (exit-wave state per position and mode, chi = 2 P o - psi through the pc modulus step,
+    overlap projection alternating: the object step, then the probe step from the new object; E of
+    the estimate P o): configuration 0, 10 iterations."""
+    p = make_problem(0)
+    check(p, dict(p.params, engine="dm"), 10)
+
+
+@pytest.mark.parametrize("M,K,start", [(16, 1, 0), (128, 4, 2)])
+def test_pc_dm_engine_probe_sizes(M, K, start):
+    """The smallest and largest probe of the pc-DM kernel; a delayed probe step."""
+    p = make_problem(0, scan_side=3, obj_side=M + 40, M=M, K=K, sigma=1.0)
+    check(p, dict(p.params, engine="dm", probe_update_start=start), 4)
+
+
+def test_pc_dm_engine_near_field_modes_window_and_resume():
+    """Near field, two modes, intensity blur, a constraint window; the state carries across calls
+    (3 + 2 iterations equal 5 bitwise)."""
+    from paper_2406_06640_gb300.engine import Reconstruction
+
+    p = make_problem(0, scan_side=4, obj_side=128, M=64, K=2, geometry="near", sigma=2.0)
+    prm = dict(p.params, sigma1=2.0, sigma2=2.0, blur_domain="intensity", engine="dm", windows=[(2, 3)])
+    check(p, prm, 5)
+    dev = _dev()
+    outs = []
+    for chunks in ([5], [3, 2]):
+        I = torch.from_numpy(p.I).to(dev)
+        O = torch.from_numpy(p.O0.astype(np.complex64)).to(dev)
+        P = torch.from_numpy(p.P0.astype(np.complex64)).to(dev)
+        rec = Reconstruction(prm, I, p.positions)
+        for c in chunks:
+            rec.iterate(O, P, c)
+        outs.append((O.cpu().numpy(), P.cpu().numpy(), rec.errors(5)))
+        rec.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
 def test_near_field_two_modes():
     p = make_problem(0, scan_side=4, obj_side=128, M=64, K=2, geometry="near", sigma=2.0)
     check(p, dict(p.params, sigma1=2.0, sigma2=2.0), 5)
