@@ -266,6 +266,9 @@ def iteration_dm(I, positions, O, P, psi, prm: Params, t: int, eps: float, g):
     Per position: psi_ov = P o_n, chi = 2 psi_ov - psi_n, psi_n <- psi_n + Pi_F(chi) - psi_ov. Then the
     overlap projection, alternating: the object takes one normalised step with dpsi = psi_n - psi_ov,
     then the probe one from the new object, sum conj(o'_n) (psi_n - P o'_n) over sum |o'_n|^2.
+    Inside a complex-constraint window the constraint (Eqs. 9-11) acts on the object between the
+    two steps, and every state moves with its box, psi_n += P (o_n constrained - o_n), so that the
+    difference psi_n - P o_n the map carries is the constraint's to keep.
     E_t is the estimate's error: the pc model of psi_ov against I_n."""
     M, K = prm.M, prm.K
     NO = np.zeros(O.shape, np.complex128)
@@ -289,6 +292,11 @@ def iteration_dm(I, positions, O, P, psi, prm: Params, t: int, eps: float, g):
         DO[y:y + M, x:x + M] += P2
     c_obj, c_probe = step_coefficients(prm)
     O_new = O + _normalised_step(prm.beta_obj, NO, DO, *c_obj)
+    if in_window(t, prm.windows):
+        O_con = complex_constraint(O_new, positions, prm)
+        for n, (y, x) in enumerate(positions):
+            psi[n] += P * (O_con[y:y + M, x:x + M] - O_new[y:y + M, x:x + M])[None]
+        O_new = O_con
     if t >= prm.probe_update_start:
         for n, (y, x) in enumerate(positions):
             o = O_new[y:y + M, x:x + M]
@@ -297,8 +305,6 @@ def iteration_dm(I, positions, O, P, psi, prm: Params, t: int, eps: float, g):
         P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, *c_probe) for k in range(K)])
     else:
         P_new = P.copy()
-    if in_window(t, prm.windows):
-        O_new = complex_constraint(O_new, positions, prm)
     return O_new, P_new, math.sqrt(math.fsum(errnum) / math.fsum(errden))
 
 

@@ -646,3 +646,44 @@ def test_probe_update_starts_at_the_given_iteration():
 def test_windows_are_one_based_inclusive():
     assert pe.in_window(5, [(5, 35)]) and pe.in_window(35, [(5, 35)])
     assert not pe.in_window(4, [(5, 35)]) and not pe.in_window(36, [(5, 35)])
+
+
+def test_dm_constraint_sits_between_the_steps_and_keeps_the_difference():
+    """Inside a window the complex constraint acts on the object after the object step and before
+    the probe step, and each state moves with its box: with the probe step off, O equals the
+    constraint of the no-window result and psi_n - P o_n is the same with and without the window;
+    with the probe step on, the probe step sees the constrained object."""
+    rng = _rng(34)
+    M, side = 16, 30
+    O = (0.5 + rng.random((side, side))) * np.exp(1j * (rng.random((side, side)) - 0.5))
+    P = _crandn(rng, 2, M, M)
+    pos = np.array([(0, 0), (0, 14), (14, 0), (14, 14), (7, 7)])
+    I = rng.random((len(pos), M, M)) * 10
+    base = dict(M=M, K=2, N=len(pos), obj_h=side, obj_w=side, sigma1=0.8, sigma2=0.8, engine="dm",
+                alpha1=1.0, alpha2=0.3)
+    eps = pe.default_eps(I)
+    for start, in ((10 ** 9,), (1,)):
+        prm_w = pe.Params(**base, windows=[(1, 1)], probe_update_start=start)
+        prm_n = pe.Params(**base, probe_update_start=start)
+        g = pe.gaussian_kernel(prm_w.kernel_size, prm_w.sigma1, prm_w.sigma2)
+        psi0 = np.stack([P * O[y:y + M, x:x + M][None] for y, x in pos])
+        psi_w, psi_n = psi0.copy(), psi0.copy()
+        Ow, Pw, Ew = pe.iteration_dm(I, pos, O, P, psi_w, prm_w, 1, eps, g)
+        On, Pn, En = pe.iteration_dm(I, pos, O, P, psi_n, prm_n, 1, eps, g)
+        assert Ew == En
+        assert np.max(np.abs(Ow - On)) > 1e-3  # the constraint does something here
+        if start > 1:
+            assert np.array_equal(Ow, pe.complex_constraint(On, pos, prm_w)) and np.array_equal(Pw, P)
+            for n, (y, x) in enumerate(pos):
+                dw = psi_w[n] - P * Ow[y:y + M, x:x + M][None]
+                dn = psi_n[n] - P * On[y:y + M, x:x + M][None]
+                assert np.max(np.abs(dw - dn)) < 1e-10 * np.max(np.abs(dn))
+        else:
+            Oc = pe.complex_constraint(On, pos, prm_w)
+            assert np.max(np.abs(Ow - Oc)) < 1e-13
+            NP = sum(np.conj(Oc[y:y + M, x:x + M])[None] * (psi_n[n] - P * On[y:y + M, x:x + M][None])
+                     for n, (y, x) in enumerate(pos))
+            DP = sum(np.abs(Oc[y:y + M, x:x + M]) ** 2 for y, x in pos)
+            c = pe.step_coefficients(prm_w)[1]
+            ref = P + np.stack([pe._normalised_step(prm_w.beta_probe, NP[k], DP, *c) for k in range(2)])
+            assert np.max(np.abs(Pw - ref)) < 1e-12 * np.max(np.abs(ref))
