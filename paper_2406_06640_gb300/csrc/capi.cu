@@ -135,6 +135,7 @@ struct ptycho_plan_s {
   double* d_err_acc = nullptr;
   // pc-DM: exit-wave state, and whether the next iteration starts it at P o_n
   float2* d_psi = nullptr;
+  float2* d_obj_prev = nullptr;  // the object before the complex constraint (pc-DM windows)
   bool dm_fresh = true;
   // batch plans: one work-queue launch per shape class (M, K, geometry, kernel width class)
   struct QueueClass {
@@ -452,6 +453,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   pl->d_starts = d_start;
   if (p.engine == PTYCHO_ENGINE_DM) {
     PT_CUDA(pl->alloc(&pl->d_psi, (size_t)N * K * MM), "alloc exit-wave state");
+    PT_CUDA(pl->alloc(&pl->d_obj_prev, (size_t)p.obj_h * p.obj_w), "alloc object copy");
     pl->ua.dm_psi = pl->d_psi;
   }
   PT_CUDA(pl->alloc(&pl->d_err_acc, 1), "alloc error accumulator");
@@ -695,6 +697,21 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
     pl->prof_count++;
   }
   ua.update_probe = t >= pl->p.probe_update_start;
+  if (pl->d_psi) {
+    // pc-DM: the complex constraint acts between the object and the probe step, and the states
+    // move with their boxes by P (O constrained - O)
+    PT_CUDA(launch_update_object(ua, s), "update launch");
+    ua.dm_obj_prev = nullptr;
+    if (pl->in_window(t)) {
+      PT_CUDA(cudaMemcpyAsync(pl->d_obj_prev, ua.O, (size_t)pl->p.obj_h * pl->p.obj_w * sizeof(float2),
+                              cudaMemcpyDeviceToDevice, s),
+              "object copy");
+      PT_CUDA(launch_constraint(ca, s), "constraint launch");
+      ua.dm_obj_prev = pl->d_obj_prev;
+    }
+    PT_CUDA(launch_update_probe(ua, s), "update launch");
+    return PTYCHO_OK;
+  }
   PT_CUDA(launch_update(ua, s), "update launch");
   if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
   return PTYCHO_OK;
@@ -709,6 +726,21 @@ static ptycho_status enqueue_update(ptycho_plan_s* pl, void* object, void* probe
   ua.P = static_cast<float2*>(probe);
   ca.O = static_cast<float2*>(object);
   ua.update_probe = t >= pl->p.probe_update_start;
+  if (pl->d_psi) {
+    // pc-DM: the complex constraint acts between the object and the probe step, and the states
+    // move with their boxes by P (O constrained - O)
+    PT_CUDA(launch_update_object(ua, s), "update launch");
+    ua.dm_obj_prev = nullptr;
+    if (pl->in_window(t)) {
+      PT_CUDA(cudaMemcpyAsync(pl->d_obj_prev, ua.O, (size_t)pl->p.obj_h * pl->p.obj_w * sizeof(float2),
+                              cudaMemcpyDeviceToDevice, s),
+              "object copy");
+      PT_CUDA(launch_constraint(ca, s), "constraint launch");
+      ua.dm_obj_prev = pl->d_obj_prev;
+    }
+    PT_CUDA(launch_update_probe(ua, s), "update launch");
+    return PTYCHO_OK;
+  }
   PT_CUDA(launch_update(ua, s), "update launch");
   if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
   return PTYCHO_OK;
@@ -1166,6 +1198,7 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
     fft = chunks * (pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5);
   }
   if (pl->mb > 0) fft = pl->nb * 6 - 5;  // per batch: the fused kernel and the 5 update kernels
+  if (pl->d_psi) fft += 2;                // pc-DM probe partials and their gather (probe step on)
   return fft + 5 + (in_window ? 6 : 0);
 }
 

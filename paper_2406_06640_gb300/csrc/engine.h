@@ -134,9 +134,16 @@ struct UpdateArgs {
   int update_probe;
   // pc-DM: exit-wave state (N x K x M x M). When set, the probe step follows the object step and is
   // taken from the new object and this state (alternating overlap projection)
-  const float2* dm_psi;
+  float2* dm_psi;
+  // pc-DM inside a complex-constraint window: the object before the constraint (the states move by
+  // P (O - dm_obj_prev) under their boxes); null otherwise
+  const float2* dm_obj_prev;
 };
+// launch_update = launch_update_object then launch_update_probe (pc-DM runs the complex constraint
+// between the two)
 cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);
+cudaError_t launch_update_object(const UpdateArgs& u, cudaStream_t s);
+cudaError_t launch_update_probe(const UpdateArgs& u, cudaStream_t s);
 
 // complex constraint (constraint.cu)
 struct ConstraintArgs {

@@ -125,8 +125,10 @@ __global__ void k_probe_gather(const UpdateArgs u) {
 
 // ------------------------------------------------------------------ pc-DM probe partials
 // After the object step: slot s sums, over positions n = s, s + slots, ..., conj(o'_n)(psi_n,k - P_k o'_n)
-// into pacc[s][k] and |o'_n|^2 into dacc[s] (o'_n: the new object under position n). grid
-// (ceil(M^2 / 256), slots); one thread per probe pixel and every mode, so o'_n is read once
+// into pacc[s][k] and |o'_n|^2 into dacc[s] (o'_n: the new object under position n). Inside a
+// complex-constraint window the states first move with their boxes, psi_n,k += P_k (o'_n - o''_n),
+// o''_n the object before the constraint. grid (ceil(M^2 / 256), slots); one thread per probe pixel
+// and every mode, so o'_n is read once
 __global__ void k_dm_probe_partials(const UpdateArgs u) {
   const int MM = u.M * u.M;
   const int p = blockIdx.x * 256 + threadIdx.x;
@@ -142,12 +144,24 @@ __global__ void k_dm_probe_partials(const UpdateArgs u) {
   float d = 0.f;
   for (int n = s; n < u.N; n += u.slots) {
     const int2 r = u.pos[n];
-    const float2 o = u.O[(size_t)(r.x + row) * u.obj_w + r.y + col];
+    const size_t q = (size_t)(r.x + row) * u.obj_w + r.y + col;
+    const float2 o = u.O[q];
     d += cabs2(o);
-    const float2* ps = u.dm_psi + (size_t)n * u.K * MM + p;
+    float2* ps = u.dm_psi + (size_t)n * u.K * MM + p;
+    if (u.dm_obj_prev) {
+      const float2 dlt = csub(o, u.dm_obj_prev[q]);
 #pragma unroll
-    for (int k = 0; k < kMaxModes; ++k)
-      if (k < u.K) acc[k] = cadd(acc[k], cconjmul(o, csub(ps[(size_t)k * MM], cmul(pk[k], o))));
+      for (int k = 0; k < kMaxModes; ++k)
+        if (k < u.K) {
+          const float2 st = cadd(ps[(size_t)k * MM], cmul(pk[k], dlt));
+          ps[(size_t)k * MM] = st;
+          acc[k] = cadd(acc[k], cconjmul(o, csub(st, cmul(pk[k], o))));
+        }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMaxModes; ++k)
+        if (k < u.K) acc[k] = cadd(acc[k], cconjmul(o, csub(ps[(size_t)k * MM], cmul(pk[k], o))));
+    }
   }
 #pragma unroll
   for (int k = 0; k < kMaxModes; ++k)
@@ -305,7 +319,7 @@ __global__ void k_probe_apply(const UpdateArgs u) {
   }
 }
 
-cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s) {
+cudaError_t launch_update_object(const UpdateArgs& u, cudaStream_t s) {
   const int MM = u.M * u.M;
   const int pb = (MM + 255) / 256;
   if (u.dm_psi) {
@@ -320,12 +334,23 @@ cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s) {
   k_obj_gather<<<dim3(u.tiles_x, u.tiles_y, kObjSplit), tb, 0, s>>>(u);
   k_obj_finalize<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
   k_obj_apply<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
-  if (u.dm_psi && u.update_probe) {
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_probe(const UpdateArgs& u, cudaStream_t s) {
+  const int MM = u.M * u.M;
+  const int pb = (MM + 255) / 256;
+  if (u.dm_psi && (u.update_probe || u.dm_obj_prev)) {
     k_dm_probe_partials<<<dim3(pb, u.slots), 256, 0, s>>>(u);
-    k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+    if (u.update_probe) k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
   }
   k_probe_apply<<<dim3(pb, u.K), 256, 0, s>>>(u);
   return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s) {
+  cudaError_t e = launch_update_object(u, s);
+  return e != cudaSuccess ? e : launch_update_probe(u, s);
 }
 
 }  // namespace ptycho

@@ -128,6 +128,13 @@ def test_pc_dm_engine():
     check(p, dict(p.params, engine="dm"), 10)
 
 
+def test_pc_dm_engine_constraint_window():
+    """pc-DM with a complex-constraint window that opens before the probe step starts: the
+    constraint acts between the object and the probe step and the states move with their boxes."""
+    p = make_problem(0)
+    check(p, dict(p.params, engine="dm", windows=[(2, 6)], alpha1=1.0, alpha2=0.2, probe_update_start=3), 8)
+
+
 @pytest.mark.parametrize("M,K,start", [(16, 1, 0), (128, 4, 2)])
 def test_pc_dm_engine_probe_sizes(M, K, start):
     """The smallest and largest probe of the pc-DM kernel; a delayed probe step."""
