@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="far128x4",
-                    help="far128x4: the benchmark workload; near256x8 and far64x1 for reference runs")
+                    help="far128x4: the benchmark workload; the others for reference runs")
     return ap.parse_args()
 
 
@@ -61,6 +61,14 @@ WORKLOADS = {
                      "object 1024^2, sigma 2, 1e5 photons)"),
     "far64x1": (0, "far-field single-mode pc-engine iteration (probe 64^2, N=100 raster, object 192^2, "
                    "sigma 1, 1e5 photons)"),
+    "far128x4-rpie": (1, "far128x4 with the rPIE step rule (alpha 0.2 object, 0.5 probe)",
+                      dict(step_rule="rpie", rpie_alpha_obj=0.2, rpie_alpha_probe=0.5)),
+    "far128x4-mb32": (1, "far128x4 as the mini-batch (sequential) engine: batches of 32 positions in a Philox "
+                         "order, one fused launch and one update per batch (29 per iteration), rPIE steps",
+                      dict(minibatch=32, order_seed=11, step_rule="rpie", rpie_alpha_obj=0.2,
+                           rpie_alpha_probe=0.5)),
+    "far128x4-dm": (1, "far128x4 with the pc-DM engine (exit-wave state per position and mode in HBM)",
+                    dict(engine="dm")),
     "batch64": (3, "64 independent reconstructions of uneven sizes (probe 64-256, 100-1600 positions, K 1-4, "
                    "far/near 50/50, sigma 0.5-3), one CUDA graph launch per iteration"),
     "warmstart": (4, "time to intensity NRMSE <= 0.05 against the noise-free patterns: flat start with the true "
@@ -78,6 +86,8 @@ def workload():
 
     prob = make_problem(WORKLOADS[_WORKLOAD][0])
     params = dict(prob.params, windows=[(1, 1 << 30)])  # complex constraint in every step
+    if len(WORKLOADS[_WORKLOAD]) > 2:
+        params.update(WORKLOADS[_WORKLOAD][2])
     return prob, params
 
 
@@ -92,13 +102,15 @@ def config_of(prob, extra=None):
     return cfg
 
 
-def algorithmic_flops(M, K, N, near):
+def algorithmic_flops(M, K, N, near, dm=False):
     """Nominal FLOPs of one iteration: 5 M^2 log2(M^2) per 2-D FFT (2 per pattern-mode in the far
     field, 4 in the near field), 26 FLOP per pixel per mode and 55 FLOP per pixel per pattern for
-    the elementwise work (exit wave, modulus, blur, ratio, contributions, error)."""
+    the elementwise work (exit wave, modulus, blur, ratio, contributions, error). pc-DM propagates
+    the estimate as well (one more forward propagation per mode, 12 more FLOP per pixel per mode
+    for the reflected wave and the state, one more blur and error pass, 30 FLOP per pixel)."""
     fft = 5.0 * M * M * math.log2(M * M)
-    per_mode = (4 if near else 2) * fft + 26.0 * M * M
-    return N * K * per_mode + N * 55.0 * M * M
+    per_mode = ((6 if near else 3) if dm else (4 if near else 2)) * fft + (38.0 if dm else 26.0) * M * M
+    return N * K * per_mode + N * (85.0 if dm else 55.0) * M * M
 
 
 # ------------------------------------------------------------------ clocks
@@ -216,6 +228,17 @@ def kernel_source_hash():
     i = hdr.find("struct FusedArgs")
     h.update(hdr[i:hdr.find("};", i)].encode() if i >= 0 else b"")
     return h.hexdigest()
+
+
+def kernel_label(prob, params):
+    if prob.M > 128:
+        return "staged passes (M=256)"
+    geo = "near" if params["geometry"] == "near" else "far"
+    if params.get("minibatch", 0):
+        return f"pc_fused_kernel<{prob.M}, {geo}> per batch with its update kernels (events around the batch loop)"
+    if params.get("engine") == "dm":
+        return f"pc_fused_kernel<{prob.M}, {geo}, DM>"
+    return f"pc_fused_kernel<{prob.M}, {geo}>"
 
 
 # ------------------------------------------------------------------ arms
@@ -510,7 +533,7 @@ def run_ours(args):
     value = ws * units_per_step * args.steps / (t_max / 1e3)
 
     # roofline of the dominant (fused) kernel: algorithmic FLOPs per launch / its event-timed duration
-    flops = algorithmic_flops(prob.M, prob.K, prob.N, params["geometry"] == "near")
+    flops = algorithmic_flops(prob.M, prob.K, prob.N, params["geometry"] == "near", params.get("engine") == "dm")
     fused_avg_s = fused_ms / max(fused_launches, 1) / 1e3
     achieved = flops / fused_avg_s / 1e12
     peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -549,10 +572,13 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_of(prob, {"parallelism": f"replicas{ws}" if ws > 1 else "single GPU"}),
+                "config": config_of(prob, {"parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
+                                           "engine": params.get("engine", "pie"),
+                                           "step_rule": params.get("step_rule", "normalised"),
+                                           "minibatch": params.get("minibatch", 0) or prob.N}),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "kernel": "pc_fused_kernel<128, far>" if prob.M <= 128 else "staged passes (M=256)",
+                             "kernel": kernel_label(prob, params),
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FMA pipe, max clock)",
                              "flops_per_launch": flops, "avg_launch_ms": fused_avg_s * 1e3},
                 "cpu_baseline": cpu,

@@ -332,6 +332,28 @@ ptycho_status ptycho_warmstart(ptycho_unet_t net, const float* intensities, cons
  * t = 0) and visiting order (stream 4, iteration t). */
 ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32_t t, int32_t* out);
 
+/* ---- Numerical monochromatisation (Sec. 4.2, Eqs. 12-13) ------------------------------------
+ * A broadband far-field pattern is modelled as b = C m: the monochromatic pattern m at the
+ * reference wavelength lambda_c, magnified about the detector centre c = M / 2 by each relative
+ * wavelength a_j = lambda_j / lambda_c and weighted by weight_j / a_j^2 (the weight's share of the
+ * energy):  (C m)(y, x) = sum_j weight_j / a_j^2 m(c + (y - c) / a_j, c + (x - c) / a_j), with linear
+ * interpolation and zero outside the grid. For every pattern, x_n = k steps of CGLS on
+ * min ||C x - b_n||_2 from x = 0: the least-squares solution over the Krylov subspace
+ * span{C^T b, (C^T C) C^T b, ..., (C^T C)^(k-1) C^T b} (Eq. 13); k is the regularisation.
+ *   M: 8, 16, 32, 64 or 128 (EUNSUPPORTED otherwise); J: 1..64 spectral samples;
+ *   scale: host, J values a_j in (0, 2.5]; weight: host, J finite values >= 0, not all zero;
+ *   N >= 0 patterns; k >= 0 steps;
+ *   b: device float32, N x M x M, row-major, detector-centred (DC at (M/2, M/2));
+ *   x: device float32, N x M x M (x == b is allowed: each pattern is read before it is written);
+ *   resid: device float64, N x (k + 1) residual norms ||b_n - C x_i|| for i = 0..k, or NULL;
+ *   clamp: 1 sets negative values of x to zero (the pc engine takes non-negative patterns).
+ * Enqueued on cuda_stream (NULL: the default stream); returns before the work finishes. The caller
+ * owns every buffer. PTYCHO_EINVAL for invalid sizes, values or NULL buffers, PTYCHO_ECUDA for a
+ * failed launch. Computed in FP32 with FP64 step sizes and norms. */
+ptycho_status ptycho_monochromatise(int32_t M, int32_t J, const double* scale, const double* weight, int32_t N,
+                                    int32_t k, const float* b, float* x, double* resid, int32_t clamp,
+                                    void* cuda_stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ptycho_last_error(void);
 

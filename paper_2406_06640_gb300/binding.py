@@ -26,7 +26,7 @@ EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_histo
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
             "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_permutation", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
             "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
-            "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart")
+            "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart", "ptycho_monochromatise")
 
 
 class PtychoError(RuntimeError):
@@ -116,6 +116,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]
     lib.ptycho_permutation.restype = st
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.ptycho_monochromatise.argtypes = [ctypes.c_int32, ctypes.c_int32, D, D, ctypes.c_int32, ctypes.c_int32,
+                                          P, P, P, ctypes.c_int32, P]
+    lib.ptycho_monochromatise.restype = st
     lib.ptycho_set_staged_chunk.argtypes = [ctypes.c_int32]
     lib.ptycho_set_staged_chunk.restype = st
     lib.ptycho_staged_chunk.argtypes = [P]
@@ -397,6 +401,19 @@ def set_batch_chunk(chunk_len: int):
 def set_staged_chunk(chunk: int):
     """Fix the positions per chunk of the staged M = 256 passes of later plans (4, 8, 16, 32; 0 = autotune)."""
     _check(load().ptycho_set_staged_chunk(chunk))
+
+
+def monochromatise_raw(M: int, scales, weights, N: int, k: int, b_ptr: int, x_ptr: int, resid_ptr: int = 0,
+                       clamp: bool = False, stream: int = 0):
+    """ptycho_monochromatise on device pointers: x = k CGLS steps of min ||C x - b|| per pattern."""
+    J = len(scales)
+    if len(weights) != J:
+        raise ValueError("scales and weights differ in length")
+    sc = (ctypes.c_double * max(J, 1))(*[float(v) for v in scales])
+    wt = (ctypes.c_double * max(J, 1))(*[float(v) for v in weights])
+    _check(load().ptycho_monochromatise(M, J, sc, wt, N, k, ctypes.c_void_p(b_ptr or None),
+                                        ctypes.c_void_p(x_ptr or None), ctypes.c_void_p(resid_ptr or None),
+                                        1 if clamp else 0, ctypes.c_void_p(stream or None)))
 
 
 def permutation(n: int, seed: int, stream: int, t: int) -> list:

@@ -1209,6 +1209,40 @@ ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32
   return PTYCHO_OK;
 }
 
+ptycho_status ptycho_monochromatise(int32_t M, int32_t J, const double* scale, const double* weight, int32_t N,
+                                    int32_t k, const float* b, float* x, double* resid, int32_t clamp,
+                                    void* cuda_stream) {
+  if (M <= 0 || N < 0 || k < 0 || J <= 0) return fail(PTYCHO_EINVAL, "need M > 0, J > 0, N >= 0, k >= 0");
+  if (M != 8 && M != 16 && M != 32 && M != 64 && M != 128)
+    return fail(PTYCHO_EUNSUPPORTED, "monochromatisation handles M = 8, 16, 32, 64, 128");
+  if (J > kMonoMaxJ) return fail(PTYCHO_EUNSUPPORTED, "more than 64 spectral samples");
+  if (!scale || !weight) return fail(PTYCHO_EINVAL, "scale and weight must be non-NULL");
+  if (N > 0 && (!b || !x)) return fail(PTYCHO_EINVAL, "b and x must be non-NULL");
+  if (clamp != 0 && clamp != 1) return fail(PTYCHO_EINVAL, "clamp must be 0 or 1");
+  MonoArgs a{};
+  double wsum = 0.0;
+  for (int j = 0; j < J; ++j) {
+    if (!(scale[j] > 0.0 && scale[j] <= 2.5)) return fail(PTYCHO_EINVAL, "scale values must lie in (0, 2.5]");
+    if (!(weight[j] >= 0.0 && std::isfinite(weight[j]))) return fail(PTYCHO_EINVAL, "weights must be finite, >= 0");
+    wsum += weight[j];
+    a.a[j] = (float)scale[j];
+    a.inv_a[j] = (float)(1.0 / scale[j]);
+    a.w[j] = (float)(weight[j] / (scale[j] * scale[j]));
+  }
+  if (!(wsum > 0.0)) return fail(PTYCHO_EINVAL, "weights are all zero");
+  a.b = b;
+  a.x = x;
+  a.resid = resid;
+  a.N = N;
+  a.M = M;
+  a.J = J;
+  a.k = k;
+  a.clamp = clamp;
+  PT_CUDA(launch_mono(a, static_cast<cudaStream_t>(cuda_stream)), "monochromatisation launch");
+  g_last_error.clear();
+  return PTYCHO_OK;
+}
+
 const char* ptycho_last_error(void) { return g_last_error.c_str(); }
 
 const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }

@@ -145,6 +145,18 @@ cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);
 cudaError_t launch_update_object(const UpdateArgs& u, cudaStream_t s);
 cudaError_t launch_update_probe(const UpdateArgs& u, cudaStream_t s);
 
+// numerical monochromatisation by CGLS (mono.cu): x_n = k CGLS steps on min ||C x - b_n|| from 0,
+// C = sum_j w[j] T_j, T_j sampling at c + (i - c) inv_a[j] (c = M / 2) with linear interpolation and
+// zero outside; one CTA per pattern
+constexpr int kMonoMaxJ = 64;
+struct MonoArgs {
+  const float* b; float* x;  // N x M x M each (x may be b)
+  double* resid;             // N x (k + 1) residual norms ||b - C x_i||, or null
+  int N, M, J, k, clamp;
+  float inv_a[kMonoMaxJ], a[kMonoMaxJ], w[kMonoMaxJ];  // 1 / a_j, a_j, weight_j / a_j^2
+};
+cudaError_t launch_mono(const MonoArgs& a, cudaStream_t s);
+
 // complex constraint (constraint.cu)
 struct ConstraintArgs {
   float2* O; const int2* pos; int N, M, obj_h, obj_w;

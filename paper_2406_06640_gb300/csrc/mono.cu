@@ -1,0 +1,290 @@
+// Numerical monochromatisation by CGLS (Sec. 4.2, Eqs. 12-13).
+//
+// Broadband pattern b = C m, C = sum_j w_j T_j (w_j: spectral weight / a_j^2), where T_j samples m at
+// c + (i - c) / a_j along both axes (c = M / 2, a_j = lambda_j / lambda_c) with linear interpolation
+// and zero outside the grid. k CGLS steps from x_0 = 0 give the least-squares solution over the
+// Krylov subspace of Eq. 13.
+//
+// One CTA per pattern runs all k steps on chip: the search direction p (with a one-pixel zero
+// border, so samples outside the grid read zeros) and the residual r live in shared memory; x and
+// the step's product vector live in registers (thread t owns the pixels t + m TPB, one column per
+// thread). C p gathers four neighbours per wavelength. C^T r runs separably per wavelength, r S_j
+// then S_j^T (.), from a table of the transposed interpolation built in shared memory with the same
+// coordinate formula as C, so the GPU's C^T is exactly the transpose of its C. Step sizes and norms
+// are FP64 block reductions in a fixed order (bitwise reproducible).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "engine.h"
+
+namespace ptycho {
+
+namespace {
+
+constexpr int kTapsT = 8;  // entries of one column of S_j (a_j <= 2.5: at most 2 a_j + 3)
+
+template <int M>
+struct MonoShape {
+  static constexpr int TPB = M == 128 ? 1024 : (M == 8 ? 64 : 256);
+  static constexpr int PPT = M * M / TPB;  // pixels per thread
+  static constexpr int LDP = M + 2;        // padded row of p
+  static constexpr size_t P_BYTES = (size_t)LDP * LDP * 4;
+  static constexpr size_t R_BYTES = (size_t)M * M * 4;
+  static constexpr size_t TAB_BYTES = (size_t)M * kTapsT * 8;
+  static constexpr size_t RED_BYTES = (size_t)(TPB / 32) * 2 * 8;
+  static constexpr size_t SPEC_BYTES = (size_t)3 * kMonoMaxJ * 4;
+  static constexpr size_t BYTES = P_BYTES + 2 * R_BYTES + TAB_BYTES + RED_BYTES + SPEC_BYTES;
+  static_assert(M * M % TPB == 0 && TPB % M == 0, "pixel ownership");
+};
+
+// sample position of output index i under scale 1 / a: i0 in [-1, M - 1] and fraction f (zero
+// weight outside the grid: i0 = -1, f = 0 reads the zero border)
+__device__ __forceinline__ void interp_at(int i, float c, float inv_a, int M, int& i0, float& f) {
+  const float t = fmaf((float)i - c, inv_a, c);
+  if (!(t >= -1.f && t < (float)M)) {
+    i0 = -1;
+    f = 0.f;
+    return;
+  }
+  const float fl = floorf(t);
+  i0 = (int)fl;
+  f = t - fl;
+}
+
+// FP64 sums of two per-thread values over the CTA, in a fixed order; every thread gets both
+template <int TPB>
+__device__ __forceinline__ void block_sum2(double a, double b, double* red, double& oa, double& ob) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();  // red is free (previous readers are done)
+  if (lane == 0) {
+    red[2 * warp] = a;
+    red[2 * warp + 1] = b;
+  }
+  __syncthreads();
+  double sa = 0.0, sb = 0.0;
+  for (int w = 0; w < TPB / 32; ++w) {
+    sa += red[2 * w];
+    sb += red[2 * w + 1];
+  }
+  oa = sa;
+  ob = sb;
+}
+
+template <int M>
+__global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoArgs a) {
+  using SH = MonoShape<M>;
+  constexpr int TPB = SH::TPB, PPT = SH::PPT, LDP = SH::LDP, RSTEP = TPB / M;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Pp = reinterpret_cast<float*>(smem);                        // (M + 2)^2, zero border
+  float* R = reinterpret_cast<float*>(smem + SH::P_BYTES);           // M^2
+  float* T = reinterpret_cast<float*>(smem + SH::P_BYTES + SH::R_BYTES);  // M^2, r S_j
+  int* tab_i = reinterpret_cast<int*>(smem + SH::P_BYTES + 2 * SH::R_BYTES);
+  float* tab_w = reinterpret_cast<float*>(tab_i + M * kTapsT);
+  double* red = reinterpret_cast<double*>(smem + SH::P_BYTES + 2 * SH::R_BYTES + SH::TAB_BYTES);
+  // spectrum: 1 / a_j, a_j, w_j
+  float* s_inv = reinterpret_cast<float*>(smem + SH::P_BYTES + 2 * SH::R_BYTES + SH::TAB_BYTES + SH::RED_BYTES);
+  float* s_a = s_inv + kMonoMaxJ;
+  float* s_w = s_a + kMonoMaxJ;
+
+  const int tid = threadIdx.x;
+  const int col = tid % M, row0 = tid / M;
+  const float c = 0.5f * (float)M;
+  const int n = blockIdx.x;
+  const float* bn = a.b + (size_t)n * M * M;
+  float* xn = a.x + (size_t)n * M * M;
+  double* rs = a.resid ? a.resid + (size_t)n * (a.k + 1) : nullptr;
+
+  // C^T v for the own pixels into acc, v in R (separable per wavelength, through T)
+  auto adjoint = [&](float (&acc)[PPT]) {
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) acc[m] = 0.f;
+    for (int j = 0; j < a.J; ++j) {
+      const float inv_a = s_inv[j], sa = s_a[j];
+      // column u of S_j: the sources x with i0(x) in {u - 1, u}; weight 1 - f (i0 = u) or f (i0 = u - 1)
+      for (int e = tid; e < M * kTapsT; e += TPB) {
+        const int u = e / kTapsT, l = e % kTapsT;
+        const int lo = max(0, (int)ceilf(fmaf((float)(u - 1) - c, sa, c)) - 1);
+        const int hi = min(M - 1, (int)floorf(fmaf((float)(u + 1) - c, sa, c)) + 1);
+        const int src = lo + l;
+        float w = 0.f;
+        if (src <= hi) {
+          int i0;
+          float f;
+          interp_at(src, c, inv_a, M, i0, f);
+          w = i0 == u ? 1.f - f : (i0 == u - 1 ? f : 0.f);
+        }
+        tab_i[e] = src <= hi ? src : 0;
+        tab_w[e] = w;
+      }
+      __syncthreads();
+      // T(y, v) = sum_x S_j[x, v] R(y, x) for the own (y, v)
+      {
+        int ci[kTapsT];
+        float cw[kTapsT];
+#pragma unroll
+        for (int l = 0; l < kTapsT; ++l) {
+          ci[l] = tab_i[col * kTapsT + l];
+          cw[l] = tab_w[col * kTapsT + l];
+        }
+#pragma unroll
+        for (int m = 0; m < PPT; ++m) {
+          const int y = row0 + m * RSTEP;
+          float s = 0.f;
+#pragma unroll
+          for (int l = 0; l < kTapsT; ++l) s = fmaf(cw[l], R[y * M + ci[l]], s);
+          T[y * M + col] = s;
+        }
+      }
+      __syncthreads();
+      // acc(u, v) += w_j sum_y S_j[y, u] T(y, v)
+      const float wj = s_w[j];
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) {
+        const int u = row0 + m * RSTEP;
+        float s = 0.f;
+#pragma unroll
+        for (int l = 0; l < kTapsT; ++l) s = fmaf(tab_w[u * kTapsT + l], T[tab_i[u * kTapsT + l] * M + col], s);
+        acc[m] = fmaf(wj, s, acc[m]);
+      }
+      __syncthreads();  // the table and T are rebuilt for the next wavelength
+    }
+  };
+
+  // C p for the own pixels into acc, p in Pp
+  auto forward = [&](float (&acc)[PPT]) {
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) acc[m] = 0.f;
+    for (int j = 0; j < a.J; ++j) {
+      const float inv_a = s_inv[j], wj = s_w[j];
+      int x0;
+      float fx;
+      interp_at(col, c, inv_a, M, x0, fx);
+      const float gx = 1.f - fx;
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) {
+        int y0;
+        float fy;
+        interp_at(row0 + m * RSTEP, c, inv_a, M, y0, fy);
+        const float* p0 = Pp + (y0 + 1) * LDP + (x0 + 1);
+        const float top = fmaf(fx, p0[1], gx * p0[0]);
+        const float bot = fmaf(fx, p0[LDP + 1], gx * p0[LDP]);
+        acc[m] = fmaf(wj, fmaf(fy, bot, (1.f - fy) * top), acc[m]);
+      }
+    }
+  };
+
+  // ---- start: spectrum to shared memory, zero border of p, r = b, x = 0
+  for (int i = tid; i < a.J; i += TPB) {
+    s_inv[i] = a.inv_a[i];
+    s_a[i] = a.a[i];
+    s_w[i] = a.w[i];
+  }
+  for (int i = tid; i < LDP * LDP; i += TPB) Pp[i] = 0.f;
+  float xk[PPT], acc[PPT];
+  double rr = 0.0;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    const int q = (row0 + m * RSTEP) * M + col;
+    const float v = bn[q];
+    R[q] = v;
+    rr += (double)v * (double)v;
+    xk[m] = 0.f;
+  }
+  __syncthreads();
+  adjoint(acc);  // s_0 = C^T b
+  double gamma = 0.0, rr_all = 0.0;
+  {
+    double g = 0.0;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) g += (double)acc[m] * (double)acc[m];
+    block_sum2<TPB>(g, rr, red, gamma, rr_all);
+  }
+  if (rs && tid == 0) rs[0] = sqrt(rr_all);
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) Pp[(row0 + m * RSTEP + 1) * LDP + col + 1] = acc[m];
+  __syncthreads();
+
+  for (int it = 0; it < a.k; ++it) {
+    if (!(gamma > 0.0)) {  // C^T r = 0: x is the least-squares solution already
+      if (rs && tid == 0) rs[it + 1] = sqrt(rr_all);
+      continue;
+    }
+    forward(acc);  // q = C p
+    double qq = 0.0;
+    {
+      double l = 0.0;
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) l += (double)acc[m] * (double)acc[m];
+      double unused;
+      block_sum2<TPB>(l, 0.0, red, qq, unused);
+    }
+    if (!(qq > 0.0)) {
+      if (rs && tid == 0) rs[it + 1] = sqrt(rr_all);
+      continue;
+    }
+    const float alpha = (float)(gamma / qq);
+    rr = 0.0;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      const int y = row0 + m * RSTEP;
+      xk[m] = fmaf(alpha, Pp[(y + 1) * LDP + col + 1], xk[m]);
+      const float r = fmaf(-alpha, acc[m], R[y * M + col]);
+      R[y * M + col] = r;
+      rr += (double)r * (double)r;
+    }
+    __syncthreads();
+    adjoint(acc);  // s = C^T r
+    double gnew = 0.0;
+    {
+      double g = 0.0;
+#pragma unroll
+      for (int m = 0; m < PPT; ++m) g += (double)acc[m] * (double)acc[m];
+      block_sum2<TPB>(g, rr, red, gnew, rr_all);
+    }
+    if (rs && tid == 0) rs[it + 1] = sqrt(rr_all);
+    const float beta = (float)(gnew / gamma);
+    gamma = gnew;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      float* pp = Pp + (row0 + m * RSTEP + 1) * LDP + col + 1;
+      *pp = fmaf(beta, *pp, acc[m]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    const float v = xk[m];
+    xn[(row0 + m * RSTEP) * M + col] = a.clamp ? fmaxf(v, 0.f) : v;
+  }
+}
+
+template <int M>
+cudaError_t launch_mono_t(const MonoArgs& a, cudaStream_t s) {
+  using SH = MonoShape<M>;
+  auto kern = k_mono_cgls<M>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::BYTES);
+  if (e != cudaSuccess) return e;
+  kern<<<a.N, SH::TPB, SH::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mono(const MonoArgs& a, cudaStream_t s) {
+  if (a.N == 0) return cudaSuccess;
+  switch (a.M) {
+    case 8: return launch_mono_t<8>(a, s);
+    case 16: return launch_mono_t<16>(a, s);
+    case 32: return launch_mono_t<32>(a, s);
+    case 64: return launch_mono_t<64>(a, s);
+    case 128: return launch_mono_t<128>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ptycho

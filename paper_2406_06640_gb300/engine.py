@@ -10,7 +10,7 @@ from typing import Optional
 import numpy as np
 import torch
 
-from .binding import BatchPlan, Plan
+from .binding import BatchPlan, Plan, monochromatise_raw
 
 
 def _require_cuda(t: torch.Tensor, name: str, dtype: torch.dtype):
@@ -106,3 +106,24 @@ class ReconstructionBatch:
 
     def close(self):
         self._plan.close()
+
+
+def monochromatise(b: torch.Tensor, scales, weights, k: int, clamp: bool = False, out: Optional[torch.Tensor] = None,
+                   with_residuals: bool = False, stream: Optional[torch.cuda.Stream] = None):
+    """Numerical monochromatisation (Sec. 4.2, Eqs. 12-13) of broadband patterns b ((N, M, M) float32 CUDA,
+    detector-centred): k CGLS steps per pattern on min ||C x - b|| with C the spectrum operator of
+    relative wavelengths `scales` (a_j = lambda_j / lambda_c) and `weights`. Returns x (or out), and
+    with_residuals the (N, k + 1) float64 residual norms as well. Enqueued on `stream`."""
+    _require_cuda(b, "b", torch.float32)
+    if b.dim() != 3 or b.shape[1] != b.shape[2]:
+        raise ValueError("b must be (N, M, M)")
+    x = out if out is not None else torch.empty_like(b)
+    _require_cuda(x, "out", torch.float32)
+    if x.shape != b.shape:
+        raise ValueError("out must have the shape of b")
+    N, M = b.shape[0], b.shape[1]
+    res = torch.empty((N, k + 1), dtype=torch.float64, device=b.device) if with_residuals else None
+    st = stream if stream is not None else torch.cuda.current_stream(b.device)
+    monochromatise_raw(M, scales, weights, N, k, b.data_ptr(), x.data_ptr(), res.data_ptr() if res is not None else 0,
+                       clamp, st.cuda_stream)
+    return (x, res) if with_residuals else x
