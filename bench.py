@@ -30,9 +30,22 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# the CPU oracle legs report rates on a stated number of cores: BLAS / OpenMP pools default to one
+# thread (set before numpy loads its BLAS)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def cpu_threads():
+    """Threads the CPU oracle legs may use (the BLAS pool size set above or by the caller)."""
+    try:
+        return max(1, int(os.environ.get("OPENBLAS_NUM_THREADS", "1")))
+    except ValueError:
+        return 1
 sys.path.insert(0, ROOT)
 
 METRIC = "pattern-mode updates/s"
@@ -54,6 +67,10 @@ def parse():
     return ap.parse_args()
 
 
+MONO_LINES5 = [1.0, 1.0125, 1.025, 1.0375, 1.05]
+MONO_WHITE32 = [1.0 + 0.75 * j / 31 for j in range(32)]
+MONO_WHITE32_W = [math.exp(-0.5 * ((a - 1.3) / 0.2) ** 2) for a in MONO_WHITE32]
+
 WORKLOADS = {
     "far128x4": (1, "far-field 4-mode pc-engine iteration (probe 128^2, K=4, N=900 Fermat spiral, "
                     "object 640^2, 5% bandwidth, sigma 1.5, 1e6 photons)"),
@@ -69,6 +86,14 @@ WORKLOADS = {
                            rpie_alpha_probe=0.5)),
     "far128x4-dm": (1, "far128x4 with the pc-DM engine (exit-wave state per position and mode in HBM)",
                     dict(engine="dm")),
+    "mono128": (1, "numerical monochromatisation (CGLS, k=25) of the 900 broadband 128^2 patterns of far128x4, "
+                   "5-line spectrum of 5% bandwidth about the shortest wavelength (the one the data were "
+                   "generated with), one CTA per pattern",
+                dict(mono=(MONO_LINES5, [0.2] * 5, 25))),
+    "mono128-white": (1, "numerical monochromatisation (CGLS, k=25) of 900 patterns of 128^2 with a white-light "
+                         "spectrum: 32 lines over a factor 1.75 (400-700 nm about 400 nm), Gaussian weights; the "
+                         "patterns of far128x4 stand in for white-light data (the cost does not depend on b)",
+                      dict(mono=(MONO_WHITE32, MONO_WHITE32_W, 25))),
     "batch64": (3, "64 independent reconstructions of uneven sizes (probe 64-256, 100-1600 positions, K 1-4, "
                    "far/near 50/50, sigma 0.5-3), one CUDA graph launch per iteration"),
     "warmstart": (4, "time to intensity NRMSE <= 0.05 against the noise-free patterns: flat start with the true "
@@ -203,29 +228,29 @@ def oracle_rate(prob, params, n_positions, iterations=1):
     return n_positions * prob.K * iterations / dt, dt
 
 
-def traffic_record(kernel_tag):
-    """DRAM bytes per launch of the fused kernel from a committed ncu summary, if it was taken on
-    the current kernel source (hash match); None otherwise."""
-    path = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
+def traffic_record(kernel_tag, name="fused_kernel_traffic.json", workload="far128x4"):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if it was taken on the current
+    kernel source (hash match) and this workload; None otherwise."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     try:
         rec = json.load(open(path))
     except ValueError:
         return None
-    if rec.get("source_sha256") != kernel_tag:
+    if rec.get("source_sha256") != kernel_tag or rec.get("bench_workload", "far128x4") != workload:
         return None
     return rec.get("dram_bytes_per_launch_full_size")
 
 
-def kernel_source_hash():
-    """Hash of what the fused kernel is compiled from: fft.cuh, pc_fused.cu and its argument struct."""
+def kernel_source_hash(files=("fft.cuh", "pc_fused_kernel.cuh", "pc_fused.cu"), struct="FusedArgs"):
+    """Hash of what a kernel is compiled from: its sources and its argument struct."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_06640_gb300", "csrc")
-    for f in ("fft.cuh", "pc_fused_kernel.cuh", "pc_fused.cu"):
+    for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     hdr = open(os.path.join(csrc, "engine.h")).read()
-    i = hdr.find("struct FusedArgs")
+    i = hdr.find("struct " + struct)
     h.update(hdr[i:hdr.find("};", i)].encode() if i >= 0 else b"")
     return h.hexdigest()
 
@@ -246,6 +271,11 @@ def run_reference(args):
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
+    if _WORKLOAD.startswith("mono"):
+        from synth import make_problem
+
+        scales, weights, k = WORKLOADS[_WORKLOAD][2]["mono"]
+        return run_reference_mono(args, make_problem(WORKLOADS[_WORKLOAD][0]), scales, weights, k)
     prob, params = workload()
     n_pos = 100
     for _ in range(args.warmup):
@@ -263,11 +293,145 @@ def run_reference(args):
             "impl": "reference",
             "config": config_of(prob, {"sample": f"each step: one oracle iteration over the first {n_pos} "
                                                  f"of the {prob.N} positions"}),
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"{args.steps} steps of one FP64 oracle iteration over {n_pos} positions x "
                                        f"{prob.K} modes (numpy/scipy, single-threaded)"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def mono_flops(M, J, k):
+    """Algorithmic FLOPs of k CGLS steps on one pattern: C and C^T each hold 4 J M^2 non-zeros
+    (a multiply and an add each), applied 2 k + 1 times, plus 10 M^2 per step for the vector updates
+    and norms."""
+    return (2 * k + 1) * 8.0 * J * M * M + 10.0 * k * M * M
+
+
+def run_reference_mono(args, prob, scales, weights, k):
+    from oracle import mono
+
+    n_pat = 2
+    B = prob.I[:n_pat].astype(np.float64)
+    for _ in range(args.warmup):
+        mono.monochromatise(B, scales, weights, k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        mono.monochromatise(B, scales, weights, k)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_pat * args.steps / total
+    unit = "patterns/s"
+    line = {"metric": "monochromatised patterns/s", "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOADS[_WORKLOAD][1], "M": prob.M, "J": len(scales), "k": k,
+                       "sample": f"each step: the oracle on {n_pat} of the {prob.N} patterns"},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} steps of the FP64 oracle CGLS on {n_pat} patterns (numpy)"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours_mono(args):
+    """Monochromatisation: one step = one call over every pattern (one launch, one CTA each)."""
+    ws, rank, local = dist_setup(args)
+    import torch
+
+    from paper_2406_06640_gb300.engine import monochromatise
+    from synth import make_problem
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: a CUDA device is required (no CPU fallback)")
+    scales, weights, k = WORKLOADS[_WORKLOAD][2]["mono"]
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prob = make_problem(WORKLOADS[_WORKLOAD][0])
+    N, M, J = prob.N, prob.M, len(scales)
+    stream = torch.cuda.current_stream(dev)
+    b = torch.from_numpy(prob.I).to(dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        monochromatise(b, scales, weights, k, out=x, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        monochromatise(b, scales, weights, k, out=x, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_max = max_over_ranks(ws, sum(step_ms), dev)
+    value = ws * N * args.steps / (t_max / 1e3)
+    flops = N * mono_flops(M, J, k)
+    avg_s = sum(step_ms) / len(step_ms) / 1e3
+    achieved = flops / avg_s / 1e12
+    peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = traffic_record(kernel_source_hash(("mono.cu",), "MonoArgs"), "mono_kernel_traffic.json",
+                             _WORKLOAD)
+    # end to end: the broadband patterns from pinned host memory, the monochromatic ones back
+    b_h = torch.from_numpy(prob.I).pin_memory()
+    x_h = torch.empty_like(b_h).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    t_e2e = 0.0
+    for i in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        b.copy_(b_h, non_blocking=True)
+        monochromatise(b, scales, weights, k, out=x, stream=stream)
+        x_h.copy_(x, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            t_e2e += time.perf_counter() - t0
+    t_e2e = max_over_ranks(ws, t_e2e, dev)
+    e2e_value = ws * N * e2e_steps / t_e2e
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import mono
+
+        # patterns one after another until about 10 s of CPU work (at least 2)
+        n_pat, t0 = 0, time.perf_counter()
+        while n_pat < N and (n_pat < 2 or time.perf_counter() - t0 < 10.0):
+            mono.monochromatise(prob.I[n_pat:n_pat + 1].astype(np.float64), scales, weights, k)
+            n_pat += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": n_pat / dt, "unit": "patterns/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"the FP64 oracle CGLS on the first {n_pat} of the {N} patterns ({dt:.1f} s, numpy)"}
+    if rank == 0:
+        line = {"metric": "monochromatised patterns/s", "value": value, "unit": "patterns/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS[_WORKLOAD][1], "N": N, "M": M, "J": J, "k": k,
+                           "l2": "flushed before each timed step (256 MiB write)",
+                           "parallelism": f"replicas{ws}" if ws > 1 else "single GPU"},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": traffic, "kernel": f"k_mono_cgls<{M}>",
+                             "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FMA pipe, max clock)",
+                             "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "patterns/s", "h2d_bytes_per_step": b.numel() * 4,
+                        "d2h_bytes_per_step": x.numel() * 4},
+                "gpu_launches": args.steps, "clocks": clocks,
+                "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
     return 0
 
 
@@ -485,6 +649,8 @@ def run_ours_warmstart(args):
 def run_ours(args):
     if _WORKLOAD == "batch64":
         return run_ours_batch(args)
+    if _WORKLOAD.startswith("mono"):
+        return run_ours_mono(args)
     if _WORKLOAD == "warmstart":
         return run_ours_warmstart(args)
     ws, rank, local = dist_setup(args)
@@ -565,7 +731,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, dt = oracle_rate(prob, params, prob.N)
-        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
                "sample": f"one FP64 oracle iteration of the full workload ({prob.N} positions x {prob.K} modes, "
                          f"{dt:.1f} s, numpy/scipy single-threaded)"}
     if rank == 0:

@@ -125,3 +125,32 @@ def test_host_permutation_matches_the_oracle(n, seed, stream, t):
     from oracle import philox
 
     assert pg.permutation(n, seed, stream, t) == philox.permutation(n, seed, stream, t).tolist()
+
+
+@pytest.mark.parametrize("M,scales,weights,N,k,clamp,expect", [
+    (48, [1.0], [1.0], 1, 3, 0, 4), (256, [1.0], [1.0], 1, 3, 0, 4), (0, [1.0], [1.0], 1, 3, 0, 1),
+    (64, [], [], 1, 3, 0, 1), (64, [1.0] * 65, [1.0] * 65, 1, 3, 0, 4), (64, [1.0], [1.0], 1, -1, 0, 1),
+    (64, [1.0], [1.0], -1, 3, 0, 1), (64, [2.6], [1.0], 1, 3, 0, 1), (64, [0.0], [1.0], 1, 3, 0, 1),
+    (64, [1.0], [float("nan")], 1, 3, 0, 1), (64, [1.0, 1.2], [0.0, 0.0], 1, 3, 0, 1),
+    (64, [1.0], [1.0], 1, 3, 2, 1),
+])
+def test_monochromatisation_validation(M, scales, weights, N, k, clamp, expect):
+    """Rejected before any device work (non-NULL dummy pointers stand in for the device buffers)."""
+    lib = pg.load()
+    J = len(scales)
+    sc = (ctypes.c_double * max(J, 1))(*scales)
+    wt = (ctypes.c_double * max(J, 1))(*weights)
+    dummy = ctypes.c_void_p(16)
+    st = lib.ptycho_monochromatise(M, J, sc, wt, N, k, dummy, dummy, None, clamp, None)
+    assert st == expect, lib.ptycho_last_error().decode()
+    assert lib.ptycho_last_error().decode()
+
+
+def test_monochromatisation_null_buffers_and_empty_batch():
+    lib = pg.load()
+    one = (ctypes.c_double * 1)(1.0)
+    assert lib.ptycho_monochromatise(64, 1, one, one, 2, 3, None, None, None, 0, None) == 1
+    assert lib.ptycho_monochromatise(64, 1, None, one, 2, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None, 0,
+                                     None) == 1
+    # no patterns: nothing to launch, no device needed
+    assert lib.ptycho_monochromatise(64, 1, one, one, 0, 3, None, None, None, 0, None) == 0
