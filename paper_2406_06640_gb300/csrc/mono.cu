@@ -30,7 +30,7 @@ struct MonoShape {
   static constexpr int LDP = M + 2;        // padded row of p
   static constexpr size_t P_BYTES = (size_t)LDP * LDP * 4;
   static constexpr size_t R_BYTES = (size_t)M * M * 4;
-  static constexpr size_t TAB_BYTES = (size_t)M * kTapsT * 8;
+  static constexpr size_t TAB_BYTES = (size_t)M * kTapsT * 8 + (size_t)M * 4;  // taps, then counts
   static constexpr size_t RED_BYTES = (size_t)(TPB / 32) * 2 * 8;
   static constexpr size_t SPEC_BYTES = (size_t)3 * kMonoMaxJ * 4;
   static constexpr size_t BYTES = P_BYTES + 2 * R_BYTES + TAB_BYTES + RED_BYTES + SPEC_BYTES;
@@ -83,8 +83,11 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
   float* Pp = reinterpret_cast<float*>(smem);                        // (M + 2)^2, zero border
   float* R = reinterpret_cast<float*>(smem + SH::P_BYTES);           // M^2
   float* T = reinterpret_cast<float*>(smem + SH::P_BYTES + SH::R_BYTES);  // M^2, r S_j
-  int* tab_i = reinterpret_cast<int*>(smem + SH::P_BYTES + 2 * SH::R_BYTES);
-  float* tab_w = reinterpret_cast<float*>(tab_i + M * kTapsT);
+  // column u of S_j: its non-zero taps (weight, source index as float bits) in increasing source
+  // order, zero-filled to kTapsT, and their count
+  float2* tab = reinterpret_cast<float2*>(smem + SH::P_BYTES + 2 * SH::R_BYTES);
+  const float4* tab4 = reinterpret_cast<const float4*>(tab);
+  int* tab_n = reinterpret_cast<int*>(tab + M * kTapsT);
   double* red = reinterpret_cast<double*>(smem + SH::P_BYTES + 2 * SH::R_BYTES + SH::TAB_BYTES);
   // spectrum: 1 / a_j, a_j, w_j
   float* s_inv = reinterpret_cast<float*>(smem + SH::P_BYTES + 2 * SH::R_BYTES + SH::TAB_BYTES + SH::RED_BYTES);
@@ -106,6 +109,8 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
     for (int j = 0; j < a.J; ++j) {
       const float inv_a = s_inv[j], sa = s_a[j];
       // column u of S_j: the sources x with i0(x) in {u - 1, u}; weight 1 - f (i0 = u) or f (i0 = u - 1)
+      // (M * kTapsT is a multiple of 32 and so is TPB: every warp runs whole iterations, and the 8
+      // lanes of one column sit in one warp)
       for (int e = tid; e < M * kTapsT; e += TPB) {
         const int u = e / kTapsT, l = e % kTapsT;
         const int lo = max(0, (int)ceilf(fmaf((float)(u - 1) - c, sa, c)) - 1);
@@ -118,25 +123,34 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
           interp_at(src, c, inv_a, M, i0, f);
           w = i0 == u ? 1.f - f : (i0 == u - 1 ? f : 0.f);
         }
-        tab_i[e] = src <= hi ? src : 0;
-        tab_w[e] = w;
+        const unsigned nz = __ballot_sync(0xffffffffu, w != 0.f);
+        const unsigned grp = (nz >> ((tid & 31) & ~(kTapsT - 1))) & ((1u << kTapsT) - 1u);
+        const int cnt = __popc(grp);
+        if (w != 0.f) tab[u * kTapsT + __popc(grp & ((1u << l) - 1u))] = make_float2(w, __int_as_float(src));
+        if (l >= cnt) tab[u * kTapsT + l] = make_float2(0.f, __int_as_float(0));
+        if (l == 0) tab_n[u] = cnt;
       }
       __syncthreads();
-      // T(y, v) = sum_x S_j[x, v] R(y, x) for the own (y, v)
+      // T(y, v) = sum_x S_j[x, v] R(y, x) for the own (y, v); zero-filled taps add exact zeros
       {
         int ci[kTapsT];
         float cw[kTapsT];
 #pragma unroll
-        for (int l = 0; l < kTapsT; ++l) {
-          ci[l] = tab_i[col * kTapsT + l];
-          cw[l] = tab_w[col * kTapsT + l];
+        for (int h = 0; h < kTapsT / 2; ++h) {
+          const float4 e = tab4[col * (kTapsT / 2) + h];
+          cw[2 * h] = e.x;
+          ci[2 * h] = __float_as_int(e.y);
+          cw[2 * h + 1] = e.z;
+          ci[2 * h + 1] = __float_as_int(e.w);
         }
+        const int nt = __reduce_max_sync(0xffffffffu, tab_n[col]);
 #pragma unroll
         for (int m = 0; m < PPT; ++m) {
           const int y = row0 + m * RSTEP;
           float s = 0.f;
 #pragma unroll
-          for (int l = 0; l < kTapsT; ++l) s = fmaf(cw[l], R[y * M + ci[l]], s);
+          for (int l = 0; l < kTapsT; ++l)
+            if (l < nt) s = fmaf(cw[l], R[y * M + ci[l]], s);
           T[y * M + col] = s;
         }
       }
@@ -146,9 +160,15 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
 #pragma unroll
       for (int m = 0; m < PPT; ++m) {
         const int u = row0 + m * RSTEP;
+        const int nh = (__reduce_max_sync(0xffffffffu, tab_n[u]) + 1) / 2;
         float s = 0.f;
 #pragma unroll
-        for (int l = 0; l < kTapsT; ++l) s = fmaf(tab_w[u * kTapsT + l], T[tab_i[u * kTapsT + l] * M + col], s);
+        for (int h = 0; h < kTapsT / 2; ++h)
+          if (h < nh) {
+            const float4 e = tab4[u * (kTapsT / 2) + h];
+            s = fmaf(e.x, T[__float_as_int(e.y) * M + col], s);
+            s = fmaf(e.z, T[__float_as_int(e.w) * M + col], s);
+          }
         acc[m] = fmaf(wj, s, acc[m]);
       }
       __syncthreads();  // the table and T are rebuilt for the next wavelength
@@ -186,22 +206,22 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
   }
   for (int i = tid; i < LDP * LDP; i += TPB) Pp[i] = 0.f;
   float xk[PPT], acc[PPT];
-  double rr = 0.0;
+  float rr = 0.f;  // per-thread partial sums in FP32 (PPT terms), CTA sums in FP64
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
     const int q = (row0 + m * RSTEP) * M + col;
     const float v = bn[q];
     R[q] = v;
-    rr += (double)v * (double)v;
+    rr = fmaf(v, v, rr);
     xk[m] = 0.f;
   }
   __syncthreads();
   adjoint(acc);  // s_0 = C^T b
   double gamma = 0.0, rr_all = 0.0;
   {
-    double g = 0.0;
+    float g = 0.f;
 #pragma unroll
-    for (int m = 0; m < PPT; ++m) g += (double)acc[m] * (double)acc[m];
+    for (int m = 0; m < PPT; ++m) g = fmaf(acc[m], acc[m], g);
     block_sum2<TPB>(g, rr, red, gamma, rr_all);
   }
   if (rs && tid == 0) rs[0] = sqrt(rr_all);
@@ -217,9 +237,9 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
     forward(acc);  // q = C p
     double qq = 0.0;
     {
-      double l = 0.0;
+      float l = 0.f;
 #pragma unroll
-      for (int m = 0; m < PPT; ++m) l += (double)acc[m] * (double)acc[m];
+      for (int m = 0; m < PPT; ++m) l = fmaf(acc[m], acc[m], l);
       double unused;
       block_sum2<TPB>(l, 0.0, red, qq, unused);
     }
@@ -228,22 +248,22 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
       continue;
     }
     const float alpha = (float)(gamma / qq);
-    rr = 0.0;
+    rr = 0.f;
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       const int y = row0 + m * RSTEP;
       xk[m] = fmaf(alpha, Pp[(y + 1) * LDP + col + 1], xk[m]);
       const float r = fmaf(-alpha, acc[m], R[y * M + col]);
       R[y * M + col] = r;
-      rr += (double)r * (double)r;
+      rr = fmaf(r, r, rr);
     }
     __syncthreads();
     adjoint(acc);  // s = C^T r
     double gnew = 0.0;
     {
-      double g = 0.0;
+      float g = 0.f;
 #pragma unroll
-      for (int m = 0; m < PPT; ++m) g += (double)acc[m] * (double)acc[m];
+      for (int m = 0; m < PPT; ++m) g = fmaf(acc[m], acc[m], g);
       block_sum2<TPB>(g, rr, red, gnew, rr_all);
     }
     if (rs && tid == 0) rs[it + 1] = sqrt(rr_all);
