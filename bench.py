@@ -243,7 +243,7 @@ def traffic_record(kernel_tag, name="fused_kernel_traffic.json", workload="far12
     return rec.get("dram_bytes_per_launch_full_size")
 
 
-def kernel_source_hash(files=("fft.cuh", "pc_fused_kernel.cuh", "pc_fused.cu"), struct="FusedArgs"):
+def kernel_source_hash(files=("cluster.cuh", "fft.cuh", "pc_fused_kernel.cuh", "pc_fused.cu"), struct="FusedArgs"):
     """Hash of what a kernel is compiled from: its sources and its argument struct."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_06640_gb300", "csrc")

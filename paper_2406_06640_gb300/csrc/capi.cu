@@ -462,8 +462,8 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   const size_t plane = (size_t)p.obj_h * p.obj_w;
   float2* d_no;
   float *d_do, *d_bmo;
-  PT_CUDA(pl->alloc(&d_no, (size_t)kObjSplit * plane), "alloc object partials");
-  PT_CUDA(pl->alloc(&d_do, (size_t)kObjSplit * plane), "alloc object partials");
+  PT_CUDA(pl->alloc(&d_no, plane), "alloc object sums");
+  PT_CUDA(pl->alloc(&d_do, plane), "alloc object sums");
   PT_CUDA(pl->alloc(&d_bmo, (size_t)tx * ty), "alloc tile maxima");
   const int pb = (int)((MM + 255) / 256);
   float2* d_np;
@@ -473,15 +473,36 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_p2, MM), "alloc probe sums");
   PT_CUDA(pl->alloc(&d_bmp, (size_t)pb), "alloc probe maxima");
   PT_CUDA(pl->alloc(&d_cbar, (size_t)N), "alloc cbar");
-  long long *d_lna, *d_phi, *d_diff;
-  int* d_cover;
-  PT_CUDA(pl->alloc(&d_lna, (size_t)(p.obj_h + 1) * (p.obj_w + 1)), "alloc constraint tables");
-  PT_CUDA(pl->alloc(&d_phi, (size_t)(p.obj_h + 1) * (p.obj_w + 1)), "alloc constraint tables");
-  PT_CUDA(pl->alloc(&d_diff, (size_t)(p.obj_h + 1) * (p.obj_w + 1)), "alloc constraint sums");
-  PT_CUDA(pl->alloc(&d_cover, plane), "alloc coverage");
-  {
-    const std::vector<int> cover = coverage_counts(pl->h_pos, M, p.obj_h, p.obj_w);
-    PT_CUDA(cudaMemcpy(d_cover, cover.data(), sizeof(int) * plane, cudaMemcpyHostToDevice), "copy coverage");
+  long long *d_lna, *d_phi, *d_cbar_q;
+  PT_CUDA(pl->alloc(&d_lna, plane), "alloc constraint maps");
+  PT_CUDA(pl->alloc(&d_phi, plane), "alloc constraint maps");
+  PT_CUDA(pl->alloc(&d_cbar_q, (size_t)N), "alloc cbar");
+  // the constraint visits every box of a tile: the whole scan's lists (the batch lists when
+  // there is one batch)
+  const int* d_cstart = d_start;
+  const int4* d_clist = d_list;
+  if (pl->nb > 1) {
+    std::vector<std::vector<int>> lists((size_t)tx * ty);
+    for (int n = 0; n < N; ++n) {
+      const int2 q = pl->h_pos[n];
+      for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
+        for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
+    }
+    std::vector<int> cs;
+    std::vector<int4> cl;
+    for (const auto& l : lists) {
+      cs.push_back((int)cl.size());
+      for (int n : l) cl.push_back(make_int4(n, pl->h_pos[n].x, pl->h_pos[n].y, 0));
+    }
+    cs.push_back((int)cl.size());
+    int* ds;
+    int4* dl;
+    PT_CUDA(pl->alloc(&ds, cs.size()), "alloc constraint tile lists");
+    PT_CUDA(pl->alloc(&dl, cl.size()), "alloc constraint tile lists");
+    PT_CUDA(cudaMemcpy(ds, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice), "copy tiles");
+    PT_CUDA(cudaMemcpy(dl, cl.data(), sizeof(int4) * cl.size(), cudaMemcpyHostToDevice), "copy tiles");
+    d_cstart = ds;
+    d_clist = dl;
   }
   PT_CUDA(pl->alloc(&pl->d_errhist, (size_t)kErrHistory), "alloc error history");
   unsigned long long* d_runs;
@@ -546,10 +567,13 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ca.obj_h = p.obj_h;
   ca.obj_w = p.obj_w;
   ca.cbar = d_cbar;
-  ca.sat_lna = d_lna;
-  ca.sat_phi = d_phi;
-  ca.diff = d_diff;
-  ca.cover = d_cover;
+  ca.map_lna = d_lna;
+  ca.map_phi = d_phi;
+  ca.cbar_q = d_cbar_q;
+  ca.tile_start = d_cstart;
+  ca.tile_pos = d_clist;
+  ca.tiles_x = tx;
+  ca.tiles_y = ty;
   ca.alpha1 = (float)p.alpha1;
   ca.alpha2 = (float)p.alpha2;
   ca.cbar_min = (float)p.cbar_min;
@@ -1199,7 +1223,7 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
   }
   if (pl->mb > 0) fft = pl->nb * 6 - 5;  // per batch: the fused kernel and the 5 update kernels
   if (pl->d_psi) fft += 2;                // pc-DM probe partials and their gather (probe step on)
-  return fft + 5 + (in_window ? 6 : 0);
+  return fft + 5 + (in_window ? 3 : 0);  // constraint: maps, box sums, apply
 }
 
 ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32_t t, int32_t* out) {
@@ -1251,25 +1275,6 @@ const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }
 
 // ---- helpers shared with the allocation-free entry point (capi_static.cu)
 namespace ptycho {
-std::vector<int> coverage_counts(const std::vector<int2>& pos, int M, int obj_h, int obj_w) {
-  // 2-D difference array of the boxes, then prefix sums along both axes
-  std::vector<int> d((size_t)(obj_h + 1) * (obj_w + 1), 0);
-  const int W1 = obj_w + 1;
-  for (const int2& q : pos) {
-    d[(size_t)q.x * W1 + q.y] += 1;
-    d[(size_t)q.x * W1 + q.y + M] -= 1;
-    d[(size_t)(q.x + M) * W1 + q.y] -= 1;
-    d[(size_t)(q.x + M) * W1 + q.y + M] += 1;
-  }
-  for (int y = 0; y <= obj_h; ++y)
-    for (int x = 1; x <= obj_w; ++x) d[(size_t)y * W1 + x] += d[(size_t)y * W1 + x - 1];
-  for (int y = 1; y <= obj_h; ++y)
-    for (int x = 0; x <= obj_w; ++x) d[(size_t)y * W1 + x] += d[(size_t)(y - 1) * W1 + x];
-  std::vector<int> out((size_t)obj_h * obj_w);
-  for (int y = 0; y < obj_h; ++y)
-    for (int x = 0; x < obj_w; ++x) out[(size_t)y * obj_w + x] = d[(size_t)y * W1 + x];
-  return out;
-}
 ptycho_status capi_validate(const ptycho_params* p) { return validate(p); }
 void capi_step_coefficients(const ptycho_params* p, UpdateArgs* u) { step_coefficients(*p, *u); }
 ptycho_status capi_fail(ptycho_status s, const std::string& msg) { return fail(s, msg); }

@@ -145,8 +145,8 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     fa.errpart = cv.take<double>((size_t)slots * K);
     ua.tile_start = cv.take<int>(start.size());
     ua.tile_pos = cv.take<int4>(flat.size());
-    ua.no_part = cv.take<float2>((size_t)kObjSplit * plane);
-    ua.do_part = cv.take<float>((size_t)kObjSplit * plane);
+    ua.no_part = cv.take<float2>(plane);
+    ua.do_part = cv.take<float>(plane);
     ua.blk_max_o = cv.take<float>((size_t)tx * ty);
     ua.np_sum = cv.take<float2>((size_t)K * MM);
     ua.dp_sum = cv.take<float>(MM);
@@ -155,10 +155,9 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     ua.errhist = cv.take<double>((size_t)kErrHistory);
     ua.run_counter = cv.take<unsigned long long>(1);
     ca.cbar = cv.take<float>((size_t)N);
-    ca.sat_lna = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
-    ca.sat_phi = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
-    ca.diff = cv.take<long long>((size_t)(p->obj_h + 1) * (p->obj_w + 1));
-    ca.cover = cv.take<int>(plane);
+    ca.cbar_q = cv.take<long long>((size_t)N);
+    ca.map_lna = cv.take<long long>(plane);
+    ca.map_phi = cv.take<long long>(plane);
   };
   FusedArgs fa{};
   UpdateArgs ua{};
@@ -188,11 +187,6 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   if (!flat.empty())
     PS_CUDA(cudaMemcpyAsync(const_cast<int4*>(ua.tile_pos), flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice, s),
             "copy tile lists");
-  {
-    const std::vector<int> cover = coverage_counts(hpos, M, p->obj_h, p->obj_w);
-    PS_CUDA(cudaMemcpyAsync(const_cast<int*>(ca.cover), cover.data(), sizeof(int) * plane, cudaMemcpyHostToDevice, s),
-            "copy coverage");
-  }
   std::vector<float2> tw(M), hq(M);
   for (int m = 0; m < M; ++m) {
     const double a = -2.0 * M_PI * m / M;
@@ -264,6 +258,10 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   ca.alpha2 = (float)p->alpha2;
   ca.cbar_min = (float)p->cbar_min;
   ca.cbar_max = (float)p->cbar_max;
+  ca.tile_start = ua.tile_start;
+  ca.tile_pos = ua.tile_pos;
+  ca.tiles_x = tx;
+  ca.tiles_y = ty;
 
   for (int i = 0; i < n_iter; ++i) {
     const long long t = (long long)p->start_iteration + i;

@@ -11,7 +11,7 @@ namespace ptycho {
 constexpr int kMaxTaps = 31;        // largest odd Gaussian kernel side accepted (Eq. 7 support)
 constexpr int kObjTile = 32;        // object tile side of the gather kernels
 constexpr int kMaxModes = 8;        // probe modes K handled (one cluster rank per mode)
-constexpr int kObjSplit = 8;        // position groups per object tile (partial sums, fixed order)
+constexpr int kObjSplit = 8;        // position groups per object tile (one cluster, fixed order)
 constexpr int kErrHistory = 4096;   // ring of per-iteration errors kept on the device
 
 // Arguments of the fused per-position kernel (one cluster of K CTAs per position).
@@ -117,7 +117,7 @@ struct UpdateArgs {
   const int* tile_start;  // (tiles_y * tiles_x + 1) CSR offsets into tile_pos
   const int4* tile_pos;   // per tile, (n, row, col, 0) of each overlapping position, increasing n
   int tiles_x, tiles_y;
-  float2* no_part; float* do_part;  // kObjSplit x obj_h x obj_w partials
+  float2* no_part; float* do_part;  // N_O and D_O, obj_h x obj_w each
   float* blk_max_o;                  // per object tile
   // probe gather
   float2* np_sum; float* dp_sum; float* p2;  // K x M x M, M x M, M x M
@@ -161,13 +161,12 @@ cudaError_t launch_mono(const MonoArgs& a, cudaStream_t s);
 struct ConstraintArgs {
   float2* O; const int2* pos; int N, M, obj_h, obj_w;
   float* cbar; float alpha1, alpha2, cbar_min, cbar_max;
-  long long* sat_lna; long long* sat_phi;  // summed-area tables of |ln a| and |phi|, 32.32 fixed point
-  long long* diff;                 // (obj_h + 1) x (obj_w + 1) difference array, 32.32 fixed point
-  const int* cover;                // boxes covering each object pixel (fixed per plan)
+  long long* map_lna; long long* map_phi;  // |ln a| and |phi| per object pixel, 32.32 fixed point
+  long long* cbar_q;                       // C_n in 32.32 fixed point (N)
+  const int* tile_start;  // (tiles_y * tiles_x + 1) CSR offsets into tile_pos, kObjTile tiles
+  const int4* tile_pos;   // per tile, (n, row, col, 0) of every position whose box overlaps it
+  int tiles_x, tiles_y;
 };
-
-// boxes covering each object pixel, obj_h x obj_w (host helper, plan time)
-std::vector<int> coverage_counts(const std::vector<int2>& pos, int M, int obj_h, int obj_w);
 cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s);
 
 // plan-time helpers (update.cu)

@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "engine.h"
+#include "cluster.cuh"
 #include "fft.cuh"
 
 namespace ptycho {
@@ -170,12 +171,24 @@ __global__ void k_dm_probe_partials(const UpdateArgs u) {
 }
 
 // ------------------------------------------------------------------ object: per-tile gather of the contributions
-// grid (tiles_x, tiles_y, kObjSplit), block 32 x 8; thread (tx, ty) owns pixels (Y0 + ty + 8 i, X0 + tx)
+// grid (tiles_x, tiles_y, kObjSplit) in clusters of the kObjSplit blocks of one tile, block 32 x 8;
+// thread (tx, ty) owns pixels (Y0 + ty + 8 i, X0 + tx). Block `split` sums positions split,
+// split + kObjSplit, ... of the tile's list; the partial tiles meet in distributed shared memory,
+// where rank r adds up rows 4r .. 4r + 3 over the ranks in order and writes N_O, D_O; rank 0 also
+// takes the tile maximum of D_O.
 __global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
+  constexpr int TT = kObjTile * kObjTile, RPR = TT / kObjSplit;  // pixels finished per rank
+  static_assert(RPR <= 256 && RPR % 32 == 0 && kObjTile == 32, "tile split");
+  __shared__ float2 s_acc[TT];
+  __shared__ float s_den[TT];
+  __shared__ float s_max[kObjSplit * (RPR / 32)];
   const int tile = blockIdx.y * u.tiles_x + blockIdx.x;
   const int split = blockIdx.z;
-  const int X = blockIdx.x * kObjTile + threadIdx.x;
-  const int Y0 = blockIdx.y * kObjTile + threadIdx.y;
+  const unsigned rank = cluster_ctarank();
+  const int tx0 = blockIdx.x * kObjTile, ty0 = blockIdx.y * kObjTile;
+  const int X = tx0 + threadIdx.x;
+  const int Y0 = ty0 + threadIdx.y;
+  const int lt = threadIdx.y * 32 + threadIdx.x;
   const int M = u.M;
   const size_t MM = (size_t)M * M;
   float2 acc[4];
@@ -186,65 +199,67 @@ __global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
     den[i] = 0.f;
   }
   const int s0 = u.tile_start[tile], s1 = u.tile_start[tile + 1];
-  for (int idx = s0 + split; idx < s1; idx += kObjSplit) {
-    const int4 ent = u.tile_pos[idx];  // (n, row, col)
-    const int cx = X - ent.z;
-    if (cx < 0 || cx >= M) continue;
-    const float2* cn = u.cn + (size_t)ent.x * MM;
+  // eight positions per round: every load of the round is in flight before the sums, which run in
+  // list order (a tile in the middle of a dense scan holds hundreds of positions)
+  constexpr int kU = 8;
+  for (int base = s0 + split; base < s1; base += kU * kObjSplit) {
+    float2 cv[kU][4];
+    float dv[kU][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int cy = Y0 + 8 * i - ent.y;
-      if (cy >= 0 && cy < M) {
-        acc[i] = cadd(acc[i], cn[(size_t)cy * M + cx]);
-        den[i] += u.p2[cy * M + cx];
+    for (int r = 0; r < kU; ++r) {
+      const int idx = base + r * kObjSplit;
+      const int4 ent = idx < s1 ? u.tile_pos[idx] : make_int4(0, 0, -(1 << 20), 0);  // (n, row, col)
+      const int cx = X - ent.z;
+      const bool inx = cx >= 0 && cx < M;
+      const float2* cn = u.cn + (size_t)ent.x * MM;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int cy = Y0 + 8 * i - ent.y;
+        const bool in = inx && cy >= 0 && cy < M;
+        cv[r][i] = in ? cn[(size_t)cy * M + cx] : make_float2(0.f, 0.f);
+        dv[r][i] = in ? u.p2[cy * M + cx] : 0.f;
       }
     }
+#pragma unroll
+    for (int r = 0; r < kU; ++r)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i] = cadd(acc[i], cv[r][i]);
+        den[i] += dv[r][i];
+      }
   }
-  if (X >= u.obj_w) return;
-  const size_t plane = (size_t)u.obj_h * u.obj_w;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int Y = Y0 + 8 * i;
-    if (Y < u.obj_h) {
-      u.no_part[split * plane + (size_t)Y * u.obj_w + X] = acc[i];
-      u.do_part[split * plane + (size_t)Y * u.obj_w + X] = den[i];
-    }
+    s_acc[(threadIdx.y + 8 * i) * kObjTile + threadIdx.x] = acc[i];
+    s_den[(threadIdx.y + 8 * i) * kObjTile + threadIdx.x] = den[i];
   }
-}
-
-// sum the kObjSplit partials in order (into split 0) and take the tile maximum of D_O
-__global__ void __launch_bounds__(256) k_obj_finalize(const UpdateArgs u) {
-  const int tile = blockIdx.y * u.tiles_x + blockIdx.x;
-  const int X = blockIdx.x * kObjTile + threadIdx.x;
-  const int Y0 = blockIdx.y * kObjTile + threadIdx.y;
-  const size_t plane = (size_t)u.obj_h * u.obj_w;
-  __shared__ float smax[256];
+  cluster_sync_all();  // every rank's partial tile is complete
   float m = 0.f;
-  if (X < u.obj_w) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int Y = Y0 + 8 * i;
-      if (Y >= u.obj_h) break;
-      const size_t q = (size_t)Y * u.obj_w + X;
-      float2 a = u.no_part[q];
-      float d = u.do_part[q];
-      for (int s = 1; s < kObjSplit; ++s) {
-        a = cadd(a, u.no_part[s * plane + q]);
-        d += u.do_part[s * plane + q];
-      }
+  if (lt < RPR) {
+    const int lp = (int)rank * RPR + lt;
+    const uint32_t oa = smem_addr(&s_acc[lp]), od = smem_addr(&s_den[lp]);
+    float2 a = ld_cluster_f2(map_rank(oa, 0));
+    float d = ld_cluster_f32(map_rank(od, 0));
+    for (int q = 1; q < kObjSplit; ++q) {
+      a = cadd(a, ld_cluster_f2(map_rank(oa, (unsigned)q)));
+      d += ld_cluster_f32(map_rank(od, (unsigned)q));
+    }
+    const int Y = ty0 + lp / kObjTile, Xp = tx0 + lp % kObjTile;
+    if (Y < u.obj_h && Xp < u.obj_w) {
+      const size_t q = (size_t)Y * u.obj_w + Xp;
       u.no_part[q] = a;
       u.do_part[q] = d;
-      m = fmaxf(m, d);
+      m = d;  // D_O >= 0
     }
+    const int wm = __reduce_max_sync(0xffffffffu, __float_as_int(m));  // non-negative floats order as ints
+    if ((lt & 31) == 0) st_cluster_f32(map_rank(smem_addr(&s_max[rank * (RPR / 32) + lt / 32]), 0), __int_as_float(wm));
   }
-  const int lt = threadIdx.y * 32 + threadIdx.x;
-  smax[lt] = m;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (lt < w) smax[lt] = fmaxf(smax[lt], smax[lt + w]);
-    __syncthreads();
+  cluster_sync_all();  // remote reads and the maxima are done
+  if (rank == 0 && lt == 0) {
+    float mm = 0.f;
+    for (int i = 0; i < kObjSplit * (RPR / 32); ++i) mm = fmaxf(mm, s_max[i]);
+    u.blk_max_o[tile] = mm;
   }
-  if (lt == 0) u.blk_max_o[tile] = smax[0];
 }
 
 __device__ float block_max_of(const float* vals, int n) {
@@ -331,8 +346,21 @@ cudaError_t launch_update_object(const UpdateArgs& u, cudaStream_t s) {
     k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
   }
   const dim3 tb(32, 8);
-  k_obj_gather<<<dim3(u.tiles_x, u.tiles_y, kObjSplit), tb, 0, s>>>(u);
-  k_obj_finalize<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)u.tiles_x, (unsigned)u.tiles_y, kObjSplit);
+    cfg.blockDim = tb;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = kObjSplit;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_obj_gather, u);
+    if (e != cudaSuccess) return e;
+  }
   k_obj_apply<<<dim3(u.tiles_x, u.tiles_y), tb, 0, s>>>(u);
   return cudaGetLastError();
 }
