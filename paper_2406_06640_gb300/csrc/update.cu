@@ -176,7 +176,7 @@ __global__ void k_dm_probe_partials(const UpdateArgs u) {
 // split + kObjSplit, ... of the tile's list; the partial tiles meet in distributed shared memory,
 // where rank r adds up rows 4r .. 4r + 3 over the ranks in order and writes N_O, D_O; rank 0 also
 // takes the tile maximum of D_O.
-__global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
+__global__ void __launch_bounds__(256, 3) k_obj_gather(const UpdateArgs u) {
   constexpr int TT = kObjTile * kObjTile, RPR = TT / kObjSplit;  // pixels finished per rank
   static_assert(RPR <= 256 && RPR % 32 == 0 && kObjTile == 32, "tile split");
   __shared__ float2 s_acc[TT];
@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(256) k_obj_gather(const UpdateArgs u) {
     den[i] = 0.f;
   }
   const int s0 = u.tile_start[tile], s1 = u.tile_start[tile + 1];
-  // eight positions per round: every load of the round is in flight before the sums, which run in
-  // list order (a tile in the middle of a dense scan holds hundreds of positions)
-  constexpr int kU = 8;
+  // four positions per round: every load of the round is in flight before the sums, which run in
+  // list order (a tile in the middle of a dense scan holds hundreds of positions); three blocks
+  // per SM
+  constexpr int kU = 4;
   for (int base = s0 + split; base < s1; base += kU * kObjSplit) {
     float2 cv[kU][4];
     float dv[kU][4];
@@ -305,9 +306,20 @@ __global__ void __launch_bounds__(256) k_obj_apply(const UpdateArgs u) {
 // grid (ceil(M^2 / 256), K): apply the probe step; block (0, 0) also finishes the FP64 error
 __global__ void k_probe_apply(const UpdateArgs u) {
   const float maxd = block_max_of(u.blk_max_p, u.probe_blocks);
+  double e = 0.0;
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    // error numerator: strided partial sums, then a fixed tree (every load in flight at once)
+    __shared__ double s_e[256];
+    for (int s = threadIdx.x; s < u.nerr; s += 256) e += u.errpart[s];
+    s_e[threadIdx.x] = e;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) s_e[threadIdx.x] += s_e[threadIdx.x + w];
+      __syncthreads();
+    }
+    e = s_e[0];
+  }
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-    double e = 0.0;
-    for (int s = 0; s < u.nerr; ++s) e += u.errpart[s];
     if (u.err_mode != 0) e += *u.err_acc;
     if (u.err_mode == 1) {
       *u.err_acc = e;
