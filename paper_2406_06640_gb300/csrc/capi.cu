@@ -474,8 +474,8 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_bmp, (size_t)pb), "alloc probe maxima");
   PT_CUDA(pl->alloc(&d_cbar, (size_t)N), "alloc cbar");
   long long *d_lna, *d_phi, *d_cbar_q;
-  PT_CUDA(pl->alloc(&d_lna, plane), "alloc constraint maps");
-  PT_CUDA(pl->alloc(&d_phi, plane), "alloc constraint maps");
+  PT_CUDA(pl->alloc(&d_lna, (size_t)p.obj_h * (p.obj_w + 1)), "alloc constraint maps");
+  PT_CUDA(pl->alloc(&d_phi, (size_t)p.obj_h * (p.obj_w + 1)), "alloc constraint maps");
   PT_CUDA(pl->alloc(&d_cbar_q, (size_t)N), "alloc cbar");
   // the constraint visits every box of a tile: the whole scan's lists (the batch lists when
   // there is one batch)

@@ -156,8 +156,8 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
     ua.run_counter = cv.take<unsigned long long>(1);
     ca.cbar = cv.take<float>((size_t)N);
     ca.cbar_q = cv.take<long long>((size_t)N);
-    ca.map_lna = cv.take<long long>(plane);
-    ca.map_phi = cv.take<long long>(plane);
+    ca.map_lna = cv.take<long long>((size_t)p->obj_h * (p->obj_w + 1));
+    ca.map_phi = cv.take<long long>((size_t)p->obj_h * (p->obj_w + 1));
   };
   FusedArgs fa{};
   UpdateArgs ua{};

@@ -13,9 +13,10 @@
 //
 // All box sums are exact: values are held in 32.32 fixed point (int64) and
 // summed with integer arithmetic, so the results do not depend on order.
-//   (1) |ln a| and |phi| of every object pixel, in 32.32 fixed point;
-//   (2) one block per box sums both maps over the box with integer adds -> C_n, and C_n in
-//       fixed point;
+//   (1) |ln a| and |phi| of every object pixel in 32.32 fixed point, as prefix sums along the
+//       object rows;
+//   (2) one warp per box: each box sum is M differences of two row prefix sums -> C_n, and C_n
+//       in fixed point;
 //   (3) one block per 32 x 32 object tile: the boxes of the tile's position list, clipped to the
 //       tile, add their fixed-point C_n at the corners of a difference array in shared memory;
 //       its prefix sums give every pixel the sum over the boxes that contain it and their
@@ -31,42 +32,89 @@ namespace ptycho {
 
 constexpr double kFix = 4294967296.0;  // 2^32
 
-// |ln a| and |phi| of every object pixel in 32.32 fixed point (obj_h x obj_w each)
-__global__ void __launch_bounds__(256) k_cc_maps(const ConstraintArgs c) {
-  const size_t n = (size_t)c.obj_h * c.obj_w;
-  for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256) {
-    const float2 o = c.O[i];
-    c.map_lna[i] = llrint((double)fabsf(logf(fmaxf(sqrtf(cabs2(o)), 1e-6f))) * kFix);
-    c.map_phi[i] = llrint((double)fabsf(atan2f(o.y, o.x)) * kFix);
+// Row prefix sums of |ln a| and |phi| in 32.32 fixed point: P(y, x) = sum over x' < x of the value at
+// (y, x'), obj_h x (obj_w + 1) each. One warp per object row, 4 consecutive pixels per lane (128
+// per step, warp scan of the lane totals with a carry), 8 rows per block. v * 2^32 is exact in
+// FP32, so llrintf of it is the nearest 32.32 value of v.
+__device__ __forceinline__ void cc_values(float2 o, long long& l, long long& p) {
+  const float f = 4294967296.0f;
+  l = llrintf(fabsf(logf(fmaxf(sqrtf(cabs2(o)), 1e-6f))) * f);
+  p = llrintf(fabsf(atan2f(o.y, o.x)) * f);
+}
+
+__global__ void __launch_bounds__(256) k_cc_rows(const ConstraintArgs c) {
+  const int lane = threadIdx.x & 31;
+  const int y = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (y >= c.obj_h) return;
+  const int W1 = c.obj_w + 1;
+  long long* pl = c.map_lna + (size_t)y * W1;
+  long long* pp = c.map_phi + (size_t)y * W1;
+  const float2* Oy = c.O + (size_t)y * c.obj_w;
+  if (lane == 0) {
+    pl[0] = 0;
+    pp[0] = 0;
+  }
+  long long cl = 0, cp = 0;  // carries: the sums up to the current step
+  for (int x0 = 0; x0 < c.obj_w; x0 += 128) {
+    long long vl[4], vp[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int x = x0 + 4 * lane + j;
+      vl[j] = 0;
+      vp[j] = 0;
+      if (x < c.obj_w) cc_values(Oy[x], vl[j], vp[j]);
+    }
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+      vl[j] += vl[j - 1];
+      vp[j] += vp[j - 1];
+    }
+    long long tl = vl[3], tp = vp[3];  // inclusive scan of the lane totals
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long ul = __shfl_up_sync(0xffffffffu, tl, d);
+      const long long up = __shfl_up_sync(0xffffffffu, tp, d);
+      if (lane >= d) {
+        tl += ul;
+        tp += up;
+      }
+    }
+    const long long el = cl + tl - vl[3], ep = cp + tp - vp[3];  // sums before this lane's pixels
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int x = x0 + 4 * lane + j;
+      if (x < c.obj_w) {
+        pl[x + 1] = el + vl[j];
+        pp[x + 1] = ep + vp[j];
+      }
+    }
+    cl += __shfl_sync(0xffffffffu, tl, 31);
+    cp += __shfl_sync(0xffffffffu, tp, 31);
   }
 }
 
-// one block of 256 threads per box: the two box sums (exact), C_n clamped, C_n in fixed point
+// one warp per box: the two box sums (exact) from M row differences each, C_n clamped, C_n in fixed
+// point
 __global__ void __launch_bounds__(256) k_cc_cbar(const ConstraintArgs c) {
-  __shared__ long long s1[256], s2[256];
-  const int n = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (n >= c.N) return;
   const int2 pn = c.pos[n];
-  const int M = c.M;
-  const int lg = __ffs(M) - 1;  // M is a power of two
+  const int M = c.M, W1 = c.obj_w + 1;
   long long a = 0, b = 0;
-  for (int p = threadIdx.x; p < M * M; p += 256) {
-    const size_t q = (size_t)(pn.x + (p >> lg)) * c.obj_w + pn.y + (p & (M - 1));
-    a += c.map_lna[q];
-    b += c.map_phi[q];
+  for (int i = lane; i < M; i += 32) {
+    const size_t r = (size_t)(pn.x + i) * W1;
+    a += c.map_lna[r + pn.y + M] - c.map_lna[r + pn.y];
+    b += c.map_phi[r + pn.y + M] - c.map_phi[r + pn.y];
   }
-  s1[threadIdx.x] = a;
-  s2[threadIdx.x] = b;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      s1[threadIdx.x] += s1[threadIdx.x + w];
-      s2[threadIdx.x] += s2[threadIdx.x + w];
-    }
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
   }
-  if (threadIdx.x == 0) {
-    const double sl = (double)s1[0] / kFix;
-    const double sp = (double)s2[0] / kFix;
+  if (lane == 0) {
+    const double sl = (double)a / kFix;
+    const double sp = (double)b / kFix;
     const double r = sl / fmax(sp, 1e-30);
     const float cb = (float)fmin(fmax(r, (double)c.cbar_min), (double)c.cbar_max);
     c.cbar[n] = cb;
@@ -179,10 +227,8 @@ __global__ void __launch_bounds__(256) k_cc_apply(const ConstraintArgs c) {
 
 cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s) {
   if (c.N == 0) return cudaSuccess;
-  const size_t n = (size_t)c.obj_h * c.obj_w;
-  const int nb = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  k_cc_maps<<<nb, 256, 0, s>>>(c);
-  k_cc_cbar<<<c.N, 256, 0, s>>>(c);
+  k_cc_rows<<<(c.obj_h + 7) / 8, 256, 0, s>>>(c);
+  k_cc_cbar<<<(c.N + 7) / 8, 256, 0, s>>>(c);
   k_cc_apply<<<dim3(c.tiles_x, c.tiles_y), dim3(32, 8), 0, s>>>(c);
   return cudaGetLastError();
 }

@@ -161,7 +161,7 @@ cudaError_t launch_mono(const MonoArgs& a, cudaStream_t s);
 struct ConstraintArgs {
   float2* O; const int2* pos; int N, M, obj_h, obj_w;
   float* cbar; float alpha1, alpha2, cbar_min, cbar_max;
-  long long* map_lna; long long* map_phi;  // |ln a| and |phi| per object pixel, 32.32 fixed point
+  long long* map_lna; long long* map_phi;  // row prefix sums of |ln a|, |phi|: obj_h x (obj_w + 1), 32.32
   long long* cbar_q;                       // C_n in 32.32 fixed point (N)
   const int* tile_start;  // (tiles_y * tiles_x + 1) CSR offsets into tile_pos, kObjTile tiles
   const int4* tile_pos;   // per tile, (n, row, col, 0) of every position whose box overlaps it
