@@ -31,7 +31,7 @@ struct MonoShape {
   static constexpr size_t P_BYTES = (size_t)LDP * LDP * 4;
   static constexpr size_t R_BYTES = (size_t)M * M * 4;
   static constexpr size_t TAB_BYTES = (size_t)M * kTapsT * 8 + (size_t)M * 4;  // taps, then counts
-  static constexpr size_t RED_BYTES = (size_t)(TPB / 32) * 2 * 8;
+  static constexpr size_t RED_BYTES = (size_t)(TPB / 32 + 1) * 2 * 8;
   static constexpr size_t SPEC_BYTES = (size_t)3 * kMonoMaxJ * 4;
   static constexpr size_t BYTES = P_BYTES + 2 * R_BYTES + TAB_BYTES + RED_BYTES + SPEC_BYTES;
   static_assert(M * M % TPB == 0 && TPB % M == 0, "pixel ownership");
@@ -51,9 +51,11 @@ __device__ __forceinline__ void interp_at(int i, float c, float inv_a, int M, in
   f = t - fl;
 }
 
-// FP64 sums of two per-thread values over the CTA, in a fixed order; every thread gets both
+// FP64 sums of two per-thread values over the CTA, in a fixed order; every thread gets both. The
+// warps' sums are finished by warp 0 alone (shuffle tree) and broadcast through shared memory.
 template <int TPB>
 __device__ __forceinline__ void block_sum2(double a, double b, double* red, double& oa, double& ob) {
+  constexpr int NW = TPB / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -66,13 +68,21 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* red, doub
     red[2 * warp + 1] = b;
   }
   __syncthreads();
-  double sa = 0.0, sb = 0.0;
-  for (int w = 0; w < TPB / 32; ++w) {
-    sa += red[2 * w];
-    sb += red[2 * w + 1];
+  if (warp == 0) {
+    double x = lane < NW ? red[2 * lane] : 0.0, y = lane < NW ? red[2 * lane + 1] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) {
+      red[2 * NW] = x;
+      red[2 * NW + 1] = y;
+    }
   }
-  oa = sa;
-  ob = sb;
+  __syncthreads();
+  oa = red[2 * NW];
+  ob = red[2 * NW + 1];
 }
 
 template <int M>

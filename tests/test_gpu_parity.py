@@ -238,6 +238,14 @@ def test_config1_full_size_two_iterations():
     check(p, p.params, 2)
 
 
+@pytest.mark.parametrize("engine", ["pie", "dm"])
+def test_config1_full_size_bench_configuration(engine):
+    """Configuration 1 exactly as bench.py times it (the complex constraint in every iteration), for
+    the simultaneous engine and pc-DM, element by element against the oracle over two iterations."""
+    p = make_problem(1)
+    check(p, dict(p.params, windows=[(1, 1 << 30)], engine=engine), 2)
+
+
 @pytest.mark.parametrize("M,geometry", [(64, "far"), (256, "near")])
 def test_deterministic_and_resumable(M, geometry):
     """Bitwise-equal reruns (no atomics, fixed reduction orders, no cross-block races) and resume."""
