@@ -29,7 +29,8 @@ struct MonoShape {
   static constexpr int PPT = M * M / TPB;  // pixels per thread
   static constexpr int LDP = M + 2;        // padded row of p
   static constexpr size_t P_BYTES = (size_t)LDP * LDP * 4;
-  static constexpr size_t R_BYTES = (size_t)M * M * 4;
+  static constexpr int LDR = M + 1;         // padded row of r and T (conflict-free column walks)
+  static constexpr size_t R_BYTES = (size_t)M * LDR * 4;
   static constexpr size_t TAB_BYTES = (size_t)M * kTapsT * 8 + (size_t)M * 4;  // taps, then counts
   static constexpr size_t RED_BYTES = (size_t)(TPB / 32 + 1) * 2 * 8;
   static constexpr size_t SPEC_BYTES = (size_t)3 * kMonoMaxJ * 4;
@@ -88,11 +89,11 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* red, doub
 template <int M>
 __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoArgs a) {
   using SH = MonoShape<M>;
-  constexpr int TPB = SH::TPB, PPT = SH::PPT, LDP = SH::LDP, RSTEP = TPB / M;
+  constexpr int TPB = SH::TPB, PPT = SH::PPT, LDP = SH::LDP, LDR = SH::LDR, RSTEP = TPB / M;
   extern __shared__ __align__(16) unsigned char smem[];
   float* Pp = reinterpret_cast<float*>(smem);                        // (M + 2)^2, zero border
-  float* R = reinterpret_cast<float*>(smem + SH::P_BYTES);           // M^2
-  float* T = reinterpret_cast<float*>(smem + SH::P_BYTES + SH::R_BYTES);  // M^2, r S_j
+  float* R = reinterpret_cast<float*>(smem + SH::P_BYTES);               // M x LDR
+  float* T = reinterpret_cast<float*>(smem + SH::P_BYTES + SH::R_BYTES);  // M x LDR, r S_j
   // column u of S_j: its non-zero taps (weight, source index as float bits) in increasing source
   // order, zero-filled to kTapsT, and their count
   float2* tab = reinterpret_cast<float2*>(smem + SH::P_BYTES + 2 * SH::R_BYTES);
@@ -141,8 +142,27 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
         if (l == 0) tab_n[u] = cnt;
       }
       __syncthreads();
-      // T(y, v) = sum_x S_j[x, v] R(y, x) for the own (y, v); zero-filled taps add exact zeros
-      {
+      // T(y, v) = sum_x S_j[x, v] R(y, x); zero-filled taps add exact zeros
+      if constexpr (M >= 32) {
+        // a warp walks 32 consecutive rows of one column: the column's taps are a broadcast and the
+        // padded rows put the 32 loads (and the store) in 32 different banks
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll 4
+        for (int m = 0; m < PPT; ++m) {
+          const int unit = warp * PPT + m;
+          const int v = unit % M, y = (unit / M) * 32 + lane;
+          const int nt = tab_n[v];
+          float s = 0.f;
+#pragma unroll
+          for (int h = 0; h < kTapsT / 2; ++h)
+            if (2 * h < nt) {
+              const float4 e = tab4[v * (kTapsT / 2) + h];
+              s = fmaf(e.x, R[y * LDR + __float_as_int(e.y)], s);
+              s = fmaf(e.z, R[y * LDR + __float_as_int(e.w)], s);
+            }
+          T[y * LDR + v] = s;
+        }
+      } else {
         int ci[kTapsT];
         float cw[kTapsT];
 #pragma unroll
@@ -160,8 +180,8 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
           float s = 0.f;
 #pragma unroll
           for (int l = 0; l < kTapsT; ++l)
-            if (l < nt) s = fmaf(cw[l], R[y * M + ci[l]], s);
-          T[y * M + col] = s;
+            if (l < nt) s = fmaf(cw[l], R[y * LDR + ci[l]], s);
+          T[y * LDR + col] = s;
         }
       }
       __syncthreads();
@@ -176,8 +196,8 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
         for (int h = 0; h < kTapsT / 2; ++h)
           if (h < nh) {
             const float4 e = tab4[u * (kTapsT / 2) + h];
-            s = fmaf(e.x, T[__float_as_int(e.y) * M + col], s);
-            s = fmaf(e.z, T[__float_as_int(e.w) * M + col], s);
+            s = fmaf(e.x, T[__float_as_int(e.y) * LDR + col], s);
+            s = fmaf(e.z, T[__float_as_int(e.w) * LDR + col], s);
           }
         acc[m] = fmaf(wj, s, acc[m]);
       }
@@ -219,9 +239,9 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
   float rr = 0.f;  // per-thread partial sums in FP32 (PPT terms), CTA sums in FP64
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
-    const int q = (row0 + m * RSTEP) * M + col;
-    const float v = bn[q];
-    R[q] = v;
+    const int y = row0 + m * RSTEP;
+    const float v = bn[y * M + col];
+    R[y * LDR + col] = v;
     rr = fmaf(v, v, rr);
     xk[m] = 0.f;
   }
@@ -263,8 +283,8 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
     for (int m = 0; m < PPT; ++m) {
       const int y = row0 + m * RSTEP;
       xk[m] = fmaf(alpha, Pp[(y + 1) * LDP + col + 1], xk[m]);
-      const float r = fmaf(-alpha, acc[m], R[y * M + col]);
-      R[y * M + col] = r;
+      const float r = fmaf(-alpha, acc[m], R[y * LDR + col]);
+      R[y * LDR + col] = r;
       rr = fmaf(r, r, rr);
     }
     __syncthreads();
