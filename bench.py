@@ -523,7 +523,8 @@ def run_ours_batch(args):
                 "cpu_baseline": None,
                 "e2e": {"value": ws * units * e2e_steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes + 8 * len(descr)},
-                "gpu_launches": None, "clocks": clocks, "nrmse_mean_last": float(np.mean(E))}
+                "gpu_launches": args.steps * batch.launches_per_iteration(), "clocks": clocks,
+                "nrmse_mean_last": float(np.mean(E))}
         print(json.dumps(line), flush=True)
     batch.close()
     return 0

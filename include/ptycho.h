@@ -195,6 +195,11 @@ int32_t ptycho_staged_chunk(ptycho_plan_t plan);
  * number of classes. */
 ptycho_status ptycho_batch_classes(ptycho_plan_t plan, int32_t max_classes, int32_t* out, int32_t* count);
 
+/* Kernel launches of one iteration of a batch plan: the kernel nodes of the CUDA graph that the last
+ * ptycho_iterate_batch replayed per iteration (0 before the first call). kernels: host. EINVAL if
+ * plan is not a batch plan or kernels is NULL. */
+ptycho_status ptycho_batch_launches(ptycho_plan_t plan, int32_t* kernels);
+
 /* Tensor-core GEMM used by the warm-start network (the paper has no learned
  * component; this is the contraction under its 3x3 convolutions):
  *   D[M x N] = A[M x K] . B[N x K]^T      (accumulate != 0: D += A . B^T)

@@ -24,7 +24,7 @@ ENGINE_PIE, ENGINE_DM = 0, 1
 EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_history", "ptycho_destroy",
             "ptycho_plan_batch", "ptycho_iterate_batch", "ptycho_error_batch",
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
-            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_permutation", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
+            "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_batch_launches", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_permutation", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
             "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
             "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart", "ptycho_monochromatise")
 
@@ -127,6 +127,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_batch_classes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32)]
     lib.ptycho_batch_classes.restype = st
+    lib.ptycho_batch_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.ptycho_batch_launches.restype = st
     lib.ptycho_last_error.argtypes = []
     lib.ptycho_last_error.restype = ctypes.c_char_p
     lib.ptycho_version.argtypes = []
@@ -293,6 +295,12 @@ class BatchPlan:
         _check(load().ptycho_batch_classes(self._h, n.value, buf, ctypes.byref(n)))
         keys = ("M", "K", "near", "kh", "members", "chunk_len", "chunks", "slots")
         return [dict(zip(keys, buf[8 * c:8 * c + 8])) for c in range(n.value)]
+
+    def launches_per_iteration(self) -> int:
+        """Kernel nodes of the graph the last iterate replayed per iteration."""
+        n = ctypes.c_int32()
+        _check(load().ptycho_batch_launches(self._h, ctypes.byref(n)))
+        return n.value
 
     def errors(self) -> list:
         out = (ctypes.c_double * self.B)()

@@ -123,6 +123,8 @@ struct ptycho_plan_s {
   std::vector<cudaEvent_t> branch_ev;
   std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
   std::vector<std::vector<FusedArgs*>> graph_descs;  // per graph: each class's device argument array
+  std::vector<int> graph_kernels;                     // per graph: kernel nodes (launches per replay)
+  int last_kernels = 0;                               // kernel nodes of the last replayed graph
   cudaStream_t origin = nullptr;          // capture / replay stream of a batch plan
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int chunk = 0;
@@ -1022,8 +1024,12 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
       key.push_back((uintptr_t)probes[b]);
     }
     cudaGraphExec_t exec = nullptr;
-    for (auto& g : pl->graphs)
-      if (g.first == key) exec = g.second;
+    int kernels = 0;
+    for (size_t gi = 0; gi < pl->graphs.size(); ++gi)
+      if (pl->graphs[gi].first == key) {
+        exec = pl->graphs[gi].second;
+        kernels = pl->graph_kernels[gi];
+      }
     if (!exec) {
       // each class's per-problem arguments with this call's object / probe pointers (kept with the graph)
       std::vector<FusedArgs*> descs;
@@ -1080,12 +1086,29 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
         return cuda_fail(ce, "capture of the batch iteration");
       }
       PT_CUDA(ee, "end capture");
+      {
+        size_t nn = 0;
+        cudaError_t ge = cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (ge == cudaSuccess && nn) ge = cudaGraphGetNodes(graph, nodes.data(), &nn);
+        for (size_t q = 0; q < nn && ge == cudaSuccess; ++q) {
+          cudaGraphNodeType ty;
+          ge = cudaGraphNodeGetType(nodes[q], &ty);
+          if (ge == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+        }
+        if (ge != cudaSuccess) {
+          cudaGraphDestroy(graph);
+          return cuda_fail(ge, "count the batch graph's kernels");
+        }
+      }
       const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       PT_CUDA(ie, "instantiate the batch graph");
       pl->graphs.emplace_back(key, exec);
       pl->graph_descs.push_back(descs);
+      pl->graph_kernels.push_back(kernels);
     }
+    pl->last_kernels = kernels;
     PT_CUDA(cudaEventRecord(pl->ev_in, pl->stream), "event");
     PT_CUDA(cudaStreamWaitEvent(pl->origin, pl->ev_in, 0), "wait");
     PT_CUDA(cudaGraphLaunch(exec, pl->origin), "graph launch");
@@ -1116,6 +1139,12 @@ ptycho_status ptycho_set_staged_chunk(int32_t chunk) {
 }
 
 int32_t ptycho_staged_chunk(ptycho_plan_t pl) { return (pl && pl->big) ? pl->chunk : 0; }
+
+ptycho_status ptycho_batch_launches(ptycho_plan_t pl, int32_t* kernels) {
+  if (!pl || pl->members.empty() || !kernels) return fail(PTYCHO_EINVAL, "not a batch plan or bad output");
+  *kernels = pl->last_kernels;
+  return PTYCHO_OK;
+}
 
 ptycho_status ptycho_batch_classes(ptycho_plan_t pl, int32_t max_classes, int32_t* out, int32_t* count) {
   if (!pl || pl->members.empty() || !count || max_classes < 0 || (max_classes > 0 && !out))
@@ -1221,9 +1250,11 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
     const int chunks = (pl->p.N + pl->chunk - 1) / pl->chunk;
     fft = chunks * (pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5);
   }
-  if (pl->mb > 0) fft = pl->nb * 6 - 5;  // per batch: the fused kernel and the 5 update kernels
+  if (pl->mb > 0) fft = pl->nb * 5 - 4;  // per batch: the fused kernel and the 4 update kernels
   if (pl->d_psi) fft += 2;                // pc-DM probe partials and their gather (probe step on)
-  return fft + 5 + (in_window ? 3 : 0);  // constraint: maps, box sums, apply
+  // update: probe gather, object gather (one clustered launch), object step, probe step;
+  // constraint: row prefix sums, box sums, tile apply
+  return fft + 4 + (in_window ? 3 : 0);
 }
 
 ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32_t t, int32_t* out) {

@@ -104,6 +104,10 @@ class ReconstructionBatch:
         """The work-queue classes of this batch (shape, members, tuned chunk length, ...)."""
         return self._plan.classes()
 
+    def launches_per_iteration(self) -> int:
+        """Kernel launches of one iteration (kernel nodes of the last replayed graph)."""
+        return self._plan.launches_per_iteration()
+
     def close(self):
         self._plan.close()
 

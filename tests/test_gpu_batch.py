@@ -109,6 +109,24 @@ def test_work_queue_shares_chunks_across_problems_and_is_deterministic():
         assert rel(O1[b], Oo) < 1e-4 and rel(P1[b], Po) < 1e-4 and abs(E1[b] - Eo[-1]) / Eo[-1] < 1e-4, b
 
 
+def test_batch_reports_its_kernel_launches():
+    """One queued launch for the shape class plus the four update kernels of every member (no
+    constraint window): the kernel nodes of the replayed graph."""
+    from paper_2406_06640_gb300.engine import ReconstructionBatch
+
+    dev = torch.device("cuda:0")
+    probs = []
+    for side in (2, 3, 4):
+        p = make_problem(0, scan_side=side, obj_side=64 + 10 * side + 16, M=64, K=2, sigma=1.0)
+        probs.append((p, dict(p.params, windows=[])))
+    tens = [_tensors(dev, prob) for prob, _ in probs]
+    batch = ReconstructionBatch([(prm, t[0], prob.positions) for (prob, prm), t in zip(probs, tens)])
+    assert batch.launches_per_iteration() == 0
+    batch.iterate([t[1] for t in tens], [t[2] for t in tens], 2)
+    assert batch.launches_per_iteration() == 1 + 4 * len(probs)
+    batch.close()
+
+
 def test_batch_rejects_single_plan_calls():
     from paper_2406_06640_gb300 import PtychoError
     from paper_2406_06640_gb300.engine import ReconstructionBatch
