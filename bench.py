@@ -94,6 +94,10 @@ WORKLOADS = {
                          "spectrum: 32 lines over a factor 1.75 (400-700 nm about 400 nm), Gaussian weights; the "
                          "patterns of far128x4 stand in for white-light data (the cost does not depend on b)",
                       dict(mono=(MONO_WHITE32, MONO_WHITE32_W, 25))),
+    "mono256-white": (2, "numerical monochromatisation (CGLS, k=25) of 256 patterns of 256^2 with the 32-line "
+                         "white-light spectrum (one cluster of four CTAs per pattern); the patterns of near256x8 "
+                         "stand in for white-light data (the cost does not depend on b)",
+                      dict(mono=(MONO_WHITE32, MONO_WHITE32_W, 25))),
     "batch64": (3, "64 independent reconstructions of uneven sizes (probe 64-256, 100-1600 positions, K 1-4, "
                    "far/near 50/50, sigma 0.5-3), one CUDA graph launch per iteration"),
     "warmstart": (4, "time to intensity NRMSE <= 0.05 against the noise-free patterns: flat start with the true "
@@ -419,7 +423,8 @@ def run_ours_mono(args):
                            "l2": "flushed before each timed step (256 MiB write)",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single GPU"},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": traffic, "kernel": f"k_mono_cgls<{M}>",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "k_mono_cgls_band (M=256, clusters of 4)" if M == 256 else f"k_mono_cgls<{M}>",
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FMA pipe, max clock)",
                              "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3},
                 "cpu_baseline": cpu,

@@ -345,7 +345,7 @@ ptycho_status ptycho_permutation(int32_t n, uint64_t seed, int32_t stream, int32
  * interpolation and zero outside the grid. For every pattern, x_n = k steps of CGLS on
  * min ||C x - b_n||_2 from x = 0: the least-squares solution over the Krylov subspace
  * span{C^T b, (C^T C) C^T b, ..., (C^T C)^(k-1) C^T b} (Eq. 13); k is the regularisation.
- *   M: 8, 16, 32, 64 or 128 (EUNSUPPORTED otherwise); J: 1..64 spectral samples;
+ *   M: 8, 16, 32, 64, 128 or 256 (EUNSUPPORTED otherwise); J: 1..64 spectral samples;
  *   scale: host, J values a_j in (0, 2.5]; weight: host, J finite values >= 0, not all zero;
  *   N >= 0 patterns; k >= 0 steps;
  *   b: device float32, N x M x M, row-major, detector-centred (DC at (M/2, M/2));

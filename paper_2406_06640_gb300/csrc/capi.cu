@@ -1268,8 +1268,8 @@ ptycho_status ptycho_monochromatise(int32_t M, int32_t J, const double* scale, c
                                     int32_t k, const float* b, float* x, double* resid, int32_t clamp,
                                     void* cuda_stream) {
   if (M <= 0 || N < 0 || k < 0 || J <= 0) return fail(PTYCHO_EINVAL, "need M > 0, J > 0, N >= 0, k >= 0");
-  if (M != 8 && M != 16 && M != 32 && M != 64 && M != 128)
-    return fail(PTYCHO_EUNSUPPORTED, "monochromatisation handles M = 8, 16, 32, 64, 128");
+  if (M != 8 && M != 16 && M != 32 && M != 64 && M != 128 && M != 256)
+    return fail(PTYCHO_EUNSUPPORTED, "monochromatisation handles M = 8, 16, 32, 64, 128, 256");
   if (J > kMonoMaxJ) return fail(PTYCHO_EUNSUPPORTED, "more than 64 spectral samples");
   if (!scale || !weight) return fail(PTYCHO_EINVAL, "scale and weight must be non-NULL");
   if (N > 0 && (!b || !x)) return fail(PTYCHO_EINVAL, "b and x must be non-NULL");

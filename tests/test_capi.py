@@ -128,7 +128,7 @@ def test_host_permutation_matches_the_oracle(n, seed, stream, t):
 
 
 @pytest.mark.parametrize("M,scales,weights,N,k,clamp,expect", [
-    (48, [1.0], [1.0], 1, 3, 0, 4), (256, [1.0], [1.0], 1, 3, 0, 4), (0, [1.0], [1.0], 1, 3, 0, 1),
+    (48, [1.0], [1.0], 1, 3, 0, 4), (512, [1.0], [1.0], 1, 3, 0, 4), (0, [1.0], [1.0], 1, 3, 0, 1),
     (64, [], [], 1, 3, 0, 1), (64, [1.0] * 65, [1.0] * 65, 1, 3, 0, 4), (64, [1.0], [1.0], 1, -1, 0, 1),
     (64, [1.0], [1.0], -1, 3, 0, 1), (64, [2.6], [1.0], 1, 3, 0, 1), (64, [0.0], [1.0], 1, 3, 0, 1),
     (64, [1.0], [float("nan")], 1, 3, 0, 1), (64, [1.0, 1.2], [0.0, 0.0], 1, 3, 0, 1),

@@ -76,6 +76,16 @@ def test_probe_sizes_and_scales_below_one(M):
     check(B, [0.8, 0.95, 1.0, 1.3, 2.5], [0.1, 0.3, 0.3, 0.2, 0.1], 5)
 
 
+@pytest.mark.parametrize("scales,weights,k", [([1.0, 1.05, 1.1], [0.5, 0.3, 0.2], 6),
+                                              ([0.8, 1.0, 1.4, 2.5], [0.2, 0.4, 0.3, 0.1], 4)])
+def test_m256_cluster_of_four_bands(scales, weights, k):
+    """256^2 patterns: one cluster of four CTAs per pattern (64-row bands, neighbours read across
+    bands, CTA sums combined in rank order); scales on both sides of 1 and the widest accepted."""
+    rng = np.random.default_rng(256)
+    B = rng.random((3, 256, 256)) * 50
+    check(B, scales, weights, k)
+
+
 def test_monochromatic_light_is_exact_and_clamp():
     rng = np.random.default_rng(3)
     B = rng.standard_normal((3, 32, 32)).astype(np.float32).astype(np.float64)
@@ -108,6 +118,8 @@ def test_empty_batch_and_invalid_arguments():
             monochromatise(b, scales, weights, 3)
     with pytest.raises(PtychoError):
         monochromatise(torch.zeros((1, 48, 48), dtype=torch.float32, device=dev), [1.0], [1.0], 3)
+    with pytest.raises(PtychoError):
+        monochromatise(torch.zeros((1, 512, 512), dtype=torch.float32, device=dev), [1.0], [1.0], 3)
 
 
 def test_full_size_sampled():
