@@ -102,7 +102,8 @@ typedef struct {
    * ptycho_permutation(batches, order_seed, 4, t); each batch takes one step of the rule above over
    * its own positions, from the object and probe the previous batch left. The complex constraint
    * (inside its windows) follows the last batch; E_t sums every position's error numerator at the
-   * state its batch saw. M <= 128 only; not available in batch plans or ptycho_iterate_static. */
+   * state its batch saw. Every M (M = 256 runs each batch through the staged passes); not available
+   * in batch plans or ptycho_iterate_static. */
   int32_t minibatch;
   uint64_t order_seed;
   /* Engine: PTYCHO_ENGINE_PIE (0, default) takes the steps above from dpsi = Pi_F(P o_n) - P o_n;
@@ -110,8 +111,11 @@ typedef struct {
    * plan keeps an exit wave psi_{n,k} per position and mode (N K M^2 complex, started at P_k o_n
    * when the plan first iterates), each position forms chi = 2 P_k o_n - psi_{n,k}, runs it through
    * the propagation and the pc modulus step, sets psi_{n,k} <- psi_{n,k} + Pi_F(chi) - P_k o_n,
-   * and O and P take the step of the chosen rule with dpsi = psi_{n,k} - P_k o_n (the overlap
-   * projection); E_t is evaluated on chi. M <= 128, without mini-batches, single plans only. */
+   * and the overlap projection alternates: O takes the step of the chosen rule with
+   * dpsi = psi_{n,k} - P_k o_n; inside a complex-constraint window the constraint acts on O next
+   * and every psi_{n,k} moves by P_k (o_n after - o_n before); then P takes its step from the new
+   * object, sum conj(o'_n) (psi_{n,k} - P_k o'_n) over sum |o'_n|^2. E_t is the pc model error
+   * of the estimate P_k o_n. M <= 128, without mini-batches, single plans only. */
   int32_t engine;
 } ptycho_params;
 
@@ -222,9 +226,9 @@ ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
 ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
 
 /* Kernel launches one iteration issues: the fused kernel (M <= 128) or 5 (far)
- * / 7 (near) staged passes per chunk of 16 positions (M = 256), 5 update
- * kernels, and 6 complex-constraint kernels when `in_window` is non-zero
- * (memsets not counted). */
+ * / 7 (near) staged passes per chunk of positions (M = 256), 4 update kernels
+ * (2 more for pc-DM), per batch for the mini-batch engine, and 3 complex-constraint
+ * kernels when `in_window` is non-zero (copies not counted). */
 int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
 
 /* Allocation-free one-shot run (this entry point has no counterpart in the paper).

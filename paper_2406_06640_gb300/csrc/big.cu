@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
   const int y = blockIdx.x * LROW + li;
   const int c = blockIdx.y;
   const int n = b.n0 + c;
-  const bool first = b.n0 == 0;
+  const bool first = b.n0 == b.n_first;
   const size_t MM = (size_t)BL * BL;
   const int2 pn = b.pos[n];
   const float2* On = b.O + (size_t)(pn.x + y) * b.obj_w + pn.y;

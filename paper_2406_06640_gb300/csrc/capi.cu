@@ -219,8 +219,6 @@ static ptycho_status validate(const ptycho_params* p) {
     return fail(PTYCHO_EINVAL, "engine must be PTYCHO_ENGINE_PIE or PTYCHO_ENGINE_DM");
   if (p->engine == PTYCHO_ENGINE_DM && (p->M > 128 || (p->minibatch > 0 && p->minibatch < p->N)))
     return fail(PTYCHO_EUNSUPPORTED, "pc-DM handles M <= 128 without mini-batches");
-  if (p->minibatch > 0 && p->minibatch < p->N && p->M > 128)
-    return fail(PTYCHO_EUNSUPPORTED, "the mini-batch engine handles M <= 128");
   if (p->step_rule != PTYCHO_STEP_NORMALISED && p->step_rule != PTYCHO_STEP_RPIE)
     return fail(PTYCHO_EINVAL, "step_rule must be PTYCHO_STEP_NORMALISED or PTYCHO_STEP_RPIE");
   if (p->step_rule == PTYCHO_STEP_RPIE &&
@@ -671,15 +669,7 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
   ca.O = static_cast<float2*>(object);
   const int ps = pl->prof_count % ptycho_plan_s::kProfSlots;
   if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], s), "profile event");
-  if (pl->big) {
-    BigArgs ba = pl->ba;
-    ba.O = static_cast<const float2*>(object);
-    ba.P = static_cast<const float2*>(probe);
-    for (int n0 = 0; n0 < pl->p.N; n0 += pl->chunk) {
-      ba.n0 = n0;
-      PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, pl->p.N - n0), s), "staged pass launch");
-    }
-  } else if (pl->mb > 0) {
+  if (pl->mb > 0) {
     // mini-batch engine: the batches in this iteration's order, each a fused launch over its own
     // positions followed by its update; the error accumulates over the batches
     const size_t MM = (size_t)pl->p.M * pl->p.M;
@@ -688,18 +678,33 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
     for (int j = 0; j < pl->nb; ++j) {
       const int b = visit[j];
       const int s0 = b * pl->mb, len = std::min(pl->mb, pl->p.N - s0);
-      FusedArgs fb = fa;
-      fb.I = fa.I + (size_t)s0 * MM;
-      fb.sqrtI = fa.sqrtI + (size_t)s0 * MM;
-      fb.pos = fa.pos + s0;
-      fb.N = len;
-      fb.cn = fa.cn + (size_t)s0 * MM;
-      const int slots = std::min(pl->slots, len);
-      PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
       UpdateArgs ub = ua;
       ub.tile_start = pl->d_starts + (size_t)b * (pl->tiles + 1);
-      ub.slots = slots;
-      ub.nerr = slots * pl->p.K;
+      if (pl->big) {
+        // staged passes over the batch's positions; the probe partials restart at its first chunk
+        BigArgs ba = pl->ba;
+        ba.O = static_cast<const float2*>(object);
+        ba.P = static_cast<const float2*>(probe);
+        ba.n_first = s0;
+        for (int n0 = s0; n0 < s0 + len; n0 += pl->chunk) {
+          ba.n0 = n0;
+          PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, s0 + len - n0), s), "staged pass launch");
+        }
+        ub.slots = std::min(pl->chunk, len);
+        ub.errpart = ua.errpart + (size_t)s0 * big_row_blocks();
+        ub.nerr = len * big_row_blocks();
+      } else {
+        FusedArgs fb = fa;
+        fb.I = fa.I + (size_t)s0 * MM;
+        fb.sqrtI = fa.sqrtI + (size_t)s0 * MM;
+        fb.pos = fa.pos + s0;
+        fb.N = len;
+        fb.cn = fa.cn + (size_t)s0 * MM;
+        const int slots = std::min(pl->slots, len);
+        PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
+        ub.slots = slots;
+        ub.nerr = slots * pl->p.K;
+      }
       ub.err_mode = j + 1 < pl->nb ? 1 : 2;
       ub.err_acc = pl->d_err_acc;
       PT_CUDA(launch_update(ub, s), "update launch");
@@ -710,6 +715,15 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
     }
     if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
     return PTYCHO_OK;
+  } else if (pl->big) {
+    BigArgs ba = pl->ba;
+    ba.O = static_cast<const float2*>(object);
+    ba.P = static_cast<const float2*>(probe);
+    ba.n_first = 0;
+    for (int n0 = 0; n0 < pl->p.N; n0 += pl->chunk) {
+      ba.n0 = n0;
+      PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, pl->p.N - n0), s), "staged pass launch");
+    }
   } else if (pl->d_psi) {
     fa.psi = pl->d_psi;
     fa.dm_init = pl->dm_fresh ? 1 : 0;
@@ -1245,12 +1259,16 @@ ptycho_status ptycho_profile_read(ptycho_plan_t pl, double* fused_ms, int32_t* l
 
 int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
   if (!pl) return 0;
+  const int passes = pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5;  // staged passes per chunk
   int fft = 1;
-  if (pl->big) {
-    const int chunks = (pl->p.N + pl->chunk - 1) / pl->chunk;
-    fft = chunks * (pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5);
+  if (pl->big) fft = (pl->p.N + pl->chunk - 1) / pl->chunk * passes;
+  if (pl->mb > 0) {  // per batch: its fused launch or staged passes, and the 4 update kernels
+    fft = -4;
+    for (int b = 0; b < pl->nb; ++b) {
+      const int len = std::min(pl->mb, pl->p.N - b * pl->mb);
+      fft += (pl->big ? (len + pl->chunk - 1) / pl->chunk * passes : 1) + 4;
+    }
   }
-  if (pl->mb > 0) fft = pl->nb * 5 - 4;  // per batch: the fused kernel and the 4 update kernels
   if (pl->d_psi) fft += 2;                // pc-DM probe partials and their gather (probe step on)
   // update: probe gather, object gather (one clustered launch), object step, probe step;
   // constraint: row prefix sums, box sums, tile apply

@@ -74,6 +74,7 @@ struct BigArgs {
   float2* W;          // C x K x M x M scratch
   float* R;           // C x M x M modulus ratios
   int n0;             // first position of the chunk
+  int n_first;        // first position of the current accumulation (its chunk restarts the partials)
   float2* cn;         // N x M x M contributions
   float2* pacc;       // C x K x M x M probe partials (slot = position within the chunk)
   float* dacc;        // C x M x M

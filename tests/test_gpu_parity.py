@@ -114,6 +114,14 @@ def test_minibatch_engine(B, step):
     check(p, dict(p.params, minibatch=B, order_seed=11, **step), 3)
 
 
+def test_minibatch_engine_m256_staged_passes():
+    """M = 256 runs each batch through the staged passes: 9 positions in batches of 4, 4 and 1 in a
+    Philox order (batches shorter than the staged chunk), two modes, near field, a window."""
+    p = make_problem(0, scan_side=3, obj_side=400, M=256, K=2, geometry="near", sigma=1.5)
+    check(p, dict(p.params, sigma1=1.5, sigma2=1.5, minibatch=4, order_seed=5, windows=[(2, 2)], alpha1=0.5,
+                  step_rule="rpie", rpie_alpha_obj=0.3, rpie_alpha_probe=0.3), 3)
+
+
 def test_minibatch_engine_near_field_modes_window():
     p = make_problem(0, scan_side=4, obj_side=128, M=64, K=2, geometry="near", sigma=2.0)
     check(p, dict(p.params, sigma1=2.0, sigma2=2.0, minibatch=5, order_seed=3, windows=[(2, 2)], alpha1=0.5,
