@@ -115,7 +115,8 @@ typedef struct {
    * dpsi = psi_{n,k} - P_k o_n; inside a complex-constraint window the constraint acts on O next
    * and every psi_{n,k} moves by P_k (o_n after - o_n before); then P takes its step from the new
    * object, sum conj(o'_n) (psi_{n,k} - P_k o'_n) over sum |o'_n|^2. E_t is the pc model error
-   * of the estimate P_k o_n. M <= 128, without mini-batches, single plans only. */
+   * of the estimate P_k o_n. Every M (M = 256 sweeps the staged passes twice per chunk, the
+   * estimate for the error and chi to the state update); without mini-batches, single plans only. */
   int32_t engine;
 } ptycho_params;
 
@@ -226,7 +227,7 @@ ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
 ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
 
 /* Kernel launches one iteration issues: the fused kernel (M <= 128) or 5 (far)
- * / 7 (near) staged passes per chunk of positions (M = 256), 4 update kernels
+ * / 7 (near) staged passes per chunk of positions (M = 256; pc-DM 8 / 11), 4 update kernels
  * (2 more for pc-DM), per batch for the mini-batch engine, and 3 complex-constraint
  * kernels when `in_window` is non-zero (copies not counted). */
 int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);

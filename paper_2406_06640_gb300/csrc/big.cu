@@ -87,10 +87,16 @@ __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
     const int2 pn = b.pos[n];
     const float2* Pk = b.P + (size_t)k * MM + (size_t)y * BL;
     const float2* On = b.O + (size_t)(pn.x + y) * b.obj_w + pn.y;
+    // pc-DM second sweep: the reflected wave chi = 2 P o_n - psi_n
+    const float2* St = b.dm_pass == 2 ? b.psi + ((size_t)n * b.K + k) * MM + (size_t)y * BL : nullptr;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int x = t + 16 * j;
       float2 psi = cmul(Pk[x], On[x]);
+      if (St) {
+        const float2 st = b.dm_init ? psi : St[x];
+        psi = make_float2(2.f * psi.x - st.x, 2.f * psi.y - st.y);
+      }
       if (!NEAR && ((y + x) & 1)) psi = make_float2(-psi.x, -psi.y);
       a[j] = psi;
     }
@@ -241,8 +247,9 @@ __global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
     const float tt = es + yv;
     ec = (tt - es) - yv;
     es = tt;
-    b.R[(size_t)c * MM + (size_t)y * BL + x] = R;
+    if (b.dm_pass != 1) b.R[(size_t)c * MM + (size_t)y * BL + x] = R;  // pc-DM: R of chi only
   }
+  if (b.dm_pass == 2) return;  // pc-DM: the error is the estimate's (first sweep); uniform per block
   s_red[threadIdx.x] = (double)es - (double)ec;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -279,16 +286,27 @@ __global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
     line_fft<true>(a, s_sw[li], s_tw, t);
     const float2* Pk = b.P + (size_t)k * MM + (size_t)y * BL;
     float2* pacc = b.pacc + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
+    // pc-DM: psi_n <- psi_n + Pi_F(chi) - P o_n, the overlap step takes psi_n - P o_n (its probe
+    // sums follow the object step)
+    float2* St = b.psi ? b.psi + ((size_t)n * b.K + k) * MM + (size_t)y * BL : nullptr;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int x = t + 16 * j;
       float2 psi_new = cscale(a[j], s);
       if (!NEAR && ((y + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
       const float2 p = Pk[x], o = On[x];
-      const float2 dpsi = csub(psi_new, cmul(p, o));
+      float2 dpsi = csub(psi_new, cmul(p, o));
+      if (St) {
+        const float2 ov = cmul(p, o);
+        const float2 st = cadd(b.dm_init ? ov : St[x], dpsi);
+        St[x] = st;
+        dpsi = csub(st, ov);
+      }
       cacc[j] = cadd(cacc[j], cconjmul(p, dpsi));
-      const float2 pc = cconjmul(o, dpsi);
-      pacc[x] = first ? pc : cadd(pacc[x], pc);
+      if (!St) {
+        const float2 pc = cconjmul(o, dpsi);
+        pacc[x] = first ? pc : cadd(pacc[x], pc);
+      }
     }
   }
   float2* cn = b.cn + (size_t)n * MM + (size_t)y * BL;
@@ -311,7 +329,8 @@ int big_row_blocks() { return BL / RB; }
 template <int KH>
 constexpr size_t big_mod_smem() { return sizeof(float) * 2 * (size_t)(RB + 2 * KH) * BL; }
 
-cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) {
+// the passes of one chunk; `full` false stops after the modulus pass (pc-DM first sweep)
+static cudaError_t big_passes(const BigArgs& b, int nc, bool full, cudaStream_t s) {
   const dim3 blk(LINES * BT), rblk(LROW * BT);
   const dim3 grow(BL / LROW, b.K, nc), gcol(BL / LINES, b.K, nc), gfin(BL / LROW, nc), gmod(BL / RB, nc);
   const size_t cs = big_cols_smem();
@@ -335,6 +354,7 @@ cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) {
   }
   if (b.kh == 5) k_big_modulus<5><<<gmod, 256, big_mod_smem<5>(), s>>>(b);
   else k_big_modulus<15><<<gmod, 256, big_mod_smem<15>(), s>>>(b);
+  if (!full) return cudaGetLastError();
   if (b.near_field) {
     k_big_rows<1, true><<<grow, rblk, 0, s>>>(b);
     k_big_cols<3><<<gcol, blk, cs, s>>>(b);
@@ -344,6 +364,18 @@ cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) {
     k_big_final<false><<<gfin, rblk, 0, s>>>(b);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) { return big_passes(b, nc, true, s); }
+
+cudaError_t launch_big_chunk_dm(const BigArgs& b, int nc, cudaStream_t s) {
+  if (!b.psi) return cudaErrorInvalidValue;
+  BigArgs e = b;
+  e.dm_pass = 1;  // the estimate P o_n through the propagation and the model, for the error only
+  cudaError_t err = big_passes(e, nc, false, s);
+  if (err != cudaSuccess) return err;
+  e.dm_pass = 2;  // chi = 2 P o_n - psi_n: its modulus ratio, back-propagation, state update
+  return big_passes(e, nc, true, s);
 }
 
 }  // namespace ptycho

@@ -217,8 +217,8 @@ static ptycho_status validate(const ptycho_params* p) {
   if (p->minibatch < 0) return fail(PTYCHO_EINVAL, "minibatch must be >= 0");
   if (p->engine != PTYCHO_ENGINE_PIE && p->engine != PTYCHO_ENGINE_DM)
     return fail(PTYCHO_EINVAL, "engine must be PTYCHO_ENGINE_PIE or PTYCHO_ENGINE_DM");
-  if (p->engine == PTYCHO_ENGINE_DM && (p->M > 128 || (p->minibatch > 0 && p->minibatch < p->N)))
-    return fail(PTYCHO_EUNSUPPORTED, "pc-DM handles M <= 128 without mini-batches");
+  if (p->engine == PTYCHO_ENGINE_DM && p->minibatch > 0 && p->minibatch < p->N)
+    return fail(PTYCHO_EUNSUPPORTED, "pc-DM runs without mini-batches");
   if (p->step_rule != PTYCHO_STEP_NORMALISED && p->step_rule != PTYCHO_STEP_RPIE)
     return fail(PTYCHO_EINVAL, "step_rule must be PTYCHO_STEP_NORMALISED or PTYCHO_STEP_RPIE");
   if (p->step_rule == PTYCHO_STEP_RPIE &&
@@ -715,6 +715,19 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
     }
     if (pl->in_window(t)) PT_CUDA(launch_constraint(ca, s), "constraint launch");
     return PTYCHO_OK;
+  } else if (pl->big && pl->d_psi) {
+    // pc-DM on the staged path: per chunk, the estimate sweep (error) and the chi sweep
+    BigArgs ba = pl->ba;
+    ba.O = static_cast<const float2*>(object);
+    ba.P = static_cast<const float2*>(probe);
+    ba.n_first = 0;
+    ba.psi = pl->d_psi;
+    ba.dm_init = pl->dm_fresh ? 1 : 0;
+    for (int n0 = 0; n0 < pl->p.N; n0 += pl->chunk) {
+      ba.n0 = n0;
+      PT_CUDA(launch_big_chunk_dm(ba, std::min(pl->chunk, pl->p.N - n0), s), "staged pc-DM launch");
+    }
+    pl->dm_fresh = false;
   } else if (pl->big) {
     BigArgs ba = pl->ba;
     ba.O = static_cast<const float2*>(object);
@@ -1261,7 +1274,9 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
   if (!pl) return 0;
   const int passes = pl->p.geometry == PTYCHO_NEARFIELD ? 7 : 5;  // staged passes per chunk
   int fft = 1;
-  if (pl->big) fft = (pl->p.N + pl->chunk - 1) / pl->chunk * passes;
+  // pc-DM: the estimate sweep stops after the modulus pass (3 far, 4 near)
+  const int dm_extra = pl->p.geometry == PTYCHO_NEARFIELD ? 4 : 3;
+  if (pl->big) fft = (pl->p.N + pl->chunk - 1) / pl->chunk * (pl->d_psi ? passes + dm_extra : passes);
   if (pl->mb > 0) {  // per batch: its fused launch or staged passes, and the 4 update kernels
     fft = -4;
     for (int b = 0; b < pl->nb; ++b) {

@@ -79,8 +79,14 @@ struct BigArgs {
   float2* pacc;       // C x K x M x M probe partials (slot = position within the chunk)
   float* dacc;        // C x M x M
   double* errpart;    // N x (M / 16) error partials
+  // pc-DM: exit-wave state (N x K x M x M) or null; dm_init: the state starts at P o_n this pass
+  float2* psi;
+  int dm_init;
+  int dm_pass;        // pc-DM: 1 propagates P o_n for the error only, 2 propagates chi = 2 P o_n - psi_n
 };
+// the staged passes of one chunk; launch_big_chunk_dm: the two pc-DM sweeps (b.psi set)
 cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s);
+cudaError_t launch_big_chunk_dm(const BigArgs& b, int nc, cudaStream_t s);
 int big_row_blocks();
 
 // tcgen05 BF16 GEMM (unet_gemm.cu): D[M x Ntot] (+)= A[M x K] . B[Ntot x K]^T, bf16 operands

@@ -73,7 +73,6 @@ def _plan_status(**over):
     (dict(eps_mod=float("nan")), 1), (dict(step_rule=2), 1), (dict(step_rule="rpie", rpie_alpha_obj=1.5), 1),
     (dict(step_rule="rpie", rpie_alpha_probe=-0.1), 1), (dict(minibatch=-1), 1),
     (dict(engine=2), 1), (dict(engine="dm", minibatch=2), 4),
-    (dict(M=256, obj_h=300, obj_w=300, engine="dm"), 4),
 ])
 def test_validation_rejects_bad_requests(over, expect):
     st, msg = _plan_status(**over)

@@ -150,6 +150,14 @@ def test_pc_dm_engine_probe_sizes(M, K, start):
     check(p, dict(p.params, engine="dm", probe_update_start=start), 4)
 
 
+@pytest.mark.parametrize("geometry,K", [("near", 2), ("far", 1)])
+def test_pc_dm_engine_m256_staged(geometry, K):
+    """M = 256 on the staged passes: per chunk the estimate sweep (error) and the chi sweep (ratio,
+    back-propagation, state update); a constraint window."""
+    p = make_problem(0, scan_side=3, obj_side=400, M=256, K=K, geometry=geometry, sigma=1.5)
+    check(p, dict(p.params, sigma1=1.5, sigma2=1.5, engine="dm", windows=[(2, 3)], alpha1=1.0, alpha2=0.2), 4)
+
+
 def test_pc_dm_engine_near_field_modes_window_and_resume():
     """Near field, two modes, intensity blur, a constraint window; the state carries across calls
     (3 + 2 iterations equal 5 bitwise)."""
