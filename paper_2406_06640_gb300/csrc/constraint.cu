@@ -33,9 +33,8 @@ namespace ptycho {
 constexpr double kFix = 4294967296.0;  // 2^32
 
 // Row prefix sums of |ln a| and |phi| in 32.32 fixed point: P(y, x) = sum over x' < x of the value at
-// (y, x'), obj_h x (obj_w + 1) each. One warp per object row, 4 consecutive pixels per lane (128
-// per step, warp scan of the lane totals with a carry), 8 rows per block. v * 2^32 is exact in
-// FP32, so llrintf of it is the nearest 32.32 value of v.
+// (y, x'), obj_h x (obj_w + 1) each. v * 2^32 is exact in FP32, so llrintf of it is the nearest
+// 32.32 value of v.
 __device__ __forceinline__ void cc_values(float2 o, long long& l, long long& p) {
   const float f = 4294967296.0f;
   l = llrintf(fabsf(logf(fmaxf(sqrtf(cabs2(o)), 1e-6f))) * f);
@@ -43,54 +42,57 @@ __device__ __forceinline__ void cc_values(float2 o, long long& l, long long& p) 
 }
 
 __global__ void __launch_bounds__(256) k_cc_rows(const ConstraintArgs c) {
-  const int lane = threadIdx.x & 31;
-  const int y = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (y >= c.obj_h) return;
+  // one block per object row, warp w scanning segment w of SEG pixels (32 per step, a carry
+  // between steps), then every segment adds the totals of the segments before it
+  __shared__ long long s_tl[8], s_tp[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int y = blockIdx.x;
   const int W1 = c.obj_w + 1;
+  const int SEG = ((c.obj_w + 7) / 8 + 31) / 32 * 32;
+  const int x_lo = min(c.obj_w, w * SEG), x_hi = min(c.obj_w, x_lo + SEG);
   long long* pl = c.map_lna + (size_t)y * W1;
   long long* pp = c.map_phi + (size_t)y * W1;
   const float2* Oy = c.O + (size_t)y * c.obj_w;
-  if (lane == 0) {
+  if (threadIdx.x == 0) {
     pl[0] = 0;
     pp[0] = 0;
   }
-  long long cl = 0, cp = 0;  // carries: the sums up to the current step
-  for (int x0 = 0; x0 < c.obj_w; x0 += 128) {
-    long long vl[4], vp[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int x = x0 + 4 * lane + j;
-      vl[j] = 0;
-      vp[j] = 0;
-      if (x < c.obj_w) cc_values(Oy[x], vl[j], vp[j]);
-    }
-#pragma unroll
-    for (int j = 1; j < 4; ++j) {
-      vl[j] += vl[j - 1];
-      vp[j] += vp[j - 1];
-    }
-    long long tl = vl[3], tp = vp[3];  // inclusive scan of the lane totals
+  long long cl = 0, cp = 0;  // this segment's sums so far
+  for (int x0 = x_lo; x0 < x_hi; x0 += 32) {
+    const int x = x0 + lane;
+    long long vl = 0, vp = 0;
+    if (x < x_hi) cc_values(Oy[x], vl, vp);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const long long ul = __shfl_up_sync(0xffffffffu, tl, d);
-      const long long up = __shfl_up_sync(0xffffffffu, tp, d);
+      const long long ul = __shfl_up_sync(0xffffffffu, vl, d);
+      const long long up = __shfl_up_sync(0xffffffffu, vp, d);
       if (lane >= d) {
-        tl += ul;
-        tp += up;
+        vl += ul;
+        vp += up;
       }
     }
-    const long long el = cl + tl - vl[3], ep = cp + tp - vp[3];  // sums before this lane's pixels
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int x = x0 + 4 * lane + j;
-      if (x < c.obj_w) {
-        pl[x + 1] = el + vl[j];
-        pp[x + 1] = ep + vp[j];
-      }
+    if (x < x_hi) {
+      pl[x + 1] = cl + vl;
+      pp[x + 1] = cp + vp;
     }
-    cl += __shfl_sync(0xffffffffu, tl, 31);
-    cp += __shfl_sync(0xffffffffu, tp, 31);
+    cl += __shfl_sync(0xffffffffu, vl, 31);
+    cp += __shfl_sync(0xffffffffu, vp, 31);
   }
+  if (lane == 0) {
+    s_tl[w] = cl;
+    s_tp[w] = cp;
+  }
+  __syncthreads();
+  long long ol = 0, op = 0;
+  for (int q = 0; q < w; ++q) {
+    ol += s_tl[q];
+    op += s_tp[q];
+  }
+  if (w > 0)
+    for (int x = x_lo + lane; x < x_hi; x += 32) {
+      pl[x + 1] += ol;
+      pp[x + 1] += op;
+    }
 }
 
 // one warp per box: the two box sums (exact) from M row differences each, C_n clamped, C_n in fixed
@@ -181,27 +183,39 @@ __global__ void __launch_bounds__(256) k_cc_apply(const ConstraintArgs c) {
     atomicAdd(&dn[0], n00);
   }
   __syncthreads();
-  // prefix sums along the rows (one thread per row), then along the columns (one per column)
-  if (lt < T) {
-    long long sq = 0;
-    int sn = 0;
-    for (int x = 0; x < T; ++x) {
-      sq += dq[lt * T1 + x];
-      sn += dn[lt * T1 + x];
-      dq[lt * T1 + x] = sq;
-      dn[lt * T1 + x] = sn;
+  // prefix sums along the rows, then along the columns: warp scans, each warp T / 8 lines
+  static_assert(T == 32, "one lane per tile column");
+  const int wl = lt & 31, wi = lt >> 5;
+  for (int ln = wi; ln < T; ln += 8) {
+    long long q = dq[ln * T1 + wl];
+    int m = dn[ln * T1 + wl];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long uq = __shfl_up_sync(0xffffffffu, q, d);
+      const int um = __shfl_up_sync(0xffffffffu, m, d);
+      if (wl >= d) {
+        q += uq;
+        m += um;
+      }
     }
+    dq[ln * T1 + wl] = q;
+    dn[ln * T1 + wl] = m;
   }
   __syncthreads();
-  if (lt < T) {
-    long long sq = 0;
-    int sn = 0;
-    for (int y = 0; y < T; ++y) {
-      sq += dq[y * T1 + lt];
-      sn += dn[y * T1 + lt];
-      dq[y * T1 + lt] = sq;
-      dn[y * T1 + lt] = sn;
+  for (int ln = wi; ln < T; ln += 8) {
+    long long q = dq[wl * T1 + ln];
+    int m = dn[wl * T1 + ln];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long uq = __shfl_up_sync(0xffffffffu, q, d);
+      const int um = __shfl_up_sync(0xffffffffu, m, d);
+      if (wl >= d) {
+        q += uq;
+        m += um;
+      }
     }
+    dq[wl * T1 + ln] = q;
+    dn[wl * T1 + ln] = m;
   }
   __syncthreads();
   const int X = tx0 + threadIdx.x;
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(256) k_cc_apply(const ConstraintArgs c) {
 
 cudaError_t launch_constraint(const ConstraintArgs& c, cudaStream_t s) {
   if (c.N == 0) return cudaSuccess;
-  k_cc_rows<<<(c.obj_h + 7) / 8, 256, 0, s>>>(c);
+  k_cc_rows<<<c.obj_h, 256, 0, s>>>(c);
   k_cc_cbar<<<(c.N + 7) / 8, 256, 0, s>>>(c);
   k_cc_apply<<<dim3(c.tiles_x, c.tiles_y), dim3(32, 8), 0, s>>>(c);
   return cudaGetLastError();
