@@ -304,6 +304,23 @@ static ptycho_status tune_staged_chunk(ptycho_plan_s* pl, int* best) {
   return PTYCHO_OK;
 }
 
+// Object-tile position lists (CSR) of positions [n0, n1): for each kObjTile tile, in increasing n,
+// (n, row, col, 0) of every position whose box overlaps it; appends tiles + 1 offsets to `start`
+// (relative to the whole `flat` array) and the entries to `flat`.
+static void append_tile_lists(const std::vector<int2>& pos, int n0, int n1, int M, int tx, int ty,
+                              std::vector<int>& start, std::vector<int4>& flat) {
+  std::vector<std::vector<int>> lists((size_t)tx * ty);
+  for (int n = n0; n < n1; ++n)
+    for (int by = pos[n].x / kObjTile; by <= (pos[n].x + M - 1) / kObjTile; ++by)
+      for (int bx = pos[n].y / kObjTile; bx <= (pos[n].y + M - 1) / kObjTile; ++bx)
+        lists[(size_t)by * tx + bx].push_back(n);
+  for (const auto& l : lists) {
+    start.push_back((int)flat.size());
+    for (int n : l) flat.push_back(make_int4(n, pos[n].x, pos[n].y, 0));
+  }
+  start.push_back((int)flat.size());
+}
+
 static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, const int32_t* positions) {
   const ptycho_params& p = pl->p;
   const int M = p.M, K = p.K, N = p.N;
@@ -430,19 +447,8 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   const int bsize = pl->mb > 0 ? pl->mb : N;
   std::vector<int> start;
   std::vector<int4> flat;
-  for (int b = 0; b < pl->nb; ++b) {
-    std::vector<std::vector<int>> lists((size_t)tx * ty);
-    for (int n = b * bsize; n < std::min(N, (b + 1) * bsize); ++n) {
-      const int2 q = pl->h_pos[n];
-      for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
-        for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
-    }
-    for (size_t i = 0; i < lists.size(); ++i) {
-      start.push_back((int)flat.size());
-      for (int n : lists[i]) flat.push_back(make_int4(n, pl->h_pos[n].x, pl->h_pos[n].y, 0));
-    }
-    start.push_back((int)flat.size());
-  }
+  for (int b = 0; b < pl->nb; ++b)
+    append_tile_lists(pl->h_pos, b * bsize, std::min(N, (b + 1) * bsize), M, tx, ty, start, flat);
   int* d_start;
   int4* d_list;
   PT_CUDA(pl->alloc(&d_start, start.size()), "alloc tile lists");
@@ -482,19 +488,9 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   const int* d_cstart = d_start;
   const int4* d_clist = d_list;
   if (pl->nb > 1) {
-    std::vector<std::vector<int>> lists((size_t)tx * ty);
-    for (int n = 0; n < N; ++n) {
-      const int2 q = pl->h_pos[n];
-      for (int by = q.x / kObjTile; by <= (q.x + M - 1) / kObjTile; ++by)
-        for (int bx = q.y / kObjTile; bx <= (q.y + M - 1) / kObjTile; ++bx) lists[(size_t)by * tx + bx].push_back(n);
-    }
     std::vector<int> cs;
     std::vector<int4> cl;
-    for (const auto& l : lists) {
-      cs.push_back((int)cl.size());
-      for (int n : l) cl.push_back(make_int4(n, pl->h_pos[n].x, pl->h_pos[n].y, 0));
-    }
-    cs.push_back((int)cl.size());
+    append_tile_lists(pl->h_pos, 0, N, M, tx, ty, cs, cl);
     int* ds;
     int4* dl;
     PT_CUDA(pl->alloc(&ds, cs.size()), "alloc constraint tile lists");
@@ -1342,6 +1338,10 @@ namespace ptycho {
 ptycho_status capi_validate(const ptycho_params* p) { return validate(p); }
 void capi_step_coefficients(const ptycho_params* p, UpdateArgs* u) { step_coefficients(*p, *u); }
 ptycho_status capi_fail(ptycho_status s, const std::string& msg) { return fail(s, msg); }
+void capi_tile_lists(const std::vector<int2>& pos, int M, int tx, int ty, std::vector<int>& start,
+                     std::vector<int4>& flat) {
+  append_tile_lists(pos, 0, (int)pos.size(), M, tx, ty, start, flat);
+}
 ptycho_status capi_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 std::vector<double> capi_taps(double sigma, int h) { return taps_1d(sigma, h); }
 bool capi_is_device_pointer(const void* ptr) { return is_device_pointer(ptr); }

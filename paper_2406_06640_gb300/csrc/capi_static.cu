@@ -26,6 +26,8 @@ void capi_step_coefficients(const ptycho_params* p, UpdateArgs* u);
 ptycho_status capi_fail(ptycho_status s, const std::string& msg);
 ptycho_status capi_cuda_fail(cudaError_t e, const char* what);
 std::vector<double> capi_taps(double sigma, int h);
+void capi_tile_lists(const std::vector<int2>& pos, int M, int tx, int ty, std::vector<int>& start,
+                     std::vector<int4>& flat);
 bool capi_is_device_pointer(const void* ptr);
 void capi_clear_error();
 }  // namespace ptycho
@@ -113,17 +115,9 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   if (max_slots < 1) return capi_fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
   const int slots = std::min(max_slots, N);
   const int tx = (p->obj_w + kObjTile - 1) / kObjTile, ty = (p->obj_h + kObjTile - 1) / kObjTile;
-  std::vector<std::vector<int>> lists((size_t)tx * ty);
-  for (int n = 0; n < N; ++n)
-    for (int by = hpos[n].x / kObjTile; by <= (hpos[n].x + M - 1) / kObjTile; ++by)
-      for (int bx = hpos[n].y / kObjTile; bx <= (hpos[n].y + M - 1) / kObjTile; ++bx)
-        lists[(size_t)by * tx + bx].push_back(n);
-  std::vector<int> start((size_t)tx * ty + 1, 0);
+  std::vector<int> start;
   std::vector<int4> flat;
-  for (size_t i = 0; i < lists.size(); ++i) {
-    start[i + 1] = start[i] + (int)lists[i].size();
-    for (int n : lists[i]) flat.push_back(make_int4(n, hpos[n].x, hpos[n].y, 0));
-  }
+  capi_tile_lists(hpos, M, tx, ty, start, flat);
   const size_t count = (size_t)N * MM;
   const int nb = (int)std::min<size_t>(1024, (count + 255) / 256);
   const size_t plane = (size_t)p->obj_h * p->obj_w;
