@@ -35,7 +35,8 @@ struct MonoShape {
   static constexpr size_t TAB_BYTES = (size_t)M * kTapsT * 8 + (size_t)M * 4;  // taps, then counts
   static constexpr size_t RED_BYTES = (size_t)(TPB / 32 + 1) * 2 * 8;
   static constexpr size_t SPEC_BYTES = (size_t)3 * kMonoMaxJ * 4;
-  static constexpr size_t BYTES = P_BYTES + 2 * R_BYTES + TAB_BYTES + RED_BYTES + SPEC_BYTES;
+  static constexpr size_t ROW_BYTES = (size_t)2 * M * 8;  // C p: row samples (i0, f), two buffers
+  static constexpr size_t BYTES = P_BYTES + 2 * R_BYTES + TAB_BYTES + RED_BYTES + SPEC_BYTES + ROW_BYTES;
   static_assert(M * M % TPB == 0 && TPB % M == 0, "pixel ownership");
 };
 
@@ -105,6 +106,8 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
   float* s_inv = reinterpret_cast<float*>(smem + SH::P_BYTES + 2 * SH::R_BYTES + SH::TAB_BYTES + SH::RED_BYTES);
   float* s_a = s_inv + kMonoMaxJ;
   float* s_w = s_a + kMonoMaxJ;
+  float2* s_rt = reinterpret_cast<float2*>(smem + SH::P_BYTES + 2 * SH::R_BYTES + SH::TAB_BYTES + SH::RED_BYTES +
+                                           SH::SPEC_BYTES);  // 2 x M
 
   const int tid = threadIdx.x;
   const int col = tid % M, row0 = tid / M;
@@ -206,21 +209,31 @@ __global__ void __launch_bounds__(MonoShape<M>::TPB, 1) k_mono_cgls(const MonoAr
     }
   };
 
-  // C p for the own pixels into acc, p in Pp
+  // C p for the own pixels into acc, p in Pp. The row samples of a wavelength are the same for a
+  // whole row of pixels: a table per wavelength (two buffers: the barrier that publishes table j
+  // also ends every read of table j - 2)
   auto forward = [&](float (&acc)[PPT]) {
 #pragma unroll
     for (int m = 0; m < PPT; ++m) acc[m] = 0.f;
     for (int j = 0; j < a.J; ++j) {
       const float inv_a = s_inv[j], wj = s_w[j];
+      float2* rt = s_rt + (j & 1) * M;
+      for (int i = tid; i < M; i += TPB) {
+        int i0;
+        float f;
+        interp_at(i, c, inv_a, M, i0, f);
+        rt[i] = make_float2(__int_as_float(i0), f);
+      }
+      __syncthreads();
       int x0;
       float fx;
       interp_at(col, c, inv_a, M, x0, fx);
       const float gx = 1.f - fx;
 #pragma unroll
       for (int m = 0; m < PPT; ++m) {
-        int y0;
-        float fy;
-        interp_at(row0 + m * RSTEP, c, inv_a, M, y0, fy);
+        const float2 ry = rt[row0 + m * RSTEP];
+        const int y0 = __float_as_int(ry.x);
+        const float fy = ry.y;
         const float* p0 = Pp + (y0 + 1) * LDP + (x0 + 1);
         const float top = fmaf(fx, p0[1], gx * p0[0]);
         const float bot = fmaf(fx, p0[LDP + 1], gx * p0[LDP]);
