@@ -116,7 +116,8 @@ typedef struct {
    * and every psi_{n,k} moves by P_k (o_n after - o_n before); then P takes its step from the new
    * object, sum conj(o'_n) (psi_{n,k} - P_k o'_n) over sum |o'_n|^2. E_t is the pc model error
    * of the estimate P_k o_n. Every M (M = 256 sweeps the staged passes twice per chunk, the
-   * estimate for the error and chi to the state update); without mini-batches, single plans only. */
+   * estimate for the error and chi to the state update); without mini-batches; in single and
+   * batch plans (a batch member keeps its own launches), not in ptycho_iterate_static. */
   int32_t engine;
 } ptycho_params;
 
@@ -166,7 +167,9 @@ ptycho_status ptycho_destroy(ptycho_plan_t plan);
  * message naming it. ptycho_iterate_batch takes B object and B probe device
  * pointers (updated in place); ptycho_error_batch synchronises and writes the
  * last E of every problem (host, B doubles). ptycho_destroy releases a batch
- * plan and all its problems. Single-plan calls reject batch plans. */
+ * plan and all its problems. Single-plan calls reject batch plans. pc-DM problems are
+ * members with their own launches (the first iteration, which starts their exit-wave state, is a
+ * graph of its own); mini-batch problems are rejected (PTYCHO_EUNSUPPORTED). */
 ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, const float* const* intensities,
                                 const int32_t* const* positions, void* cuda_stream, ptycho_plan_t* out);
 ptycho_status ptycho_iterate_batch(ptycho_plan_t plan, void* const* objects, void* const* probes, int32_t n_iter);

@@ -924,8 +924,6 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       st = fail(PTYCHO_EINVAL, "intensities and positions must be non-NULL");
     if (st == PTYCHO_OK && params[b]->minibatch > 0 && params[b]->minibatch < params[b]->N)
       st = fail(PTYCHO_EUNSUPPORTED, "mini-batch problems run through ptycho_plan");
-    if (st == PTYCHO_OK && params[b]->engine == PTYCHO_ENGINE_DM)
-      st = fail(PTYCHO_EUNSUPPORTED, "pc-DM problems run through ptycho_plan");
     if (st != PTYCHO_OK) return fail(st, "problem " + std::to_string(b) + ": " + g_last_error);
   }
   ptycho_plan_s* pl = new (std::nothrow) ptycho_plan_s();
@@ -941,7 +939,8 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
   std::vector<int> member_class(B, -1);
   for (int b = 0; b < B; ++b) {
     const ptycho_params& q = *params[b];
-    if (!fused_queue_supported(q.M)) continue;
+    // pc-DM members keep their own launches (the work queue runs the simultaneous engine)
+    if (!fused_queue_supported(q.M) || q.engine == PTYCHO_ENGINE_DM) continue;
     const int kh = (q.kernel_size - 1) / 2 == 5 ? 5 : 15;
     const int near = q.geometry == PTYCHO_NEARFIELD ? 1 : 0;
     int ci = -1;
@@ -1042,7 +1041,9 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
     key.reserve(3 * B);
     for (int b = 0; b < B; ++b) {
       const ptycho_plan_s* m = pl->members[b];
-      key.push_back((uintptr_t)((m->iter >= m->p.probe_update_start ? 1 : 0) | (m->in_window(m->iter) ? 2 : 0)));
+      // pc-DM members: whether this iteration starts the exit-wave state (baked into the graph)
+      key.push_back((uintptr_t)((m->iter >= m->p.probe_update_start ? 1 : 0) | (m->in_window(m->iter) ? 2 : 0) |
+                                (m->d_psi && m->dm_fresh ? 4 : 0)));
       key.push_back((uintptr_t)objects[b]);
       key.push_back((uintptr_t)probes[b]);
     }
@@ -1140,6 +1141,7 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
     for (ptycho_plan_s* m : pl->members) {
       m->iter++;
       m->runs++;
+      m->dm_fresh = false;  // a replayed graph started every pc-DM state it holds
     }
   }
   return PTYCHO_OK;

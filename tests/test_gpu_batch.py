@@ -127,6 +127,26 @@ def test_batch_reports_its_kernel_launches():
     batch.close()
 
 
+def test_batch_with_pc_dm_members():
+    """pc-DM members beside simultaneous-engine members of the same shape: the DM members keep
+    their own launches, the first iteration (which starts their state) is a graph of its own; every
+    member matches the oracle, and reruns are bitwise equal."""
+    dev = torch.device("cuda:0")
+    probs = []
+    for i, (side, engine) in enumerate(((3, "dm"), (4, "pie"), (4, "dm"), (5, "pie"))):
+        p = make_problem(0, scan_side=side, obj_side=64 + 10 * side + 16, M=64, K=2, sigma=1.0)
+        probs.append((p, dict(p.params, engine=engine, windows=[(2, 3)], alpha1=1.0, alpha2=0.2)))
+    n_iter = 4
+    O1, P1, E1 = _run_batch(dev, probs, n_iter)
+    O2, P2, E2 = _run_batch(dev, probs, n_iter)
+    for b in range(len(probs)):
+        assert np.array_equal(O1[b], O2[b]) and np.array_equal(P1[b], P2[b]) and E1[b] == E2[b], b
+    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)  # noqa: E731
+    for b, (prob, prm) in enumerate(probs):
+        Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), n_iter)
+        assert rel(O1[b], Oo) < 1e-4 and rel(P1[b], Po) < 1e-4 and abs(E1[b] - Eo[-1]) / Eo[-1] < 1e-4, b
+
+
 def test_batch_rejects_single_plan_calls():
     from paper_2406_06640_gb300 import PtychoError
     from paper_2406_06640_gb300.engine import ReconstructionBatch
