@@ -153,3 +153,10 @@ def test_monochromatisation_null_buffers_and_empty_batch():
                                      None) == 1
     # no patterns: nothing to launch, no device needed
     assert lib.ptycho_monochromatise(64, 1, one, one, 0, 3, None, None, None, 0, None) == 0
+
+
+def test_batch_launch_count_arguments():
+    lib = pg.load()
+    n = ctypes.c_int32(-1)
+    assert lib.ptycho_batch_launches(None, ctypes.byref(n)) == 1
+    assert lib.ptycho_launches_per_iteration(None, 1) == 0
