@@ -243,7 +243,9 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);
  * ptycho_iterate, but takes every scratch buffer from one file-scope device
  * array of 32 MiB that the library holds on each device until the process
  * exits. It calls no cudaMalloc, cudaFree or other allocating routine.
- *   p, intensities, positions  as for ptycho_plan (intensities: device)
+ *   p, intensities, positions  as for ptycho_plan (intensities: device, 16-byte aligned -- the
+ *                              kernels read them in place; a misaligned pointer gives PTYCHO_EINVAL;
+ *                              device positions are read on cuda_stream)
  *   object, probe              device, updated in place as by ptycho_iterate
  *   n_iter                     0..4096 (M <= 128; larger M gives PTYCHO_EUNSUPPORTED)
  *   errors                     host, n_iter doubles (E of each iteration), or NULL

@@ -40,7 +40,13 @@ Readings of passages that the paper leaves open (kept identical on the GPU):
   * the complex constraint acts on the whole updated object: C_n of Eq. 11
     per box, clamped to [cbar_min, cbar_max] (Sec. 4.8), averaged over the
     boxes that cover a pixel, then Eqs. 9-10; uncovered pixels are unchanged;
-  * phase = angle() in (-pi, pi], no unwrapping; windows are 1-based inclusive.
+  * phase = angle() in (-pi, pi], no unwrapping; windows are 1-based inclusive;
+  * pc-DM (iteration_dm): the constraint acts between the object and the probe
+    steps and moves each exit-wave state with its box.
+
+Parity unpinned (only oracle <-> GPU agreement fixes them; no passage of the
+paper does): the constants beta, delta, eps and the clamp range, the per-pixel
+mean of C_n, and where pc-DM applies the complex constraint.
 """
 from __future__ import annotations
 

@@ -330,7 +330,10 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   // ---- positions
   pl->h_pos.resize(N);
   if (is_device_pointer(positions)) {
-    PT_CUDA(cudaMemcpy(pl->h_pos.data(), positions, sizeof(int2) * N, cudaMemcpyDeviceToHost), "copy positions");
+    // read on the plan's stream, after whatever the caller queued there to produce the positions
+    PT_CUDA(cudaMemcpyAsync(pl->h_pos.data(), positions, sizeof(int2) * N, cudaMemcpyDeviceToHost, s),
+            "copy positions");
+    PT_CUDA(cudaStreamSynchronize(s), "stream sync");
   } else {
     std::memcpy(pl->h_pos.data(), positions, sizeof(int2) * N);
   }

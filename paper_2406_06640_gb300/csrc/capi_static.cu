@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -94,15 +95,23 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
   if ((p->minibatch > 0 && p->minibatch < p->N) || p->engine == PTYCHO_ENGINE_DM)
     return capi_fail(PTYCHO_EUNSUPPORTED, "the mini-batch and pc-DM engines run through ptycho_plan");
   if (!capi_is_device_pointer(intensities)) return capi_fail(PTYCHO_EINVAL, "intensities must be a device pointer");
+  // the fused kernel stages each position's rows of I with bulk async copies, which start on 16-byte
+  // boundaries (the plan path copies I into its own buffer; this path reads the caller's)
+  if (reinterpret_cast<uintptr_t>(intensities) % 16 != 0)
+    return capi_fail(PTYCHO_EINVAL, "intensities must be 16-byte aligned (bulk copies of the pattern rows)");
   if (p->M > 128) return capi_fail(PTYCHO_EUNSUPPORTED, "the static entry point handles M <= 128");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int M = p->M, K = p->K, N = p->N;
   const size_t MM = (size_t)M * M;
 
-  // positions: host copy for validation and the tile lists
+  // positions: host copy for validation and the tile lists. A device array is read on the caller's
+  // stream, after whatever the caller queued there to produce it. The host vectors below are pageable:
+  // a host-to-device cudaMemcpyAsync from pageable memory is staged before the call returns, so they
+  // may go out of scope while the copies are still queued.
   std::vector<int2> hpos(N);
   if (capi_is_device_pointer(positions)) {
-    PS_CUDA(cudaMemcpy(hpos.data(), positions, sizeof(int2) * N, cudaMemcpyDeviceToHost), "copy positions");
+    PS_CUDA(cudaMemcpyAsync(hpos.data(), positions, sizeof(int2) * N, cudaMemcpyDeviceToHost, s), "copy positions");
+    PS_CUDA(cudaStreamSynchronize(s), "stream sync");
   } else {
     std::memcpy(hpos.data(), positions, sizeof(int2) * N);
   }

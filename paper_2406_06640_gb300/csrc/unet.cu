@@ -882,7 +882,9 @@ ptycho_status ptycho_warmstart(ptycho_unet_t u, const float* intensities, const 
   cudaStream_t s = u->stream;
   std::vector<int32_t> pos(2 * (size_t)N);
   if (capi_is_device_pointer(positions)) {
-    UN_CUDA(cudaMemcpy(pos.data(), positions, sizeof(int32_t) * pos.size(), cudaMemcpyDeviceToHost), "positions");
+    UN_CUDA(cudaMemcpyAsync(pos.data(), positions, sizeof(int32_t) * pos.size(), cudaMemcpyDeviceToHost, s),
+            "positions");
+    UN_CUDA(cudaStreamSynchronize(s), "stream sync");
   } else {
     std::memcpy(pos.data(), positions, sizeof(int32_t) * pos.size());
   }

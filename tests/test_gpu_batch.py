@@ -195,3 +195,35 @@ def test_autotuner_picks_a_chunk_length_caches_it_and_can_be_fixed():
     for b, (prob, prm) in enumerate(probs):
         Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), 2)
         assert rel(O[b], Oo) < 1e-4 and rel(P[b], Po) < 1e-4 and abs(E[b] - Eo[-1]) / Eo[-1] < 1e-4, b
+
+
+def test_configuration3_shaped_batch_against_the_oracle():
+    """Seven members drawn from the 64-problem batched configuration, as generated for it: the
+    largest N (1539 positions of 128^2, K = 4, far field), two M = 256 members (near and far field,
+    staged passes), and M = 64 / 128 members of both geometries with K 1-4, random sigma, iterated
+    together (one graph launch per iteration, one queued launch per shape class). Every member
+    against the oracle: rel. L2 and per-pixel bounds of O and P, and its last E."""
+    from synth.generators import make_cfg3_member
+
+    dev = torch.device("cuda:0")
+    members = (43, 32, 8, 1, 20, 49, 55)
+    probs = []
+    for i in members:
+        p = make_cfg3_member(i)
+        probs.append((p, dict(p.params)))
+    assert max(p.params["N"] for p, _ in probs) == 1539
+    assert sum(p.params["M"] == 256 for p, _ in probs) == 2
+    n_iter = 2
+    O, P, E = _run_batch(dev, probs, n_iter)
+    for b, (prob, prm) in enumerate(probs):
+        Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), n_iter)
+        eo = np.linalg.norm(O[b] - Oo) / np.linalg.norm(Oo)
+        ep = np.linalg.norm(P[b] - Po) / np.linalg.norm(Po)
+        mo = np.max(np.abs(O[b] - Oo)) / np.max(np.abs(Oo))
+        mp = np.max(np.abs(P[b] - Po)) / np.max(np.abs(Po))
+        ee = abs(E[b] - Eo[-1]) / Eo[-1]
+        print(f"[parity] configuration-3 member {members[b]} (M={prm['M']} K={prm['K']} N={prm['N']} "
+              f"{prm['geometry']}): rel L2 object {eo:.3e} probe {ep:.3e} error {ee:.3e}; "
+              f"per-pixel object {mo:.3e} probe {mp:.3e}")
+        assert eo < 1e-4 and ep < 1e-4 and ee < 1e-4, (members[b], eo, ep, ee)
+        assert mo < 1e-4 and mp < 1e-4, (members[b], mo, mp)

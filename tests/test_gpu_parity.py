@@ -53,14 +53,32 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def check(prob, params, n_iter, tol=TOL):
+def pix(a, b):
+    """Largest per-pixel deviation relative to the largest magnitude: max |a - b| / max |b|. Beside the
+    global rel. L2 it catches a localised error (a wrong border tile, a few wrong pixels) that the
+    norm of a large object would hide. Pixels no box covers are never updated, so over the whole
+    object this is the bound over the scanned field of view."""
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def compare(tag, gpu, orc, tol=TOL):
+    """rel. L2 and per-pixel bounds of object and probe, relative bound of every iteration's E."""
+    (Og, Pg, Eg), (Oo, Po, Eo) = gpu, orc
+    eo, ep, mo, mp = rel(Og, Oo), rel(Pg, Po), pix(Og, Oo), pix(Pg, Po)
+    ee = float(np.max(np.abs(np.asarray(Eg) - Eo) / Eo))
+    print(f"[parity] {tag}: rel L2 object {eo:.3e} probe {ep:.3e} error {ee:.3e}; "
+          f"per-pixel object {mo:.3e} probe {mp:.3e}")
+    assert np.shape(Eg) == np.shape(Eo)
+    assert eo <= tol and ep <= tol and ee <= tol, (eo, ep, ee)
+    assert mo <= tol and mp <= tol, (mo, mp)
+    return eo, ep, ee, mo, mp
+
+
+def check(prob, params, n_iter, tol=TOL, tag=None):
     Og, Pg, Eg = run_gpu(prob, params, n_iter)
     Oo, Po, Eo = run_oracle(prob, params, n_iter)
-    eo, ep = rel(Og, Oo), rel(Pg, Po)
-    ee = float(np.max(np.abs(Eg - Eo) / Eo))
-    print(f"rel L2 object {eo:.3e} probe {ep:.3e} error {ee:.3e}")
-    assert Eg.shape == Eo.shape
-    assert eo <= tol and ep <= tol and ee <= tol, (eo, ep, ee)
+    tag = tag or f"M={params['M']} K={params['K']} N={params['N']} {params.get('geometry', 'far')}, {n_iter} it."
+    compare(tag, (Og, Pg, Eg), (Oo, Po, Eo), tol)
     return Og, Pg, Eg
 
 
@@ -252,6 +270,32 @@ def test_config1_full_size_two_iterations():
     the benchmark times, compared element by element with the oracle over two iterations."""
     p = make_problem(1)
     check(p, p.params, 2)
+
+
+def test_config1_bench_configuration_20_iterations():
+    """Configuration 1 exactly as bench.py times it (the complex constraint in every iteration) over
+    20 of its 200 iterations: rel. L2 and per-pixel bounds of O and P, every iteration's E."""
+    p = make_problem(1)
+    check(p, dict(p.params, windows=[(1, 1 << 30)]), 20, tag="configuration 1, bench configuration, 20 it.")
+
+
+def test_config2_full_size_three_iterations():
+    """Full configuration 2 (near field F = 10, M = 256, K = 8, 256 positions, 1024^2 object) over
+    three iterations on the staged passes."""
+    p = make_problem(2)
+    check(p, p.params, 3, tag="configuration 2, 3 it.")
+
+
+def test_config4_engine_two_iterations():
+    """Configuration 4's engine run (electron-like crystal, M = 128, K = 1, 4096 positions, 256^2
+    object, 200 counts per pattern) as the warm-start comparison runs it: the intensity-blur model of
+    Eq. 2 with the simulator's +-ceil(5 sigma) taps, from the flat start, two iterations."""
+    from paper_2406_06640_gb300.warmstart import eval_kernel_size
+
+    p = make_problem(4)
+    s = p.sim_sigma
+    prm = dict(p.params, blur_domain="intensity", sigma1=s, sigma2=s, kernel_size=eval_kernel_size(s))
+    check(p, prm, 2, tag="configuration 4 engine, 2 it.")
 
 
 @pytest.mark.parametrize("engine", ["pie", "dm"])
