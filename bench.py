@@ -247,7 +247,7 @@ def traffic_record(kernel_tag, name="fused_kernel_traffic.json", workload="far12
     return rec.get("dram_bytes_per_launch_full_size")
 
 
-def kernel_source_hash(files=("cluster.cuh", "fft.cuh", "pc_fused_kernel.cuh", "pc_fused.cu"), struct="FusedArgs"):
+def kernel_source_hash(files=("cluster.cuh", "fft.cuh", "fused_common.cuh", "pc_fused_seq.cu"), struct="FusedArgs"):
     """Hash of what a kernel is compiled from: its sources and its argument struct."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_06640_gb300", "csrc")
@@ -264,10 +264,10 @@ def kernel_label(prob, params):
         return "staged passes (M=256)"
     geo = "near" if params["geometry"] == "near" else "far"
     if params.get("minibatch", 0):
-        return f"pc_fused_kernel<{prob.M}, {geo}> per batch with its update kernels (events around the batch loop)"
+        return f"pc_seq_kernel<{prob.M}, {geo}> per batch with its update kernels (events around the batch loop)"
     if params.get("engine") == "dm":
         return f"pc_fused_kernel<{prob.M}, {geo}, DM>"
-    return f"pc_fused_kernel<{prob.M}, {geo}>"
+    return f"pc_seq_kernel<{prob.M}, {geo}>"
 
 
 # ------------------------------------------------------------------ arms

@@ -363,8 +363,13 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
     pl->slots = pl->chunk;
   } else {
     int max_slots = 0;
-    PT_CUDA(fused_max_slots(M, K, &max_slots), "occupancy of the fused kernel");
-    if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
+    if (p.engine == PTYCHO_ENGINE_DM) {
+      PT_CUDA(fused_dm_max_slots(M, K, &max_slots), "occupancy of the pc-DM kernel");
+      if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
+    } else {
+      PT_CUDA(fused_max_slots(M, K, &max_slots), "occupancy of the fused kernel");
+      if (max_slots < 1) return fail(PTYCHO_EUNSUPPORTED, "the fused kernel does not fit on this device");
+    }
     pl->slots = std::min(max_slots, N);
   }
   if (pl->parts > 0) pl->slots = pl->parts;  // partials per position chunk (work-queue batch member)

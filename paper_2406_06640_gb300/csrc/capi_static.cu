@@ -121,7 +121,7 @@ extern "C" ptycho_status ptycho_iterate_static(const ptycho_params* p, const flo
 
   int max_slots = 0;
   PS_CUDA(fused_max_slots(M, K, &max_slots), "occupancy of the fused kernel");
-  if (max_slots < 1) return capi_fail(PTYCHO_EUNSUPPORTED, "a cluster of K CTAs does not fit on this device");
+  if (max_slots < 1) return capi_fail(PTYCHO_EUNSUPPORTED, "the fused kernel does not fit on this device");
   const int slots = std::min(max_slots, N);
   const int tx = (p->obj_w + kObjTile - 1) / kObjTile, ty = (p->obj_h + kObjTile - 1) / kObjTile;
   std::vector<int> start;

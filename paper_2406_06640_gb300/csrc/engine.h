@@ -46,7 +46,9 @@ struct FusedArgs {
   int dm_init;
 };
 
-// fused kernel launch; returns the number of slots (co-resident clusters) used
+// single-problem fused launch (pc_fused_seq.cu: one CTA per position, modes in sequence) over
+// `slots` persistent CTAs; fused_max_slots gives the co-resident CTAs of the GPU. Partials: pacc
+// slots x K x M x M, dacc slots x M x M, errpart slots x K (the slot's error in entry 0)
 cudaError_t launch_fused(int M, const FusedArgs& a, int slots, cudaStream_t s);
 cudaError_t fused_max_slots(int M, int K, int* slots);
 // work-queue launch (M = 32, 64, 128): `slots` persistent clusters drain a.chunks through a.queue;
@@ -55,6 +57,7 @@ cudaError_t launch_fused_queue(int M, const FusedArgs& a, int slots, cudaStream_
 cudaError_t fused_queue_max_slots(int M, int K, int* slots);
 // pc-DM launch (single problem, M <= 128): as launch_fused with the exit-wave state a.psi
 cudaError_t launch_fused_dm(int M, const FusedArgs& a, int slots, cudaStream_t s);
+cudaError_t fused_dm_max_slots(int M, int K, int* slots);
 cudaError_t fused_dm_timed_out(bool* out);
 bool fused_queue_supported(int M);
 size_t fused_smem_bytes(int M);

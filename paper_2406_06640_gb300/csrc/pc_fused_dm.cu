@@ -49,6 +49,40 @@ cudaError_t launch_fused_dm(int M, const FusedArgs& a, int slots, cudaStream_t s
   }
 }
 
+// co-resident clusters of K CTAs of the pc-DM kernel, taken for its largest shared-memory variant
+template <int M>
+static cudaError_t dm_slots_t(int K, int* slots) {
+  auto kern = pc_fused_kernel<M, false, 15, false, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M, 15>::BYTES);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)K);
+  cfg.blockDim = dim3(FusedShape<M>::TR);
+  cfg.dynamicSmemBytes = FusedSmem<M, 15>::BYTES;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+  *slots = n;
+  return e;
+}
+
+cudaError_t fused_dm_max_slots(int M, int K, int* slots) {
+  switch (M) {
+    case 8: return dm_slots_t<8>(K, slots);
+    case 16: return dm_slots_t<16>(K, slots);
+    case 32: return dm_slots_t<32>(K, slots);
+    case 64: return dm_slots_t<64>(K, slots);
+    case 128: return dm_slots_t<128>(K, slots);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // this translation unit's bounded-wait flag (read and cleared)
 cudaError_t fused_dm_timed_out(bool* out) {
   int h = 0;

@@ -176,3 +176,52 @@ def time_to_nrmse(params: dict, intensities, clean, positions, obj, probe, sigma
     rec.close()
     ev.close()
     return dict(iterations=it, engine_ms=ms, reached=curve[-1][1] <= target, curve=curve)
+
+
+def time_to_nrmse_batch(members, target: float = 0.05, max_iter: int = 100) -> dict:
+    """time_to_nrmse for several reconstructions iterated together as one batch plan (one CUDA
+    graph launch per iteration, one persistent work-queue launch per shape class).
+
+    members: sequence of dict(params, intensities, clean, positions, obj, probe, sigma_eval) as the
+    arguments of time_to_nrmse. The batch iterates until every member's intensity NRMSE against its
+    noise-free patterns reaches `target` (members that got there keep iterating with the others).
+    The evaluation runs on copies through one plan per member and is not timed; the batch's device
+    time per iteration is (CUDA events on its stream). Returns dict(iterations, engine_ms, reached,
+    curves=[[(iteration, nrmse)] per member])."""
+    import torch
+
+    from .engine import Reconstruction, ReconstructionBatch
+
+    evs = []
+    for m in members:
+        s = m["sigma_eval"]
+        ev_params = dict(m["params"], blur_domain="intensity", sigma1=s, sigma2=s, kernel_size=eval_kernel_size(s),
+                         probe_update_start=1 << 30, windows=[], start_iteration=1)
+        evs.append(Reconstruction(ev_params, m["clean"], m["positions"]))
+    batch = ReconstructionBatch([(m["params"], m["intensities"], m["positions"]) for m in members])
+    objs, prbs = [m["obj"] for m in members], [m["probe"] for m in members]
+
+    def nrmse():
+        out = []
+        for ev, o, p in zip(evs, objs, prbs):
+            oc, pc = o.clone(), p.clone()
+            ev.iterate(oc, pc, 1)
+            out.append(ev.error())
+        return out
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    curves = [[(0, e)] for e in nrmse()]
+    ms, it = 0.0, 0
+    while max(c[-1][1] for c in curves) > target and it < max_iter:
+        e0.record(batch.stream)
+        batch.iterate(objs, prbs, 1)
+        e1.record(batch.stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        it += 1
+        for c, e in zip(curves, nrmse()):
+            c.append((it, e))
+    batch.close()
+    for ev in evs:
+        ev.close()
+    return dict(iterations=it, engine_ms=ms, reached=max(c[-1][1] for c in curves) <= target, curves=curves)

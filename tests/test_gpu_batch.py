@@ -202,7 +202,8 @@ def test_configuration3_shaped_batch_against_the_oracle():
     largest N (1539 positions of 128^2, K = 4, far field), two M = 256 members (near and far field,
     staged passes), and M = 64 / 128 members of both geometries with K 1-4, random sigma, iterated
     together (one graph launch per iteration, one queued launch per shape class). Every member
-    against the oracle: rel. L2 and per-pixel bounds of O and P, and its last E."""
+    against the oracle: rel. L2 bounds of O and P, per-pixel bounds of O over the illuminated field
+    of view (as in test_gpu_parity.py) and of P, and its last E."""
     from synth.generators import make_cfg3_member
 
     dev = torch.device("cuda:0")
@@ -215,11 +216,14 @@ def test_configuration3_shaped_batch_against_the_oracle():
     assert sum(p.params["M"] == 256 for p, _ in probs) == 2
     n_iter = 2
     O, P, E = _run_batch(dev, probs, n_iter)
+    from fov import fov_mask
+
     for b, (prob, prm) in enumerate(probs):
         Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), n_iter)
         eo = np.linalg.norm(O[b] - Oo) / np.linalg.norm(Oo)
         ep = np.linalg.norm(P[b] - Po) / np.linalg.norm(Po)
-        mo = np.max(np.abs(O[b] - Oo)) / np.max(np.abs(Oo))
+        fov = fov_mask(prob.positions, prob.P0, Oo.shape, prm["M"])
+        mo = np.max(np.abs(O[b] - Oo)[fov]) / np.max(np.abs(Oo)[fov])
         mp = np.max(np.abs(P[b] - Po)) / np.max(np.abs(Po))
         ee = abs(E[b] - Eo[-1]) / Eo[-1]
         print(f"[parity] configuration-3 member {members[b]} (M={prm['M']} K={prm['K']} N={prm['N']} "
