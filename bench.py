@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-nrmse", action="store_true",
+                    help="skip the warm-start time-to-NRMSE record that the benchmark workload's line carries")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="far128x4",
                     help="far128x4: the benchmark workload; the others for reference runs")
     return ap.parse_args()
@@ -514,6 +516,13 @@ def run_ours_batch(args):
     per_step_s = t_max / args.steps / 1e3
     achieved = flops / per_step_s / 1e12
     peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # the metric's second half: time to NRMSE <= 0.05, plain engine against warm start + batching
+    ttn = None
+    if rank == 0 and ws == 1 and _WORKLOAD == "far128x4" and not args.no_time_to_nrmse:
+        try:
+            ttn = warmstart_record(args, dev, local)
+        except Exception as exc:  # the throughput line is still reported
+            ttn = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -542,112 +551,195 @@ def conv_forward_flops(S, C):
     return sum(2.0 * h * h * 9 * ci * co for h, ci, co in layers)
 
 
+WARM_BATCH_SEEDS = (4, 5, 6, 7)  # the batched comparison: four crystals of the variant
+WARM_TARGET = 0.05
+
+
+def _warm_problem(dev, seed, dose, peak):
+    import torch
+
+    from synth import make_problem
+
+    pb = make_problem(4, seed=seed, dose=dose, peak=peak)
+    prm = dict(pb.params)
+    prm.pop("n_iter", None)
+    M = prm["M"]
+    return dict(pb=pb, prm=prm, M=M, s_true=pb.sim_sigma, I=torch.from_numpy(pb.I).to(dev),
+                Ic=torch.from_numpy(pb.I_clean.astype(np.float32)).to(dev), pos=pb.positions.astype(np.int32),
+                P0=torch.from_numpy(pb.P0.reshape(1, M, M)).to(dev))
+
+
+def _engine(prm, sig):
+    from paper_2406_06640_gb300.warmstart import eval_kernel_size
+
+    return dict(prm, blur_domain="intensity", sigma1=sig, sigma2=sig, kernel_size=eval_kernel_size(sig))
+
+
+def warmstart_record(args, dev, local, with_clocks=True):
+    """Time to intensity NRMSE <= 0.05 against the noise-free patterns: the plain FP32 engine from a
+    flat start (given the true sigma) against the learned warm start (U-Net over 64 sampled patterns,
+    stitched object, median sigma), for one reconstruction and for four run as one batch plan; and the
+    stated electron workload, where the comparison is degenerate, with the fallback target."""
+    import torch
+
+    from paper_2406_06640_gb300.warmstart import (LatticeSpec, WarmStart, WarmStartConfig, subsample_scan,
+                                                  time_to_nrmse, time_to_nrmse_batch)
+
+    n_train, spacing = 200_000, 16.0
+    rec = {"target": WARM_TARGET, "train_patterns": n_train, "sampled_patterns_per_reconstruction": None}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def estimate_timed(net, w, idx):
+        Isub = w["I"][torch.from_numpy(idx).to(dev)].contiguous()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        Ow, sig = net.estimate(Isub, w["pos"][idx], w["prm"]["obj_h"], w["prm"]["obj_w"])
+        e1.record()
+        e1.synchronize()
+        return Ow, sig, e0.elapsed_time(e1)
+
+    # ---- variant: 1.0 rad peaks, 2e4 counts per pattern
+    probs = [_warm_problem(dev, sd, 2e4, 1.0) for sd in WARM_BATCH_SEEDS]
+    w0 = probs[0]
+    net = WarmStart(w0["P0"][0], WarmStartConfig(S=w0["M"], C=32, batch=64, dose=2e4, target_scale=1.0,
+                                                  lattice=LatticeSpec(peak=1.0), seed=1))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    net.train(n_train)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    idxs = [subsample_scan(w["pos"], spacing) for w in probs]
+    rec["sampled_patterns_per_reconstruction"] = len(idxs[0])
+    for _ in range(max(args.warmup, 3)):
+        estimate_timed(net, w0, idxs[0])
+    sampler = ClockSampler(local) if with_clocks else None
+    if sampler:
+        sampler.start()
+    plain, warm, est_ms = [], [], []
+    for _ in range(max(args.steps // 4, 3)):
+        O = torch.ones(w0["prm"]["obj_h"], w0["prm"]["obj_w"], dtype=torch.complex64, device=dev)
+        plain.append(time_to_nrmse(_engine(w0["prm"], w0["s_true"]), w0["I"], w0["Ic"], w0["pos"], O, w0["P0"].clone(),
+                                   w0["s_true"], WARM_TARGET))
+        Ow, sig, ms = estimate_timed(net, w0, idxs[0])
+        est_ms.append(ms)
+        warm.append(time_to_nrmse(_engine(w0["prm"], sig), w0["I"], w0["Ic"], w0["pos"], Ow.clone(), w0["P0"].clone(),
+                                  w0["s_true"], WARM_TARGET))
+    # batched: the four reconstructions run plain one after another, against warm starts + one batch plan
+    plain_b, warm_b = [], []
+    for w in probs:
+        O = torch.ones(w["prm"]["obj_h"], w["prm"]["obj_w"], dtype=torch.complex64, device=dev)
+        plain_b.append(time_to_nrmse(_engine(w["prm"], w["s_true"]), w["I"], w["Ic"], w["pos"], O, w["P0"].clone(),
+                                     w["s_true"], WARM_TARGET))
+    members, est_b = [], []
+    for w, idx in zip(probs, idxs):
+        Ow, sig, ms = estimate_timed(net, w, idx)
+        est_b.append(ms)
+        members.append(dict(params=_engine(w["prm"], sig), intensities=w["I"], clean=w["Ic"], positions=w["pos"],
+                            obj=Ow.clone(), probe=w["P0"].clone(), sigma_eval=w["s_true"]))
+    rb = time_to_nrmse_batch(members, WARM_TARGET)
+    clocks = sampler.stop() if sampler else None
+    # end to end through the public calls: the sampled patterns from pinned host memory, object back
+    hI = w0["I"][torch.from_numpy(idxs[0]).to(dev)].cpu().pin_memory()
+    hO = torch.empty(w0["prm"]["obj_h"], w0["prm"]["obj_w"], dtype=torch.complex64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    dI = hI.to(dev, non_blocking=True)
+    Ow, _ = net.estimate(dI, w0["pos"][idxs[0]], w0["prm"]["obj_h"], w0["prm"]["obj_w"])
+    hO.copy_(Ow, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_ms = 1e3 * (time.perf_counter() - t0)
+    net.close()
+    plain_ms = float(np.median([r["engine_ms"] for r in plain]))
+    warm_eng = float(np.median([r["engine_ms"] for r in warm]))
+    est = float(np.median(est_ms))
+    warm_ms = est + warm_eng
+    fwd_flops = conv_forward_flops(w0["M"], 32) * len(idxs[0])
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        peak_src = "measured bf16 burst (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 1900.0, "fallback bf16 burst"
+    achieved = fwd_flops / (est / 1e3) / 1e12
+    plain_b_ms = float(sum(r["engine_ms"] for r in plain_b))
+    warm_b_ms = float(sum(est_b)) + rb["engine_ms"]
+    rec["variant"] = {
+        "workload": "electron-like crystal with 1.0 rad peaks at 2e4 counts per pattern (probe 128^2, 64x64 raster "
+                    "step 2 px, object 256^2, sigma 2), engine with the intensity-blur model of Eq. 2",
+        "plain_ms": plain_ms, "warm_ms": warm_ms, "warm_estimate_ms": est, "warm_engine_ms": warm_eng,
+        "gain": plain_ms / warm_ms,
+        "plain_iterations": [r["iterations"] for r in plain], "warm_iterations": [r["iterations"] for r in warm],
+        "reached": all(r["reached"] for r in plain + warm),
+        "nrmse_flat_start": plain[0]["curve"][0][1], "nrmse_warm_start": warm[0]["curve"][0][1],
+        "plain_curve": [round(c[1], 4) for c in plain[0]["curve"]],
+        "warm_curve": [round(c[1], 4) for c in warm[0]["curve"]],
+        "sigma_true": w0["s_true"], "train_s": t_train, "train_patterns_per_s": n_train / t_train,
+        "batched": {"reconstructions": len(probs), "plain_sequential_ms": plain_b_ms,
+                    "warm_estimates_ms": float(sum(est_b)), "warm_batch_engine_ms": rb["engine_ms"],
+                    "warm_batched_ms": warm_b_ms, "gain": plain_b_ms / warm_b_ms,
+                    "plain_iterations": [r["iterations"] for r in plain_b], "batch_iterations": rb["iterations"],
+                    "reached": all(r["reached"] for r in plain_b) and rb["reached"]},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "peak_basis": peak_src,
+                     "kernel": f"U-Net forward over {len(idxs[0])} patterns (warm-start estimate, all launches)",
+                     "flops_per_launch": fwd_flops},
+        "e2e": {"value": e2e_ms + warm_eng, "unit": "ms", "h2d_bytes_per_step": hI.numel() * 4,
+                "d2h_bytes_per_step": hO.numel() * 8},
+        "clocks": clocks}
+
+    # ---- the stated electron workload (0.1 rad peaks, 200 counts): the flat start already lies below 0.05 and
+    # the plain engine moves away from it, so the target is 0.05 above the plain engine's plateau
+    w4 = _warm_problem(dev, 4, 200.0, 0.1)
+    O = torch.ones(w4["prm"]["obj_h"], w4["prm"]["obj_w"], dtype=torch.complex64, device=dev)
+    run = time_to_nrmse(_engine(w4["prm"], w4["s_true"]), w4["I"], w4["Ic"], w4["pos"], O, w4["P0"].clone(),
+                        w4["s_true"], -1.0, max_iter=20)
+    curve = [c[1] for c in run["curve"]]
+    plateau = float(np.mean(curve[-2:]))  # the iterates alternate; the mean of the last two
+    fallback = plateau + WARM_TARGET
+    net4 = WarmStart(w4["P0"][0], WarmStartConfig(S=w4["M"], C=32, batch=64, dose=200.0, target_scale=0.1,
+                                                   lattice=LatticeSpec(peak=0.1), seed=1))
+    net4.train(n_train)
+    idx4 = subsample_scan(w4["pos"], spacing)
+    for _ in range(2):
+        estimate_timed(net4, w4, idx4)
+    Ow4, sig4, est4 = estimate_timed(net4, w4, idx4)
+    net4.close()
+    warm4 = time_to_nrmse(_engine(w4["prm"], sig4), w4["I"], w4["Ic"], w4["pos"], Ow4.clone(), w4["P0"].clone(),
+                          w4["s_true"], -1.0, max_iter=2)
+    first = lambda cv, t: next((i for i, v in enumerate(cv) if v <= t), None)  # noqa: E731
+    it_plain = first(curve, fallback)
+    it_warm = first([c[1] for c in warm4["curve"]], fallback)
+    per_it = run["engine_ms"] / max(run["iterations"], 1)
+    rec["configuration4_as_stated"] = {
+        "workload": "electron-like crystal, 0.1 rad peaks, 200 counts per pattern (as stated)",
+        "nrmse_flat_start": curve[0], "plain_curve": [round(v, 4) for v in curve], "plain_plateau": plateau,
+        "target": "0.05 above the plain plateau (0.05 lies below the flat start's value, which the engine only "
+                  "moves away from)", "target_value": fallback,
+        "plain_iterations": it_plain, "plain_ms": None if it_plain is None else it_plain * per_it,
+        "nrmse_warm_start": warm4["curve"][0][1], "warm_iterations": it_warm,
+        "warm_ms": None if it_warm is None else est4 + it_warm * per_it,
+        "sigma_est": sig4, "sigma_true": w4["s_true"]}
+    return rec
+
+
 def run_ours_warmstart(args):
     """Learned warm start vs flat start: time to NRMSE <= 0.05 (one GPU; replicas only for N > 1)."""
     ws, rank, local = dist_setup(args)
     import torch
 
-    from paper_2406_06640_gb300.warmstart import (LatticeSpec, WarmStart, WarmStartConfig, eval_kernel_size,
-                                                  subsample_scan, time_to_nrmse)
-    from synth import make_problem
-
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    n_train, spacing, target = 200_000, 16.0, 0.05
-    out = {}
-    for case, dose, peak in (("variant", 2e4, 1.0), ("config4", 200.0, 0.1)):
-        pb = make_problem(4, dose=dose, peak=peak)
-        prm = dict(pb.params)
-        prm.pop("n_iter", None)
-        M, s_true = prm["M"], pb.sim_sigma
-        I = torch.from_numpy(pb.I).to(dev)
-        Ic = torch.from_numpy(pb.I_clean.astype(np.float32)).to(dev)
-        pos = pb.positions.astype(np.int32)
-        P0 = torch.from_numpy(pb.P0.reshape(1, M, M)).to(dev)
-
-        def engine(sig):
-            return dict(prm, blur_domain="intensity", sigma1=sig, sigma2=sig, kernel_size=eval_kernel_size(sig))
-
-        net = WarmStart(P0[0], WarmStartConfig(S=M, C=32, batch=64, dose=dose, target_scale=peak,
-                                               lattice=LatticeSpec(peak=peak), seed=1))
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        net.train(n_train)
-        torch.cuda.synchronize(dev)
-        t_train = time.perf_counter() - t0
-        idx = subsample_scan(pos, spacing)
-        Isub = I[torch.from_numpy(idx).to(dev)].contiguous()
-        for _ in range(max(args.warmup, 3)):
-            net.estimate(Isub, pos[idx], prm["obj_h"], prm["obj_w"])
-        plain, warm, est_ms, sig_est = [], [], [], None
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        sampler = ClockSampler(local) if (rank == 0 and case == "variant") else None
-        if sampler:
-            sampler.start()
-        for _ in range(args.steps if case == "variant" else 1):
-            O = torch.ones(prm["obj_h"], prm["obj_w"], dtype=torch.complex64, device=dev)
-            plain.append(time_to_nrmse(engine(s_true), I, Ic, pos, O, P0.clone(), s_true, target))
-            torch.cuda.synchronize(dev)
-            e0.record()
-            Ow, sig_est = net.estimate(Isub, pos[idx], prm["obj_h"], prm["obj_w"])
-            e1.record()
-            e1.synchronize()
-            est_ms.append(e0.elapsed_time(e1))
-            warm.append(time_to_nrmse(engine(sig_est), I, Ic, pos, Ow.clone(), P0.clone(), s_true, target))
-        clocks = sampler.stop() if sampler else None
-        # end to end through the public calls: sampled patterns from pinned host memory, object back
-        hI = Isub.cpu().pin_memory()
-        hO = torch.empty(prm["obj_h"], prm["obj_w"], dtype=torch.complex64).pin_memory()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        dI = hI.to(dev, non_blocking=True)
-        Ow, _ = net.estimate(dI, pos[idx], prm["obj_h"], prm["obj_w"])
-        hO.copy_(Ow, non_blocking=True)
-        torch.cuda.synchronize(dev)
-        e2e_ms = 1e3 * (time.perf_counter() - t0)
-        net.close()
-        out[case] = dict(plain=plain, warm=warm, est_ms=est_ms, sigma_est=sig_est, sigma_true=s_true,
-                         t_train=t_train, n_sub=len(idx), clocks=clocks, e2e_ms=e2e_ms,
-                         h2d=hI.numel() * 4, d2h=hO.numel() * 8)
-    v = out["variant"]
-    plain_ms = float(np.median([r["engine_ms"] for r in v["plain"]]))
-    warm_ms = float(np.median([e + r["engine_ms"] for e, r in zip(v["est_ms"], v["warm"])]))
-    est = float(np.median(v["est_ms"]))
-    fwd_flops = conv_forward_flops(128, 32) * v["n_sub"]
-    peak = None
-    try:
-        peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))[
-            "bf16_tflops"]
-    except (OSError, KeyError, ValueError):
-        peak = 1900.0
-    achieved = fwd_flops / (est / 1e3) / 1e12
-    c4 = out["config4"]
+    rec = warmstart_record(args, dev, local, with_clocks=rank == 0)
     if rank == 0:
-        line = {"metric": "time to NRMSE <= 0.05 (warm start)", "value": warm_ms, "unit": "ms",
-                "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": warm_ms,
+        v = rec["variant"]
+        line = {"metric": "time to NRMSE <= 0.05 (warm start)", "value": v["warm_ms"], "unit": "ms",
+                "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": v["warm_ms"],
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOADS["warmstart"][1], "train_patterns": n_train,
-                           "sampled_patterns": v["n_sub"], "target": target,
+                "config": {"workload": WORKLOADS["warmstart"][1], "train_patterns": rec["train_patterns"],
+                           "sampled_patterns": rec["sampled_patterns_per_reconstruction"], "target": WARM_TARGET,
                            "l2": "inputs resident; each measurement starts from a fresh object"},
-                "plain_ms": plain_ms, "gain": plain_ms / warm_ms,
-                "plain_iterations": [r["iterations"] for r in v["plain"]],
-                "warm_iterations": [r["iterations"] for r in v["warm"]],
-                "warm_estimate_ms": est, "nrmse_flat_start": v["plain"][0]["curve"][0][1],
-                "nrmse_warm_start": v["warm"][0]["curve"][0][1],
-                "sigma_est": v["sigma_est"], "sigma_true": v["sigma_true"], "train_s": v["t_train"],
-                "train_patterns_per_s": n_train / v["t_train"],
-                "config4": {"sigma_est": c4["sigma_est"], "sigma_true": c4["sigma_true"],
-                            "nrmse_flat_start": c4["plain"][0]["curve"][0][1],
-                            "nrmse_warm_start": c4["warm"][0]["curve"][0][1], "train_s": c4["t_train"]},
-                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None,
-                             "kernel": f"U-Net forward over {v['n_sub']} patterns (warm-start estimate)",
-                             "flops_per_launch": fwd_flops},
-                "cpu_baseline": None,
-                "e2e": {"value": v["e2e_ms"] + float(np.median([r["engine_ms"] for r in v["warm"]])),
-                        "unit": "ms", "h2d_bytes_per_step": v["h2d"], "d2h_bytes_per_step": v["d2h"]},
-                "gpu_launches": None, "clocks": v["clocks"]}
+                "roofline": v["roofline"], "cpu_baseline": None, "e2e": v["e2e"], "gpu_launches": None,
+                "clocks": v["clocks"], "time_to_nrmse": rec}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -710,6 +802,10 @@ def run_ours(args):
     achieved = flops / fused_avg_s / 1e12
     peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     traffic = traffic_record(kernel_source_hash()) if _WORKLOAD == "far128x4" else None
+    # the FP32 FMA rate measured on this device, beside the nominal peak (units x maximum clock)
+    from paper_2406_06640_gb300.binding import measure_fp32_peak
+
+    peak_meas, peak_meas_ms = measure_fp32_peak(stream.cuda_stream)
 
     # end to end through the public API: object + probe state from pinned host memory, one
     # iteration, error metric and state back to pinned host memory, every step
@@ -740,6 +836,13 @@ def run_ours(args):
         cpu = {"value": rate, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
                "sample": f"one FP64 oracle iteration of the full workload ({prob.N} positions x {prob.K} modes, "
                          f"{dt:.1f} s, numpy/scipy single-threaded)"}
+    # the metric's second half: time to NRMSE <= 0.05, plain engine against warm start + batching
+    ttn = None
+    if rank == 0 and ws == 1 and _WORKLOAD == "far128x4" and not args.no_time_to_nrmse:
+        try:
+            ttn = warmstart_record(args, dev, local)
+        except Exception as exc:  # the throughput line is still reported
+            ttn = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -752,12 +855,16 @@ def run_ours(args):
                              "frac": achieved / peak, "traffic": traffic,
                              "kernel": kernel_label(prob, params),
                              "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FMA pipe, max clock)",
+                             "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas,
+                             "peak_measured_basis": f"FFMA loop on this device, CUDA events, {peak_meas_ms:.3f} ms",
                              "flops_per_launch": flops, "avg_launch_ms": fused_avg_s * 1e3},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes + 8},
                 "gpu_launches": args.steps * rec.launches_per_iteration(True),
                 "clocks": clocks, "nrmse_last": E_last, "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
+        if ttn is not None:
+            line["time_to_nrmse"] = ttn
         print(json.dumps(line), flush=True)
     rec.close()
     if ws > 1:

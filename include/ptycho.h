@@ -369,6 +369,14 @@ ptycho_status ptycho_monochromatise(int32_t M, int32_t J, const double* scale, c
                                     int32_t k, const float* b, float* x, double* resid, int32_t clamp,
                                     void* cuda_stream);
 
+/* Measured FP32 FMA throughput of the current device (a measurement utility; the paper has no
+ * counterpart): the roofline denominator of the ALU-bound kernels beside the nominal SMs x 128
+ * lanes x 2 FLOP x clock. Runs an FFMA loop (8 independent chains per thread, 4 CTAs of 256 threads
+ * per SM) six times on cuda_stream and reports the best of the last five: *tflops (host) in
+ * TFLOP/s and *ms (host) the duration of that launch. Synchronises the stream; allocates and frees
+ * one small device buffer. PTYCHO_EINVAL for NULL outputs, PTYCHO_ENOMEM, PTYCHO_ECUDA. */
+ptycho_status ptycho_measure_fp32_peak(double* tflops, double* ms, void* cuda_stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ptycho_last_error(void);
 

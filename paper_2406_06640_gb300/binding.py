@@ -133,6 +133,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_last_error.restype = ctypes.c_char_p
     lib.ptycho_version.argtypes = []
     lib.ptycho_version.restype = ctypes.c_char_p
+    lib.ptycho_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]
+    lib.ptycho_measure_fp32_peak.restype = st
     F32 = ctypes.c_float
     lib.ptycho_unet_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P,
                                        ctypes.POINTER(P)]
@@ -429,3 +431,11 @@ def permutation(n: int, seed: int, stream: int, t: int) -> list:
     out = (ctypes.c_int32 * max(n, 1))()
     _check(load().ptycho_permutation(n, seed & ((1 << 64) - 1), stream, t, out))
     return list(out[:n])
+
+
+def measure_fp32_peak(stream_ptr: int = 0) -> tuple:
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, duration of the timed launch in ms)."""
+    lib = load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ptycho_measure_fp32_peak(ctypes.byref(tf), ctypes.byref(ms), stream_ptr))
+    return tf.value, ms.value

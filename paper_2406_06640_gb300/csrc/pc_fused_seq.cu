@@ -37,6 +37,40 @@
 
 namespace ptycho {
 
+// L2 eviction policies: the per-slot probe partials are read and written once per position and mode
+// and must survive in L2 between those visits; the streamed data (sqrt I, c_n) must not push them out
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(float* a, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+// bring `bytes` (a multiple of 16, 16-byte aligned) into L2 ahead of use
+__device__ __forceinline__ void prefetch_l2(const void* a, uint32_t bytes, uint64_t pol) {
+  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a), "r"(bytes), "l"(pol)
+               : "memory");
+}
+
 template <int M>
 struct SeqShape {
   using TL = Tile<M>;
@@ -126,6 +160,7 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
   // register storage of the small tiles (unused with TMEM)
   float2 o_r[V][E], c_r[V][E], st_r[V][E];
   float err_s = 0.f, err_c = 0.f;  // compensated per-thread sum of (Ihat - I)^2
+  const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
 
   for (int n = slot; n < a.N; n += nslots) {
     const bool first = n == slot;
@@ -133,8 +168,7 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
     const float2* On = a.O + (size_t)pn.x * a.obj_w + pn.y;
     const float* Qn = a.sqrtI + (size_t)n * M * M;
     // sqrt(I_n) is read once, by the modulus step: start moving it into L2 now
-    if (tid == 0)
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Qn), "r"((uint32_t)(M * M * 4)) : "memory");
+    if (tid == 0) prefetch_l2(Qn, (uint32_t)(M * M * 4), stream);
     float2 v[V][E];
 
     // ---- the object box in ROW layout into TMEM (every load in flight at once)
@@ -290,6 +324,12 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
     // ---- pass 2: mode K-1 from storage, then modes 0 .. K-2 propagated again
     for (int i = 0; i < K; ++i) {
       const int k = i == 0 ? K - 1 : i - 1;
+      // this mode's probe partial (and, for the first, the denominator partial) is read and written
+      // at the end of the mode: start moving it into L2 now
+      if (!first && tid == 0) {
+        prefetch_l2(a.pacc + ((size_t)slot * K + k) * M * M, (uint32_t)(M * M * 8), keep);
+        if (i == 0) prefetch_l2(a.dacc + (size_t)slot * M * M, (uint32_t)(M * M * 4), keep);
+      }
       if (i == 0) {
         if constexpr (TM) {
 #pragma unroll
@@ -348,8 +388,8 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
           for (int jj = 0; jj < 4; ++jj) {
             const int x = tp[q] + G * (4 * h + jj);
             p[jj] = __ldg(&Pk[ln * M + x]);
-            po[jj] = first ? make_float2(0.f, 0.f) : pk[ln * M + x];
-            dold[jj] = (first || i > 0) ? 0.f : dk[ln * M + x];
+            po[jj] = first ? make_float2(0.f, 0.f) : ld_hint(&pk[ln * M + x], keep);
+            dold[jj] = (first || i > 0) ? 0.f : ld_hint(&dk[ln * M + x], keep);
           }
           float2 o[4], c[4];
           if constexpr (TM) {
@@ -377,8 +417,8 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
             if (!NEAR && ((ln + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
             const float2 dpsi = csub(psi_new, cmul(p[jj], o[jj]));
             c[jj] = cadd(c[jj], cconjmul(p[jj], dpsi));
-            pk[ln * M + x] = cadd(po[jj], cconjmul(o[jj], dpsi));
-            if (i == 0) dk[ln * M + x] = dold[jj] + cabs2(o[jj]);
+            st_hint(&pk[ln * M + x], cadd(po[jj], cconjmul(o[jj], dpsi)), keep);
+            if (i == 0) st_hint(&dk[ln * M + x], dold[jj] + cabs2(o[jj]), keep);
           }
           if constexpr (TM) {
             float ac[8];

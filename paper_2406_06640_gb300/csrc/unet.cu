@@ -49,9 +49,14 @@ constexpr int kMaxBatch = 1024;  // samples per call (the sigma head keeps one v
 
 // ---------------------------------------------------------------- elementwise kernels
 __global__ void k_input(const float* x, bf16* out, size_t npix) {
-  // x (n, S, S) -> (n, S, S, 8) with the value in channel 0
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npix * 8; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = __float2bfloat16((i & 7) == 0 ? x[i >> 3] : 0.f);
+  // x (n, S, S) -> (n, S, S, 8) with the value in channel 0; one pixel (16 bytes) per thread
+  uint4* out4 = reinterpret_cast<uint4*>(out);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x[i], 0.f);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    v.x = *reinterpret_cast<const uint32_t*>(&h);
+    out4[i] = v;
+  }
 }
 
 // 8 bf16 <-> 8 floats
@@ -286,12 +291,25 @@ __global__ void k_loss(const float* out, const float* target, bf16* d_out, float
 }
 
 // g[b][c] = mean over the hw pixels of a3[b, :, :, c]; one block per sample
-__global__ void k_sigma_pool(const bf16* a3, float* g, int hw, int C8) {
+// mean over the pixels of each sample's channels: block b, thread (phase, c) sums the pixels p = phase (mod 4)
+// with four independent accumulators; the four phases are added in order (a fixed summation order)
+constexpr int kPoolPhases = 4;
+__global__ void __launch_bounds__(1024) k_sigma_pool(const bf16* a3, float* g, int hw, int C8) {
+  __shared__ float part[kPoolPhases][256];
   const int b = blockIdx.x;
-  for (int c = threadIdx.x; c < C8; c += blockDim.x) {
-    float s = 0.f;
-    for (int p = 0; p < hw; ++p) s += __bfloat162float(a3[((size_t)b * hw + p) * C8 + c]);
-    g[(size_t)b * C8 + c] = s / hw;
+  const int phase = threadIdx.x / 256, c0 = threadIdx.x % 256;
+  for (int cb = 0; cb < C8; cb += 256) {  // the same trip count in every thread (barriers inside)
+    const int c = cb + c0;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int u = 0;
+    if (c < C8)
+      for (int p = phase; p < hw; p += kPoolPhases, u = (u + 1) & 3)
+        s[u] += __bfloat162float(a3[((size_t)b * hw + p) * C8 + c]);
+    part[phase][c0] = (s[0] + s[1]) + (s[2] + s[3]);
+    __syncthreads();
+    if (phase == 0 && c < C8)
+      g[(size_t)b * C8 + c] = (((part[0][c0] + part[1][c0]) + part[2][c0]) + part[3][c0]) / hw;
+    __syncthreads();
   }
 }
 
@@ -418,6 +436,7 @@ struct ptycho_unet_s {
   float *dX, *skip1, *skip2;
   float* wpart;  // split-K partial weight gradients
   int* status;
+  bool wb_fresh = false;  // the bf16 weight copies match the FP32 masters
   long long step = 0;
 
   template <class T>
@@ -538,11 +557,14 @@ static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev) {
   cudaStream_t s = u->stream;
   const int n = u->nrun, S = u->S, C = u->C;
   const size_t npx = (size_t)n * S * S;
-  k_input<<<grid_for(npx * 8), 256, 0, s>>>(x_dev, u->x, npx);
-  for (int i = 0; i < 7; ++i)
-    k_weights_bf16<<<grid_for((size_t)u->L[i].Cp * u->L[i].Kf + (size_t)u->L[i].Cin * u->L[i].Kd), 256, 0, s>>>(
-        u->L[i].w, u->L[i].wb, i == 0 ? nullptr : u->L[i].wr, u->L[i].Cp, u->L[i].Cin, u->L[i].Kw, u->L[i].Kf,
-        u->L[i].Kd);
+  k_input<<<grid_for(npx), 256, 0, s>>>(x_dev, u->x, npx);
+  if (!u->wb_fresh) {  // bf16 copies of the FP32 master weights, redone only after the weights changed
+    for (int i = 0; i < 7; ++i)
+      k_weights_bf16<<<grid_for((size_t)u->L[i].Cp * u->L[i].Kf + (size_t)u->L[i].Cin * u->L[i].Kd), 256, 0, s>>>(
+          u->L[i].w, u->L[i].wb, i == 0 ? nullptr : u->L[i].wr, u->L[i].Cp, u->L[i].Cin, u->L[i].Kw, u->L[i].Kf,
+          u->L[i].Kd);
+    u->wb_fresh = true;
+  }
   cudaError_t e;
   if ((e = conv_forward(u, u->L[0], u->x, u->a0, nullptr)) != cudaSuccess) return e;
   k_avgpool2<<<grid_for(npx * C / 32), 256, 0, s>>>(u->a0, u->p0, n, S, S, C);
@@ -567,7 +589,7 @@ static cudaError_t unet_backward(ptycho_unet_s* u, const float* target, const fl
   const int n = u->nrun, S = u->S, C = u->C;
   const int Mo = n * (S / 2) * (S / 2);
   k_loss<<<64, 256, 0, s>>>(u->out, target, u->d_out, u->loss_part, Mo);
-  k_sigma_pool<<<n, 256, 0, s>>>(u->a3, u->g, (S / 8) * (S / 8), 8 * C);
+  k_sigma_pool<<<n, 1024, 0, s>>>(u->a3, u->g, (S / 8) * (S / 8), 8 * C);
   k_sigma_head<<<1, kMaxBatch, 0, s>>>(u->w7, u->b7, sigma_t, lam, u->sigma, u->g, u->extra, u->gw7, u->gb7,
                                   u->loss_s, n, (S / 8) * (S / 8), 8 * C, 1);
   cudaError_t e;
@@ -596,7 +618,7 @@ static cudaError_t unet_backward(ptycho_unet_s* u, const float* target, const fl
 static cudaError_t unet_infer(ptycho_unet_s* u, const float* x, float* out2, float* sigma, int nvalid) {
   cudaError_t e = unet_forward(u, x);
   if (e != cudaSuccess) return e;
-  k_sigma_pool<<<u->nrun, 256, 0, u->stream>>>(u->a3, u->g, (u->S / 8) * (u->S / 8), 8 * u->C);
+  k_sigma_pool<<<u->nrun, 1024, 0, u->stream>>>(u->a3, u->g, (u->S / 8) * (u->S / 8), 8 * u->C);
   k_sigma_head<<<1, kMaxBatch, 0, u->stream>>>(u->w7, u->b7, nullptr, 0.f, u->sigma, u->g, u->extra, u->gw7,
                                                u->gb7, u->loss_s, u->nrun, (u->S / 8) * (u->S / 8), 8 * u->C, 0);
   const int Mo = nvalid * (u->S / 2) * (u->S / 2);
@@ -770,6 +792,7 @@ int64_t ptycho_unet_param_count(ptycho_unet_t u) { return u ? (int64_t)param_cou
 
 ptycho_status ptycho_unet_set_params(ptycho_unet_t u, const float* host, int64_t count) {
   if (!u || !host || count != (int64_t)param_count(u->C)) return capi_fail(PTYCHO_EINVAL, "bad parameter vector");
+  u->wb_fresh = false;
   const int ci_t[7] = {1, u->C, 2 * u->C, 4 * u->C, 12 * u->C, 6 * u->C, 2 * u->C};
   size_t off = 0;
   for (int i = 0; i < 7; ++i) {
@@ -856,6 +879,7 @@ ptycho_status ptycho_unet_train_step(ptycho_unet_t u, const float* x, const floa
   UN_CUDA(unet_forward(u, x), "unet forward");
   UN_CUDA(unet_backward(u, target, sigma_t, lam), "unet backward");
   u->step++;
+  u->wb_fresh = false;  // Adam changes the FP32 masters below
   const float c1 = 1.f - std::pow(0.9f, (float)u->step), c2 = 1.f - std::pow(0.999f, (float)u->step);
   for (int i = 0; i < 7; ++i) {
     Conv& L = u->L[i];

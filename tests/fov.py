@@ -16,3 +16,12 @@ def fov_mask(positions, P, shape, M, frac=DELTA_FOV):
     for y, x in np.asarray(positions):
         D[y:y + M, x:x + M] += P2
     return D >= frac * D.max()
+
+
+def probe_support(P0, frac=DELTA_FOV):
+    """Probe pixels where the starting probe carries at least `frac` of its peak intensity,
+    sum_k |P0_k|^2 >= frac max; outside, the probe is zero by design and its update is the same
+    amplified rounding (the FP64 oracle with single-precision FFTs: 3.3e-4 of max |P| outside on the
+    sparse M = 256 pc-DM scan, 7.6e-6 inside)."""
+    S = np.sum(np.abs(np.asarray(P0)) ** 2, axis=0)
+    return S >= frac * S.max()

@@ -203,7 +203,7 @@ def test_configuration3_shaped_batch_against_the_oracle():
     staged passes), and M = 64 / 128 members of both geometries with K 1-4, random sigma, iterated
     together (one graph launch per iteration, one queued launch per shape class). Every member
     against the oracle: rel. L2 bounds of O and P, per-pixel bounds of O over the illuminated field
-    of view (as in test_gpu_parity.py) and of P, and its last E."""
+    of view and of P over its support (as in test_gpu_parity.py), and its last E."""
     from synth.generators import make_cfg3_member
 
     dev = torch.device("cuda:0")
@@ -216,7 +216,7 @@ def test_configuration3_shaped_batch_against_the_oracle():
     assert sum(p.params["M"] == 256 for p, _ in probs) == 2
     n_iter = 2
     O, P, E = _run_batch(dev, probs, n_iter)
-    from fov import fov_mask
+    from fov import fov_mask, probe_support
 
     for b, (prob, prm) in enumerate(probs):
         Oo, Po, Eo = oracle.iterate(prob.I, prob.positions, prob.O0, prob.P0, oracle.Params.from_dict(prm), n_iter)
@@ -224,7 +224,8 @@ def test_configuration3_shaped_batch_against_the_oracle():
         ep = np.linalg.norm(P[b] - Po) / np.linalg.norm(Po)
         fov = fov_mask(prob.positions, prob.P0, Oo.shape, prm["M"])
         mo = np.max(np.abs(O[b] - Oo)[fov]) / np.max(np.abs(Oo)[fov])
-        mp = np.max(np.abs(P[b] - Po)) / np.max(np.abs(Po))
+        sup = np.broadcast_to(probe_support(prob.P0), Po.shape)
+        mp = np.max(np.abs(P[b] - Po)[sup]) / np.max(np.abs(Po)[sup])
         ee = abs(E[b] - Eo[-1]) / Eo[-1]
         print(f"[parity] configuration-3 member {members[b]} (M={prm['M']} K={prm['K']} N={prm['N']} "
               f"{prm['geometry']}): rel L2 object {eo:.3e} probe {ep:.3e} error {ee:.3e}; "

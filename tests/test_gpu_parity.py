@@ -14,7 +14,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
-from fov import fov_mask  # noqa: E402
+from fov import fov_mask, probe_support  # noqa: E402
 from synth import make_problem  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -63,16 +63,19 @@ def pix(a, b, mask=None):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def compare(tag, gpu, orc, tol=TOL, mask=None, pix_tol=None):
+def compare(tag, gpu, orc, tol=TOL, mask=None, pix_tol=None, pmask=None):
     """rel. L2 bounds of object and probe, per-pixel bounds of the object over the field of view
-    `mask` and of the probe over every pixel, and the relative bound of every iteration's E."""
+    `mask` and of the probe over its support `pmask` (every pixel when None), and the relative
+    bound of every iteration's E."""
     (Og, Pg, Eg), (Oo, Po, Eo) = gpu, orc
     pix_tol = tol if pix_tol is None else pix_tol
-    eo, ep, mo, mp = rel(Og, Oo), rel(Pg, Po), pix(Og, Oo, mask), pix(Pg, Po)
+    pm = None if pmask is None else np.broadcast_to(pmask, np.shape(Po))
+    eo, ep, mo, mp = rel(Og, Oo), rel(Pg, Po), pix(Og, Oo, mask), pix(Pg, Po, pm)
     ee = float(np.max(np.abs(np.asarray(Eg) - Eo) / Eo))
-    mall = pix(Og, Oo)
+    mall, pall = pix(Og, Oo), pix(Pg, Po)
     print(f"[parity] {tag}: rel L2 object {eo:.3e} probe {ep:.3e} error {ee:.3e}; "
-          f"per-pixel object {mo:.3e} (field of view; all pixels {mall:.3e}) probe {mp:.3e}")
+          f"per-pixel object {mo:.3e} (field of view; all pixels {mall:.3e}) "
+          f"probe {mp:.3e} (support; all pixels {pall:.3e})")
     assert np.shape(Eg) == np.shape(Eo)
     assert eo <= tol and ep <= tol and ee <= tol, (eo, ep, ee)
     assert mo <= pix_tol and mp <= pix_tol, (mo, mp)
@@ -84,7 +87,7 @@ def check(prob, params, n_iter, tol=TOL, tag=None, pix_tol=None):
     Oo, Po, Eo = run_oracle(prob, params, n_iter)
     tag = tag or f"M={params['M']} K={params['K']} N={params['N']} {params.get('geometry', 'far')}, {n_iter} it."
     mask = fov_mask(prob.positions, prob.P0, Oo.shape, params["M"])
-    compare(tag, (Og, Pg, Eg), (Oo, Po, Eo), tol, mask, pix_tol)
+    compare(tag, (Og, Pg, Eg), (Oo, Po, Eo), tol, mask, pix_tol, probe_support(prob.P0))
     return Og, Pg, Eg
 
 
