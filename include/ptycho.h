@@ -68,7 +68,7 @@ enum { PTYCHO_STEP_NORMALISED = 0, PTYCHO_STEP_RPIE = 1 };
 enum { PTYCHO_ENGINE_PIE = 0, PTYCHO_ENGINE_DM = 1 };
 
 typedef struct {
-  int32_t M;            /* probe = box = detector side, power of two, 8..256 */
+  int32_t M;            /* probe = box = detector side, power of two, 8..512 */
   int32_t K;            /* probe modes (mixed state, Sec. 4.4), 1..8 */
   int32_t N;            /* scan positions, >= 1 */
   int32_t obj_h, obj_w; /* object size, >= M */
@@ -102,7 +102,7 @@ typedef struct {
    * ptycho_permutation(batches, order_seed, 4, t); each batch takes one step of the rule above over
    * its own positions, from the object and probe the previous batch left. The complex constraint
    * (inside its windows) follows the last batch; E_t sums every position's error numerator at the
-   * state its batch saw. Every M (M = 256 runs each batch through the staged passes); not available
+   * state its batch saw. Every M (M = 256 and 512 run each batch through the staged passes); not available
    * in batch plans or ptycho_iterate_static. */
   int32_t minibatch;
   uint64_t order_seed;
@@ -115,7 +115,7 @@ typedef struct {
    * dpsi = psi_{n,k} - P_k o_n; inside a complex-constraint window the constraint acts on O next
    * and every psi_{n,k} moves by P_k (o_n after - o_n before); then P takes its step from the new
    * object, sum conj(o'_n) (psi_{n,k} - P_k o'_n) over sum |o'_n|^2. E_t is the pc model error
-   * of the estimate P_k o_n. Every M (M = 256 sweeps the staged passes twice per chunk, the
+   * of the estimate P_k o_n. Every M (M = 256 and 512 sweep the staged passes twice per chunk, the
    * estimate for the error and chi to the state update); without mini-batches; in single and
    * batch plans (a batch member keeps its own launches), not in ptycho_iterate_static. */
   int32_t engine;
@@ -187,7 +187,7 @@ ptycho_status ptycho_error_batch(ptycho_plan_t plan, double* nrmse_last);
  * 64; 0 restores tuning), e.g. for bitwise-reproducible runs across processes:
  * different L give the same result up to the FP32 order of the partial sums. */
 ptycho_status ptycho_set_batch_chunk(int32_t chunk_len);
-/* Staged path (M = 256): positions per chunk of the staged passes (their scratch
+/* Staged path (M = 256, 512): positions per chunk of the staged passes (their scratch
  * holds chunk x K x M^2 complex values, so the chunk decides how much of it stays
  * in L2). Chosen per (device, M, K, geometry, kernel width class) by timing one
  * pass over all positions for 4, 8, 16 and 32 when the first such plan is built
@@ -221,7 +221,7 @@ int ptycho_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int 
 
 /* Per-kernel timing for roofline reports. While enabled, ptycho_iterate records
  * a CUDA event pair on the plan's stream around every launch of the fused
- * per-position kernel (the dominant kernel of an iteration); for M = 256 the
+ * per-position kernel (the dominant kernel of an iteration); for M = 256 and 512 the
  * pair brackets the staged FFT / modulus passes of the iteration.
  * ptycho_profile_read synchronises the stream, returns the summed device time
  * of those launches in milliseconds and their count, and resets both. At most
@@ -230,7 +230,7 @@ ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
 ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
 
 /* Kernel launches one iteration issues: the fused kernel (M <= 128) or 5 (far)
- * / 7 (near) staged passes per chunk of positions (M = 256; pc-DM 8 / 11), 4 update kernels
+ * / 7 (near) staged passes per chunk of positions (M = 256, 512; pc-DM 8 / 11), 4 update kernels
  * (2 more for pc-DM), per batch for the mini-batch engine, and 3 complex-constraint
  * kernels when `in_window` is non-zero (copies not counted). */
 int32_t ptycho_launches_per_iteration(ptycho_plan_t plan, int32_t in_window);

@@ -24,45 +24,103 @@ namespace ptycho {
 
 namespace {
 
-constexpr int BL = 256;       // line length handled here
-constexpr int BT = 16;        // threads per line
-constexpr int BS = BT + 1;    // padded stride of the line-internal swap
-constexpr int LINES = 32;     // columns per CTA in the column passes (512 threads)
-constexpr int LROW = 16;      // lines per CTA in the row passes (256 threads)
-constexpr int RB = 16;        // rows per modulus block
+constexpr int BT = 16;   // threads per line
+constexpr int BS = BT + 1;
+constexpr int RB = 16;   // rows per modulus block
 
-// forward: thread t holds x[t + 16 j] in a[j]; returns X[t + 16 k1] in a[k1] (unscaled)
-template <bool INV>
-__device__ __forceinline__ void line_fft(float2 (&a)[16], float2* sw, const float2* tw, int t) {
-  if constexpr (!INV) {
-    dft<16, false>(a);  // a[k2] = Y[t][k2]
+// per line length: registers per thread (E), lines per CTA in the row passes (LROW) and columns per CTA
+// in the column passes (LINES), the swap buffer of one line (SWN float2) and the twiddle table (TWN)
+template <int BL>
+struct BigShape;
+template <>
+struct BigShape<256> {
+  static constexpr int E = 16, LROW = 16, LINES = 32, SWN = BT * BS, TWS = BS, TWN = BT * BS;
+};
+template <>
+struct BigShape<512> {
+  static constexpr int E = 32, LROW = 8, LINES = 16, SWN = 2 * BT * BS, TWS = 33, TWN = BT * 33;
+};
+
+// frequency held in register r by thread t after the forward line transform (the inverse expects it)
+template <int BL>
+__device__ __forceinline__ int line_freq(int t, int r) {
+  if constexpr (BL == 256) return t + 16 * r;
+  else return 2 * t + (r >> 4) + 32 * (r & 15);
+}
+
+// forward: thread t holds x[t + 16 j] in a[j]; returns X[line_freq(t, r)] in a[r] (unscaled). The inverse
+// consumes that layout and returns x[t + 16 j] * BL in a[j].
+//   256 = 16 x 16: DFT-16 over j, twiddle W_256^(t k2), swap, DFT-16 over t for k2 = t: X[t + 16 k1]
+//   512 = 32 x 16: DFT-32 over j, twiddle W_512^(t k2), swap (k2 = 2 t' + i2 to thread t'), DFT-16 over t
+//                  for k2 = 2t and 2t + 1: X[2t + i2 + 32 k1] in a[16 i2 + k1]
+template <int BL, bool INV>
+__device__ __forceinline__ void line_fft(float2 (&a)[BigShape<BL>::E], float2* sw, const float2* tw, int t) {
+  constexpr int TWS = BigShape<BL>::TWS;
+  if constexpr (BL == 256) {
+    if constexpr (!INV) {
+      dft<16, false>(a);  // a[k2] = Y[t][k2]
 #pragma unroll
-    for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[t * BS + k2]);
+      for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[t * TWS + k2]);
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) sw[k2 * BS + t] = a[k2];
-    __syncwarp();
+      for (int k2 = 0; k2 < 16; ++k2) sw[k2 * BS + t] = a[k2];
+      __syncwarp();
 #pragma unroll
-    for (int tt = 0; tt < 16; ++tt) a[tt] = sw[t * BS + tt];  // Y[tt][k2 = t]
-    __syncwarp();
-    dft<16, false>(a);  // a[k1] = X[t + 16 k1]
+      for (int tt = 0; tt < 16; ++tt) a[tt] = sw[t * BS + tt];  // Y[tt][k2 = t]
+      __syncwarp();
+      dft<16, false>(a);  // a[k1] = X[t + 16 k1]
+    } else {
+      dft<16, true>(a);  // a[tt] = Y[tt][k2 = t]
+#pragma unroll
+      for (int tt = 0; tt < 16; ++tt) sw[t * BS + tt] = a[tt];
+      __syncwarp();
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) a[k2] = sw[k2 * BS + t];  // Y[t][k2]
+      __syncwarp();
+#pragma unroll
+      for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmulc(a[k2], tw[t * TWS + k2]);
+      dft<16, true>(a);  // a[j] = x[t + 16 j] * 256
+    }
   } else {
-    dft<16, true>(a);  // a[tt] = Y[tt][k2 = t]
+    // swap layout: Y[t][k2] at (k2 & 1) * 16 BS + (k2 >> 1) * BS + t (conflict-free both ways)
+    if constexpr (!INV) {
+      dft<32, false>(a);  // a[k2] = Y[t][k2], k2 < 32
 #pragma unroll
-    for (int tt = 0; tt < 16; ++tt) sw[t * BS + tt] = a[tt];
-    __syncwarp();
+      for (int k2 = 1; k2 < 32; ++k2) a[k2] = cmul(a[k2], tw[t * TWS + k2]);
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) a[k2] = sw[k2 * BS + t];  // Y[t][k2]
-    __syncwarp();
+      for (int k2 = 0; k2 < 32; ++k2) sw[(k2 & 1) * 16 * BS + (k2 >> 1) * BS + t] = a[k2];
+      __syncwarp();
 #pragma unroll
-    for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmulc(a[k2], tw[t * BS + k2]);
-    dft<16, true>(a);  // a[j] = x[t + 16 j] * 256
+      for (int i2 = 0; i2 < 2; ++i2)
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) a[16 * i2 + tt] = sw[i2 * 16 * BS + t * BS + tt];  // Y[tt][2t + i2]
+      __syncwarp();
+      dft<16, false>(&a[0]);
+      dft<16, false>(&a[16]);  // a[16 i2 + k1] = X[2t + i2 + 32 k1]
+    } else {
+      dft<16, true>(&a[0]);
+      dft<16, true>(&a[16]);  // a[16 i2 + tt] = Z[tt][2t + i2]
+#pragma unroll
+      for (int i2 = 0; i2 < 2; ++i2)
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) sw[i2 * 16 * BS + t * BS + tt] = a[16 * i2 + tt];
+      __syncwarp();
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) a[k2] = sw[(k2 & 1) * 16 * BS + (k2 >> 1) * BS + t];  // Z[t][k2]
+      __syncwarp();
+#pragma unroll
+      for (int k2 = 1; k2 < 32; ++k2) a[k2] = cmulc(a[k2], tw[t * TWS + k2]);
+      dft<32, true>(a);  // a[j] = x[t + 16 j] * 512
+    }
   }
 }
 
+// twiddles W_BL^(t k2) for t < 16 and the k2 of the first pass, from the host table W_BL^m
+template <int BL>
 __device__ __forceinline__ void load_tw(float2* s_tw, const float2* tw) {
-  for (int i = threadIdx.x; i < BT * BS; i += blockDim.x) {
-    const int t = i / BS, k2 = i % BS;
-    s_tw[i] = k2 < 16 ? tw[(t * k2) % BL] : make_float2(0.f, 0.f);
+  constexpr int TWS = BigShape<BL>::TWS, K2 = BigShape<BL>::E;
+  for (int i = threadIdx.x; i < BigShape<BL>::TWN; i += blockDim.x) {
+    const int t = i / TWS, k2 = i % TWS;
+    s_tw[i] = k2 < K2 ? tw[(t * k2) % BL] : make_float2(0.f, 0.f);
   }
 }
 
@@ -70,11 +128,12 @@ __device__ __forceinline__ void load_tw(float2* s_tw, const float2* tw) {
 
 // ---- row passes. mode 0: exit wave + forward DFT; 1: R x (row) then forward DFT in place;
 // 2: inverse DFT in place, / M^2
-template <int MODE, bool NEAR>
-__global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
-  __shared__ float2 s_tw[BT * BS];
-  __shared__ float2 s_sw[LROW][BT * BS];
-  load_tw(s_tw, b.tw);
+template <int BL, int MODE, bool NEAR>
+__global__ void __launch_bounds__(BigShape<BL>::LROW * BT) k_big_rows(const BigArgs b) {
+  constexpr int E = BigShape<BL>::E, LROW = BigShape<BL>::LROW;
+  __shared__ float2 s_tw[BigShape<BL>::TWN];
+  __shared__ float2 s_sw[LROW][BigShape<BL>::SWN];
+  load_tw<BL>(s_tw, b.tw);
   __syncthreads();
   const int li = threadIdx.x / BT, t = threadIdx.x % BT;
   const int y = blockIdx.x * LROW + li;
@@ -82,7 +141,7 @@ __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
   const int n = b.n0 + c;
   const size_t MM = (size_t)BL * BL;
   float2* row = b.W + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
-  float2 a[16];
+  float2 a[E];
   if constexpr (MODE == 0) {
     const int2 pn = b.pos[n];
     const float2* Pk = b.P + (size_t)k * MM + (size_t)y * BL;
@@ -90,7 +149,7 @@ __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
     // pc-DM second sweep: the reflected wave chi = 2 P o_n - psi_n
     const float2* St = b.dm_pass == 2 ? b.psi + ((size_t)n * b.K + k) * MM + (size_t)y * BL : nullptr;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < E; ++j) {
       const int x = t + 16 * j;
       float2 psi = cmul(Pk[x], On[x]);
       if (St) {
@@ -104,42 +163,43 @@ __global__ void __launch_bounds__(LROW * BT) k_big_rows(const BigArgs b) {
     // Psi' = R Psi (the modulus ratio of this position) on the way in
     const float* Rr = b.R + (size_t)c * MM + (size_t)y * BL;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = cscale(row[t + 16 * j], Rr[t + 16 * j]);
+    for (int j = 0; j < E; ++j) a[j] = cscale(row[t + 16 * j], Rr[t + 16 * j]);
   } else {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];  // X[t + 16 k1]
+    for (int r = 0; r < E; ++r) a[r] = row[line_freq<BL>(t, r)];
   }
   if constexpr (MODE == 2) {
-    line_fft<true>(a, s_sw[li], s_tw, t);
+    line_fft<BL, true>(a, s_sw[li], s_tw, t);
     const float s = 1.0f / (float)(BL * BL);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) row[t + 16 * j] = cscale(a[j], s);
+    for (int j = 0; j < E; ++j) row[t + 16 * j] = cscale(a[j], s);
   } else {
-    line_fft<false>(a, s_sw[li], s_tw, t);
+    line_fft<BL, false>(a, s_sw[li], s_tw, t);
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) row[t + 16 * k1] = a[k1];
+    for (int r = 0; r < E; ++r) row[line_freq<BL>(t, r)] = a[r];
   }
 }
 
-// ---- column passes on a 256 x 32 tile staged through shared memory.
+// ---- column passes on a BL x LINES tile staged through shared memory.
 // op 0: forward DFT; 1: R x (tile), inverse DFT (far backward); 2: DFT, x H, IDFT (near forward);
 // 3: DFT, x conj H, IDFT (near backward)
-template <int OP>
-__global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
+template <int BL, int OP>
+__global__ void __launch_bounds__(BigShape<BL>::LINES * BT) k_big_cols(const BigArgs b) {
+  constexpr int E = BigShape<BL>::E, LINES = BigShape<BL>::LINES;
   constexpr int TP = LINES + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);  // [BL][TP]
   float2* s_tw = tile + BL * TP;
-  float2* s_sw = s_tw + BT * BS;  // [LINES][BT * BS]
-  float2* s_h = s_sw + LINES * BT * BS;
-  load_tw(s_tw, b.tw);
+  float2* s_sw = s_tw + BigShape<BL>::TWN;  // [LINES][SWN]
+  float2* s_h = s_sw + LINES * BigShape<BL>::SWN;
+  load_tw<BL>(s_tw, b.tw);
   if constexpr (OP >= 2)
     for (int i = threadIdx.x; i < BL; i += blockDim.x) s_h[i] = b.hq[i];
   const int x0 = blockIdx.x * LINES, k = blockIdx.y, c = blockIdx.z;
   const size_t MM = (size_t)BL * BL;
   float2* Wk = b.W + ((size_t)c * b.K + k) * MM;
-  // coalesced tile load: 32 consecutive columns per row; the far-field inverse pass
-  // applies Psi' = R Psi (the modulus ratio of this position) on the way in
+  // coalesced tile load: LINES consecutive columns per row; the far-field inverse pass applies
+  // Psi' = R Psi (the modulus ratio of this position) on the way in
   const float* Rc = b.R + (size_t)c * MM;
   for (int i = threadIdx.x; i < BL * LINES; i += blockDim.x) {
     const int yy = i / LINES, xx = i % LINES;
@@ -148,31 +208,33 @@ __global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
   }
   __syncthreads();
   const int cl = threadIdx.x / BT, t = threadIdx.x % BT;
-  float2* sw = s_sw + cl * BT * BS;
-  float2 a[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) a[j] = tile[(t + 16 * j) * TP + cl];
+  float2* sw = s_sw + cl * BigShape<BL>::SWN;
+  float2 a[E];
   if constexpr (OP == 1) {
-    line_fft<true>(a, sw, s_tw, t);
+#pragma unroll
+    for (int r = 0; r < E; ++r) a[r] = tile[line_freq<BL>(t, r) * TP + cl];
+    line_fft<BL, true>(a, sw, s_tw, t);
   } else {
-    line_fft<false>(a, sw, s_tw, t);  // a[k1] = column spectrum at u = t + 16 k1
+#pragma unroll
+    for (int j = 0; j < E; ++j) a[j] = tile[(t + 16 * j) * TP + cl];
+    line_fft<BL, false>(a, sw, s_tw, t);  // a[r] = column spectrum at u = line_freq(t, r)
     if constexpr (OP >= 2) {
       const float2 hv = s_h[x0 + cl];  // H(u, v) = h[u] h[v], v = this column's frequency
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) {
-        const float2 hh = cmul(s_h[t + 16 * k1], hv);
-        a[k1] = OP == 2 ? cmul(a[k1], hh) : cmulc(a[k1], hh);
+      for (int r = 0; r < E; ++r) {
+        const float2 hh = cmul(s_h[line_freq<BL>(t, r)], hv);
+        a[r] = OP == 2 ? cmul(a[r], hh) : cmulc(a[r], hh);
       }
-      line_fft<true>(a, sw, s_tw, t);
+      line_fft<BL, true>(a, sw, s_tw, t);
     }
   }
   __syncthreads();
   if constexpr (OP == 0) {
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) tile[(t + 16 * k1) * TP + cl] = a[k1];
+    for (int r = 0; r < E; ++r) tile[line_freq<BL>(t, r) * TP + cl] = a[r];
   } else {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) tile[(t + 16 * j) * TP + cl] = a[j];
+    for (int j = 0; j < E; ++j) tile[(t + 16 * j) * TP + cl] = a[j];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < BL * LINES; i += blockDim.x) {
@@ -184,7 +246,7 @@ __global__ void __launch_bounds__(LINES * BT) k_big_cols(const BigArgs b) {
 // ---- modulus: rows [y0, y0 + RB) of one position, with KH halo rows for the y blur.
 // Writes the ratio R to its own buffer (W is still read by the neighbouring
 // blocks' halos); the next pass applies Psi' = R Psi as it loads W.
-template <int KH>
+template <int BL, int KH>
 __global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
   constexpr int HR = RB + 2 * KH;  // rows held
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -260,11 +322,12 @@ __global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
 }
 
 // ---- final inverse row DFT of every mode, dpsi, contributions
-template <bool NEAR>
-__global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
-  __shared__ float2 s_tw[BT * BS];
-  __shared__ float2 s_sw[LROW][BT * BS];
-  load_tw(s_tw, b.tw);
+template <int BL, bool NEAR>
+__global__ void __launch_bounds__(BigShape<BL>::LROW * BT) k_big_final(const BigArgs b) {
+  constexpr int E = BigShape<BL>::E, LROW = BigShape<BL>::LROW;
+  __shared__ float2 s_tw[BigShape<BL>::TWN];
+  __shared__ float2 s_sw[LROW][BigShape<BL>::SWN];
+  load_tw<BL>(s_tw, b.tw);
   __syncthreads();
   const int li = threadIdx.x / BT, t = threadIdx.x % BT;
   const int y = blockIdx.x * LROW + li;
@@ -275,22 +338,22 @@ __global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
   const int2 pn = b.pos[n];
   const float2* On = b.O + (size_t)(pn.x + y) * b.obj_w + pn.y;
   const float s = 1.0f / (float)(BL * BL);
-  float2 cacc[16];
+  float2 cacc[E];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) cacc[j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < E; ++j) cacc[j] = make_float2(0.f, 0.f);
   for (int k = 0; k < b.K; ++k) {
     const float2* row = b.W + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
-    float2 a[16];
+    float2 a[E];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = row[t + 16 * j];
-    line_fft<true>(a, s_sw[li], s_tw, t);
+    for (int r = 0; r < E; ++r) a[r] = row[line_freq<BL>(t, r)];
+    line_fft<BL, true>(a, s_sw[li], s_tw, t);
     const float2* Pk = b.P + (size_t)k * MM + (size_t)y * BL;
     float2* pacc = b.pacc + ((size_t)c * b.K + k) * MM + (size_t)y * BL;
     // pc-DM: psi_n <- psi_n + Pi_F(chi) - P o_n, the overlap step takes psi_n - P o_n (its probe
     // sums follow the object step)
     float2* St = b.psi ? b.psi + ((size_t)n * b.K + k) * MM + (size_t)y * BL : nullptr;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < E; ++j) {
       const int x = t + 16 * j;
       float2 psi_new = cscale(a[j], s);
       if (!NEAR && ((y + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
@@ -312,7 +375,7 @@ __global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
   float2* cn = b.cn + (size_t)n * MM + (size_t)y * BL;
   float* dacc = b.dacc + (size_t)c * MM + (size_t)y * BL;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < E; ++j) {
     const int x = t + 16 * j;
     cn[x] = cacc[j];
     const float o2 = cabs2(On[x]);
@@ -320,62 +383,72 @@ __global__ void __launch_bounds__(LROW * BT) k_big_final(const BigArgs b) {
   }
 }
 
-size_t big_cols_smem() {
-  return sizeof(float2) * ((size_t)BL * (LINES + 1) + BT * BS + (size_t)LINES * BT * BS + BL);
+template <int BL>
+static size_t big_cols_smem() {
+  constexpr int LINES = BigShape<BL>::LINES;
+  return sizeof(float2) * ((size_t)BL * (LINES + 1) + BigShape<BL>::TWN + (size_t)LINES * BigShape<BL>::SWN + BL);
 }
 
-int big_row_blocks() { return BL / RB; }
+int big_row_blocks(int M) { return M / RB; }
 
-template <int KH>
+template <int BL, int KH>
 constexpr size_t big_mod_smem() { return sizeof(float) * 2 * (size_t)(RB + 2 * KH) * BL; }
 
 // the passes of one chunk; `full` false stops after the modulus pass (pc-DM first sweep)
+template <int BL>
 static cudaError_t big_passes(const BigArgs& b, int nc, bool full, cudaStream_t s) {
+  constexpr int LINES = BigShape<BL>::LINES, LROW = BigShape<BL>::LROW;
   const dim3 blk(LINES * BT), rblk(LROW * BT);
   const dim3 grow(BL / LROW, b.K, nc), gcol(BL / LINES, b.K, nc), gfin(BL / LROW, nc), gmod(BL / RB, nc);
-  const size_t cs = big_cols_smem();
+  const size_t cs = big_cols_smem<BL>();
   cudaError_t e;
-  for (auto kern : {k_big_cols<0>, k_big_cols<1>, k_big_cols<2>, k_big_cols<3>})
+  for (auto kern : {k_big_cols<BL, 0>, k_big_cols<BL, 1>, k_big_cols<BL, 2>, k_big_cols<BL, 3>})
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs)) != cudaSuccess)
       return e;
-  if ((e = cudaFuncSetAttribute(k_big_modulus<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)big_mod_smem<5>())) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_big_modulus<BL, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)big_mod_smem<BL, 5>())) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_big_modulus<15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)big_mod_smem<15>())) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_big_modulus<BL, 15>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)big_mod_smem<BL, 15>())) != cudaSuccess)
     return e;
   if (b.near_field) {
-    k_big_rows<0, true><<<grow, rblk, 0, s>>>(b);
-    k_big_cols<2><<<gcol, blk, cs, s>>>(b);
-    k_big_rows<2, true><<<grow, rblk, 0, s>>>(b);
+    k_big_rows<BL, 0, true><<<grow, rblk, 0, s>>>(b);
+    k_big_cols<BL, 2><<<gcol, blk, cs, s>>>(b);
+    k_big_rows<BL, 2, true><<<grow, rblk, 0, s>>>(b);
   } else {
-    k_big_rows<0, false><<<grow, rblk, 0, s>>>(b);
-    k_big_cols<0><<<gcol, blk, cs, s>>>(b);
+    k_big_rows<BL, 0, false><<<grow, rblk, 0, s>>>(b);
+    k_big_cols<BL, 0><<<gcol, blk, cs, s>>>(b);
   }
-  if (b.kh == 5) k_big_modulus<5><<<gmod, 256, big_mod_smem<5>(), s>>>(b);
-  else k_big_modulus<15><<<gmod, 256, big_mod_smem<15>(), s>>>(b);
+  if (b.kh == 5) k_big_modulus<BL, 5><<<gmod, 256, big_mod_smem<BL, 5>(), s>>>(b);
+  else k_big_modulus<BL, 15><<<gmod, 256, big_mod_smem<BL, 15>(), s>>>(b);
   if (!full) return cudaGetLastError();
   if (b.near_field) {
-    k_big_rows<1, true><<<grow, rblk, 0, s>>>(b);
-    k_big_cols<3><<<gcol, blk, cs, s>>>(b);
-    k_big_final<true><<<gfin, rblk, 0, s>>>(b);
+    k_big_rows<BL, 1, true><<<grow, rblk, 0, s>>>(b);
+    k_big_cols<BL, 3><<<gcol, blk, cs, s>>>(b);
+    k_big_final<BL, true><<<gfin, rblk, 0, s>>>(b);
   } else {
-    k_big_cols<1><<<gcol, blk, cs, s>>>(b);
-    k_big_final<false><<<gfin, rblk, 0, s>>>(b);
+    k_big_cols<BL, 1><<<gcol, blk, cs, s>>>(b);
+    k_big_final<BL, false><<<gfin, rblk, 0, s>>>(b);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) { return big_passes(b, nc, true, s); }
+static cudaError_t big_dispatch(const BigArgs& b, int nc, bool full, cudaStream_t s) {
+  if (b.M == 256) return big_passes<256>(b, nc, full, s);
+  if (b.M == 512) return big_passes<512>(b, nc, full, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s) { return big_dispatch(b, nc, true, s); }
 
 cudaError_t launch_big_chunk_dm(const BigArgs& b, int nc, cudaStream_t s) {
   if (!b.psi) return cudaErrorInvalidValue;
   BigArgs e = b;
   e.dm_pass = 1;  // the estimate P o_n through the propagation and the model, for the error only
-  cudaError_t err = big_passes(e, nc, false, s);
+  cudaError_t err = big_dispatch(e, nc, false, s);
   if (err != cudaSuccess) return err;
   e.dm_pass = 2;  // chi = 2 P o_n - psi_n: its modulus ratio, back-propagation, state update
-  return big_passes(e, nc, true, s);
+  return big_dispatch(e, nc, true, s);
 }
 
 }  // namespace ptycho

@@ -66,7 +66,7 @@ constexpr int kQueueChunkMin = 8;
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
 int g_fixed_chunk = 0;
-// staged path (M = 256): positions per chunk of the staged passes, same key, and its fixed value
+// staged path (M = 256, 512): positions per chunk of the staged passes, same key, and its fixed value
 constexpr int kStagedCandidates[] = {4, 8, 16, 32};
 std::map<std::tuple<int, int, int, int, int>, int> g_tune_staged;
 int g_fixed_staged = 0;
@@ -116,7 +116,7 @@ struct ptycho_plan_s {
   UpdateArgs ua{};
   ConstraintArgs ca{};
   BigArgs ba{};
-  bool big = false;  // M = 256: staged passes over a chunk of positions
+  bool big = false;  // M = 256, 512: staged passes over a chunk of positions
   // batch plans: independent member plans replayed as one CUDA graph per iteration
   std::vector<ptycho_plan_s*> members;
   std::vector<cudaStream_t> branch;
@@ -187,7 +187,6 @@ struct ptycho_plan_s {
 static ptycho_status validate(const ptycho_params* p) {
   if (!p) return fail(PTYCHO_EINVAL, "params is NULL");
   if (!is_pow2(p->M) || p->M < 8 || p->M > 512) return fail(PTYCHO_EINVAL, "M must be a power of two in [8, 512]");
-  if (p->M > 256) return fail(PTYCHO_EUNSUPPORTED, "M > 256 is not handled by this build");
   if (p->K < 1) return fail(PTYCHO_EINVAL, "K must be >= 1");
   if (p->K > kMaxModes) return fail(PTYCHO_EUNSUPPORTED, "K > 8 probe modes is not handled by this build");
   if (p->N < 1) return fail(PTYCHO_EINVAL, "N must be >= 1");
@@ -251,7 +250,7 @@ static bool is_device_pointer(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Autotuner of the staged path (M = 256): positions per chunk of the staged passes, timed on the
+// Autotuner of the staged path (M = 256, 512): positions per chunk of the staged passes, timed on the
 // device for each candidate over one pass of all positions (object and probe from scratch buffers
 // of ones -- the passes only read them; they write the scratch, contributions and partials, which
 // the first real iteration overwrites), best of two after a warm-up.
@@ -356,7 +355,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   }
 
   // ---- slots: co-resident clusters of the fused kernel (M <= 128), or the position chunk of
-  // the staged path (M = 256), whose per-slot partials are summed in slot order
+  // the staged path (M = 256, 512), whose per-slot partials are summed in slot order
   pl->big = M > 128;
   if (pl->big) {
     pl->chunk = std::min(N, kStagedCandidates[3]);  // buffers for the largest candidate; tuned below
@@ -439,7 +438,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_cn, (size_t)N * MM), "alloc contributions");
   PT_CUDA(pl->alloc(&d_pacc, (size_t)pl->slots * K * MM), "alloc probe partials");
   PT_CUDA(pl->alloc(&d_dacc, (size_t)pl->slots * MM), "alloc probe partials");
-  const size_t nerr = pl->big ? (size_t)N * big_row_blocks() : (size_t)pl->slots * K;
+  const size_t nerr = pl->big ? (size_t)N * big_row_blocks(M) : (size_t)pl->slots * K;
   PT_CUDA(pl->alloc(&d_errpart, nerr), "alloc error partials");
   float2* d_W = nullptr;
   float* d_R = nullptr;
@@ -587,6 +586,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   ba.I = d_I;
   ba.sqrtI = fa.sqrtI;
   ba.pos = d_pos;
+  ba.M = M;
   ba.N = N;
   ba.K = K;
   ba.obj_w = p.obj_w;
@@ -695,8 +695,8 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
           PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, s0 + len - n0), s), "staged pass launch");
         }
         ub.slots = std::min(pl->chunk, len);
-        ub.errpart = ua.errpart + (size_t)s0 * big_row_blocks();
-        ub.nerr = len * big_row_blocks();
+        ub.errpart = ua.errpart + (size_t)s0 * big_row_blocks(pl->p.M);
+        ub.nerr = len * big_row_blocks(pl->p.M);
       } else {
         FusedArgs fb = fa;
         fb.I = fa.I + (size_t)s0 * MM;

@@ -64,10 +64,10 @@ size_t fused_smem_bytes(int M);
 // true if a bounded device wait of the fused kernel gave up since the last call (clears the flag; synchronous)
 cudaError_t fused_timed_out(bool* out);
 
-// staged path for M = 256 (big.cu): a chunk of C positions x K modes in the scratch W
-constexpr int kBigM = 256;
+// staged path for M = 256 and 512 (big.cu): a chunk of C positions x K modes in the scratch W
 struct BigArgs {
   const float2* O; const float2* P; const float* I; const float* sqrtI; const int2* pos;
+  int M;              // 256 or 512
   int N, K, obj_w;
   int near_field, blur_intensity, kh;
   float eps;
@@ -81,7 +81,7 @@ struct BigArgs {
   float2* cn;         // N x M x M contributions
   float2* pacc;       // C x K x M x M probe partials (slot = position within the chunk)
   float* dacc;        // C x M x M
-  double* errpart;    // N x (M / 16) error partials
+  double* errpart;    // N x big_row_blocks(M) error partials
   // pc-DM: exit-wave state (N x K x M x M) or null; dm_init: the state starts at P o_n this pass
   float2* psi;
   int dm_init;
@@ -90,7 +90,7 @@ struct BigArgs {
 // the staged passes of one chunk; launch_big_chunk_dm: the two pc-DM sweeps (b.psi set)
 cudaError_t launch_big_chunk(const BigArgs& b, int nc, cudaStream_t s);
 cudaError_t launch_big_chunk_dm(const BigArgs& b, int nc, cudaStream_t s);
-int big_row_blocks();
+int big_row_blocks(int M);  // error partials per position (row blocks of the modulus pass)
 
 // tcgen05 BF16 GEMM (unet_gemm.cu): D[M x Ntot] (+)= A[M x K] . B[Ntot x K]^T, bf16 operands
 // stored as raw 16-bit words, K contiguous

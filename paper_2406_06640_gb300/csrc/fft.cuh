@@ -148,6 +148,52 @@ __device__ __forceinline__ void dft16(float2* a) {
   }
 }
 
+// cos(2 pi m / 32): cos(pi k / 16) for k = 0..8 from the half-angle identities (exact decimal expansions of
+// cos(pi/16) = sqrt(2 + sqrt(2 + sqrt 2)) / 2 and its neighbours), extended by symmetry
+__host__ __device__ constexpr float cos32(int m) {
+  constexpr float C[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                          0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                          0.19509032201612826785f, 0.0f};
+  const int r = m & 31, a = r > 16 ? 32 - r : r;
+  return a <= 8 ? C[a] : -C[16 - a];
+}
+__host__ __device__ constexpr float sin32(int m) { return cos32(m - 8); }  // sin(a) = cos(a - pi/2)
+
+// x * W_32^m, W = e^{-2 pi i / 32} (forward) or its conjugate (inverse)
+template <bool INV, int m>
+__device__ __forceinline__ float2 mul_w32(float2 a) {
+  if constexpr ((m & 1) == 0) {
+    return mul_w16<INV, m / 2>(a);
+  } else {
+    constexpr float c = cos32(m);
+    constexpr float s = INV ? sin32(m) : -sin32(m);
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+// butterflies k, k + 1, .., 15 of the DFT-32: a[k] = e[k] + W_32^k o[k], a[k + 16] = e[k] - W_32^k o[k]
+template <bool INV, int K>
+__device__ __forceinline__ void bfly32(float2* a, const float2* e, const float2* o) {
+  const float2 t = mul_w32<INV, K>(o[K]);
+  a[K] = cadd(e[K], t);
+  a[K + 16] = csub(e[K], t);
+  if constexpr (K < 15) bfly32<INV, K + 1>(a, e, o);
+}
+
+// DFT-32 in registers, natural order in and out: even and odd halves by DFT-16, then the butterflies
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* a) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    e[j] = a[2 * j];
+    o[j] = a[2 * j + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+  bfly32<INV, 0>(a, e, o);
+}
+
 template <int N, bool INV>
 __device__ __forceinline__ void dft(float2* a) {
   if constexpr (N == 1) {
@@ -159,6 +205,8 @@ __device__ __forceinline__ void dft(float2* a) {
     dft8<INV>(a);
   } else if constexpr (N == 16) {
     dft16<INV>(a);
+  } else if constexpr (N == 32) {
+    dft32<INV>(a);
   } else {
     static_assert(N == 1, "unsupported register DFT size");
   }

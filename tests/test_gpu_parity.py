@@ -263,6 +263,24 @@ def test_m256_staged_chunk_sizes(chunk):
     assert got in (4, 8, 16, 20) if chunk == 0 else got == min(chunk, 20)
 
 
+@pytest.mark.parametrize("geometry,K,blur,ks", [("near", 2, "amplitude", 11), ("far", 1, "intensity", 31)])
+def test_m512_staged_passes(geometry, K, blur, ks):
+    """512^2 patterns (the next size of the paper's 1024^2 optical patterns) on the staged passes: a
+    512-point line is 16 threads x 32 values (radix 32 in registers, then radix 16 after a warp-local
+    swap); four positions, both geometries, a constraint window."""
+    p = make_problem(0, scan_side=2, obj_side=600, M=512, K=K, geometry=geometry, sigma=1.5)
+    check(p, dict(p.params, sigma1=1.5, sigma2=1.2, blur_domain=blur, kernel_size=ks, windows=[(2, 2)]), 3)
+
+
+def test_m512_pc_dm_and_minibatch():
+    """pc-DM and the mini-batch engine at M = 512 (the staged passes swept twice per chunk; batches of
+    two positions)."""
+    p = make_problem(0, scan_side=2, obj_side=600, M=512, K=1, sigma=1.2)
+    check(p, dict(p.params, sigma1=1.2, sigma2=1.2, engine="dm"), 2)
+    check(p, dict(p.params, sigma1=1.2, sigma2=1.2, minibatch=2, order_seed=3, step_rule="rpie",
+                  rpie_alpha_obj=0.3, rpie_alpha_probe=0.3), 2)
+
+
 def test_config2_full_size_one_iteration():
     """Full configuration 2 (near field F = 10, M = 256, K = 8, 256 positions, 1024^2 object)."""
     p = make_problem(2)
