@@ -65,7 +65,7 @@ def _plan_status(**over):
 
 
 @pytest.mark.parametrize("over,expect", [
-    (dict(M=7), 1), (dict(M=1024), 1), (dict(M=512, obj_h=600, obj_w=600), 4), (dict(K=0), 1), (dict(K=9), 4), (dict(N=0), 1),
+    (dict(M=7), 1), (dict(M=1024), 1), (dict(K=0), 1), (dict(K=9), 4), (dict(N=0), 1),
     (dict(obj_h=32), 1), (dict(geometry=5), 1), (dict(blur_domain=3), 1), (dict(geometry="near", fresnel_F=0.0), 1),
     (dict(sigma1=-1.0), 1), (dict(kernel_size=10), 1), (dict(kernel_size=33), 1), (dict(alpha1=1.5), 1),
     (dict(cbar_min=0.0), 1), (dict(cbar_min=2.0, cbar_max=1.0), 1), (dict(windows=[(0, 3)]), 1),
