@@ -110,6 +110,7 @@ struct ptycho_plan_s {
   std::vector<int2> h_pos;
   double errden = 0.0, eps = 0.0;
   int slots = 0;
+  int cluster_slots = 0;  // mini-batch plans: co-resident clusters of the cluster form (small batches)
   long long iter = 1;  // number of the next iteration
   long long runs = 0;  // iterations run so far
   FusedArgs fa{};
@@ -372,6 +373,10 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
     pl->slots = std::min(max_slots, N);
   }
   if (pl->parts > 0) pl->slots = pl->parts;  // partials per position chunk (work-queue batch member)
+  if (pl->mb > 0 && !pl->big) {
+    PT_CUDA(fused_cluster_max_slots(M, K, &pl->cluster_slots), "occupancy of the cluster form");
+    pl->cluster_slots = std::min(pl->cluster_slots, pl->slots);
+  }
 
   // ---- buffers
   FusedArgs& fa = pl->fa;
@@ -440,6 +445,10 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_dacc, (size_t)pl->slots * MM), "alloc probe partials");
   const size_t nerr = pl->big ? (size_t)N * big_row_blocks(M) : (size_t)pl->slots * K;
   PT_CUDA(pl->alloc(&d_errpart, nerr), "alloc error partials");
+  // detector fields of modes 0 .. K-2 per slot, for the single-problem fused kernel's second pass
+  float2* d_stash = nullptr;
+  if (!pl->big && K > 1 && p.engine != PTYCHO_ENGINE_DM && pl->parts == 0)
+    PT_CUDA(pl->alloc(&d_stash, (size_t)pl->slots * (K - 1) * MM), "alloc detector-field stash");
   float2* d_W = nullptr;
   float* d_R = nullptr;
   if (pl->big) {
@@ -530,6 +539,7 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   fa.hq = d_hq;
   fa.cn = d_cn;
   fa.pacc = d_pacc;
+  fa.stash = d_stash;
   fa.dacc = d_dacc;
   fa.errpart = d_errpart;
 
@@ -704,8 +714,11 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
         fb.pos = fa.pos + s0;
         fb.N = len;
         fb.cn = fa.cn + (size_t)s0 * MM;
-        const int slots = std::min(pl->slots, len);
-        PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
+        // a batch with fewer positions than one-CTA slots fills more SMs as clusters of K CTAs
+        const bool clustered = pl->p.K > 1 && len < pl->slots && pl->cluster_slots > 0;
+        const int slots = std::min(clustered ? pl->cluster_slots : pl->slots, len);
+        if (clustered) PT_CUDA(launch_fused_cluster(pl->p.M, fb, slots, s), "fused kernel launch");
+        else PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
         ub.slots = slots;
         ub.nerr = slots * pl->p.K;
       }

@@ -44,6 +44,10 @@ struct FusedArgs {
   // pc-DM launches: exit-wave state N x K x M x M (updated in place); dm_init: start it at P o_n
   float2* psi;
   int dm_init;
+  // single-problem launches: the detector fields of modes 0 .. K-2 of the position in flight,
+  // slots x (K - 1) x M x M, so that the second pass reads them instead of propagating again;
+  // null: propagate again
+  float2* stash;
 };
 
 // single-problem fused launch (pc_fused_seq.cu: one CTA per position, modes in sequence) over
@@ -51,6 +55,10 @@ struct FusedArgs {
 // slots x K x M x M, dacc slots x M x M, errpart slots x K (the slot's error in entry 0)
 cudaError_t launch_fused(int M, const FusedArgs& a, int slots, cudaStream_t s);
 cudaError_t fused_max_slots(int M, int K, int* slots);
+// cluster form for a single problem (one cluster of K CTAs per position, `slots` clusters); partials
+// as launch_fused (errpart slots x K, one entry per rank)
+cudaError_t launch_fused_cluster(int M, const FusedArgs& a, int slots, cudaStream_t s);
+cudaError_t fused_cluster_max_slots(int M, int K, int* slots);
 // work-queue launch (M = 32, 64, 128): `slots` persistent clusters drain a.chunks through a.queue;
 // a.K, a.near_field, a.kh (kernel width class) and a.tw are those of every problem in a.probs
 cudaError_t launch_fused_queue(int M, const FusedArgs& a, int slots, cudaStream_t s);

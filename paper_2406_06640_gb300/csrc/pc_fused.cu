@@ -1,5 +1,6 @@
 // Fused per-position pc-engine kernel in its cluster form, used by the work-queue launches of
-// batch plans (the single-problem launch runs the one-CTA-per-position kernel of pc_fused_seq.cu):
+// batch plans and by mini-batches too small to fill the GPU with one CTA per position (the
+// single-problem launch runs the one-CTA-per-position kernel of pc_fused_seq.cu):
 // one cluster of K CTAs per scan position,
 // CTA rank k owns probe mode k and rows [k R, (k + 1) R) of the detector
 // (R = ceil(M / K)). Everything between the object gather and the per-position
@@ -83,6 +84,51 @@ static cudaError_t launch_kh(const FusedArgs& a, int slots, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = fused_config<M, KH, QUEUED>(a, slots, s, attr);
   return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// ---- single-problem launches of the cluster form: the mini-batch engine takes them for batches
+// with fewer positions than the one-CTA form has slots (K CTAs per position then fill more SMs)
+template <int M, bool NEAR>
+static cudaError_t launch_cluster_t(const FusedArgs& a, int slots, cudaStream_t s) {
+  return a.kh == 5 ? launch_kh<M, NEAR, 5>(a, slots, s) : launch_kh<M, NEAR, 15>(a, slots, s);
+}
+
+cudaError_t launch_fused_cluster(int M, const FusedArgs& a, int slots, cudaStream_t s) {
+  const bool nf = a.near_field != 0;
+  switch (M) {
+    case 8: return nf ? launch_cluster_t<8, true>(a, slots, s) : launch_cluster_t<8, false>(a, slots, s);
+    case 16: return nf ? launch_cluster_t<16, true>(a, slots, s) : launch_cluster_t<16, false>(a, slots, s);
+    case 32: return nf ? launch_cluster_t<32, true>(a, slots, s) : launch_cluster_t<32, false>(a, slots, s);
+    case 64: return nf ? launch_cluster_t<64, true>(a, slots, s) : launch_cluster_t<64, false>(a, slots, s);
+    case 128: return nf ? launch_cluster_t<128, true>(a, slots, s) : launch_cluster_t<128, false>(a, slots, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int M>
+static cudaError_t cluster_slots_t(int K, int* slots) {
+  auto kern = pc_fused_kernel<M, false, 15, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<M, 15>::BYTES);
+  if (e != cudaSuccess) return e;
+  FusedArgs a = {};
+  a.K = K;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = fused_config<M, 15>(a, 1, 0, attr);
+  int n = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+  *slots = n;
+  return e;
+}
+
+cudaError_t fused_cluster_max_slots(int M, int K, int* slots) {
+  switch (M) {
+    case 8: return cluster_slots_t<8>(K, slots);
+    case 16: return cluster_slots_t<16>(K, slots);
+    case 32: return cluster_slots_t<32>(K, slots);
+    case 64: return cluster_slots_t<64>(K, slots);
+    case 128: return cluster_slots_t<128>(K, slots);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // ---- work-queue launches (batches of problems sharing M, K, geometry and kernel width class)

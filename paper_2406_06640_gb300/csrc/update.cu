@@ -93,35 +93,51 @@ cudaError_t launch_finish_sums(const double* partials, int nblocks, double* out,
 
 // ------------------------------------------------------------------ probe: sum the per-slot partials
 // grid (ceil(M^2 / 256), K + 1): y < K sums N_P for mode y; y == K sums D_P, |P|^2 map and block max
-__global__ void k_probe_gather(const UpdateArgs u) {
+// thread (pixel p, group g) sums the slots g, g + 4, g + 8, ..., and the four group sums are added
+// in group order (a fixed summation order; four loads in flight per pixel instead of one)
+constexpr int kProbeGroups = 4;
+__global__ void __launch_bounds__(256 * kProbeGroups) k_probe_gather(const UpdateArgs u) {
   const int MM = u.M * u.M;
-  const int p = blockIdx.x * 256 + threadIdx.x;
+  const int tx = threadIdx.x % 256, g = threadIdx.x / 256;
+  const int p = blockIdx.x * 256 + tx;
+  __shared__ float2 part[kProbeGroups][256];
   __shared__ float smax[256];
   if ((int)blockIdx.y < u.K) {
-    if (p >= MM) return;
     const int k = blockIdx.y;
     float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 8
-    for (int s = 0; s < u.slots; ++s) acc = cadd(acc, u.pacc[((size_t)s * u.K + k) * MM + p]);
-    u.np_sum[(size_t)k * MM + p] = acc;
+    if (p < MM) {
+#pragma unroll 4
+      for (int s = g; s < u.slots; s += kProbeGroups) acc = cadd(acc, u.pacc[((size_t)s * u.K + k) * MM + p]);
+    }
+    part[g][tx] = acc;
+    __syncthreads();
+    if (g == 0 && p < MM)
+      u.np_sum[(size_t)k * MM + p] = cadd(cadd(cadd(part[0][tx], part[1][tx]), part[2][tx]), part[3][tx]);
     return;
   }
   float dp = 0.f;
   if (p < MM) {
-#pragma unroll 8
-    for (int s = 0; s < u.slots; ++s) dp += u.dacc[(size_t)s * MM + p];
+#pragma unroll 4
+    for (int s = g; s < u.slots; s += kProbeGroups) dp += u.dacc[(size_t)s * MM + p];
+  }
+  part[g][tx].x = dp;
+  __syncthreads();
+  if (g != 0) return;
+  dp = ((part[0][tx].x + part[1][tx].x) + part[2][tx].x) + part[3][tx].x;
+  if (p < MM) {
     float p2 = 0.f;
     for (int k = 0; k < u.K; ++k) p2 += cabs2(u.P[(size_t)k * MM + p]);
     u.dp_sum[p] = dp;
     u.p2[p] = p2;
   }
-  smax[threadIdx.x] = dp;
-  __syncthreads();
+  smax[tx] = dp;
+  // the first 256 threads (whole warps) finish the block maximum
+  asm volatile("bar.sync 1, 256;" ::: "memory");
   for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
-    __syncthreads();
+    if (tx < w) smax[tx] = fmaxf(smax[tx], smax[tx + w]);
+    asm volatile("bar.sync 1, 256;" ::: "memory");
   }
-  if (threadIdx.x == 0) u.blk_max_p[blockIdx.x] = smax[0];
+  if (tx == 0) u.blk_max_p[blockIdx.x] = smax[0];
 }
 
 // ------------------------------------------------------------------ pc-DM probe partials
@@ -353,9 +369,9 @@ cudaError_t launch_update_object(const UpdateArgs& u, cudaStream_t s) {
     // the |P|^2 map for the object step only (no partials: the probe sums follow the object step)
     UpdateArgs u0 = u;
     u0.slots = 0;
-    k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u0);
+    k_probe_gather<<<dim3(pb, u.K + 1), 256 * kProbeGroups, 0, s>>>(u0);
   } else {
-    k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+    k_probe_gather<<<dim3(pb, u.K + 1), 256 * kProbeGroups, 0, s>>>(u);
   }
   const dim3 tb(32, 8);
   {
@@ -382,7 +398,7 @@ cudaError_t launch_update_probe(const UpdateArgs& u, cudaStream_t s) {
   const int pb = (MM + 255) / 256;
   if (u.dm_psi && (u.update_probe || u.dm_obj_prev)) {
     k_dm_probe_partials<<<dim3(pb, u.slots), 256, 0, s>>>(u);
-    if (u.update_probe) k_probe_gather<<<dim3(pb, u.K + 1), 256, 0, s>>>(u);
+    if (u.update_probe) k_probe_gather<<<dim3(pb, u.K + 1), 256 * kProbeGroups, 0, s>>>(u);
   }
   k_probe_apply<<<dim3(pb, u.K), 256, 0, s>>>(u);
   return cudaGetLastError();
