@@ -47,6 +47,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// arrive (release at CTA scope) on a barrier counting producer threads
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
@@ -374,6 +379,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_bf16(const GemmArgs g) {
 // taps t and t + 1 as its two k groups (LBO = the distance between their offsets), and the ninth tap
 // is paired with zero weight columns.
 namespace {
+constexpr int kHaloProducers = kThreads - 32;  // warps 0-6 copy, warp 7 issues the MMAs
+
 template <int N, int T>
 struct HaloCfg {
   // B ring: S stages; the copies of a step are issued D - 1 steps before its MMAs, so D - 1 steps of
@@ -400,7 +407,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) 
   using HC = HaloCfg<N, T>;
   constexpr int S = HC::S, D = HC::D;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bar[S], sbar[2];
+  // full[st]: the producers' copies of the step in stage st landed (one arrival per producer thread);
+  // bar[st]: the MMAs reading stage st are done (tcgen05.commit); sbar[b]: those of slab buffer b
+  __shared__ uint64_t bar[S], full[S], sbar[2];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int H = g.H, W = g.W, Cin = g.Cin;
@@ -422,7 +431,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) 
 
   if (warp == 0) tm_alloc(&s_tmem, NCOLS_ALL);
   if (tid == 0) {
-    for (int i = 0; i < S; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&bar[i], 1);
+      mbar_init(&full[i], kHaloProducers);
+    }
     mbar_init(&sbar[0], 1);
     mbar_init(&sbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -454,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) 
   // copies: the k groups of one row are adjacent threads (a warp reads whole 16 KG-byte pixel chunks)
   auto stage_slab = [&](int chunk, uint32_t dst) {
     const int c0 = chunk * CC;
-    for (int i = tid; i < R * KG; i += kThreads) {
+    for (int i = tid; i < R * KG; i += kHaloProducers) {
       const int j = i / KG, q = i % KG;
       const long long o = row_off(j);
       cp_async16(slab_at(dst, j, q), o >= 0 ? X + o + c0 + q * 8 : X, o >= 0 ? 16u : 0u);
@@ -465,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) 
     const int chunk = st / taps, t = st % taps;
     const int kgb = pairs ? 2 : KG;
     const int k0 = pairs ? 16 * t : t * Cin + chunk * CC;
-    for (int i = tid; i < N * kgb; i += kThreads) {
+    for (int i = tid; i < N * kgb; i += kHaloProducers) {
       const int n = i / kgb, q = i % kgb;
       const uint32_t d = SW ? dst + (uint32_t)(n * 128 + ((q ^ (n & 7)) << 4)) : dst + (uint32_t)((q * N + n) * 16);
       cp_async16(d, B + (size_t)n * Kw + k0 + q * 8, 16u);
@@ -473,78 +485,86 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) 
   };
   auto tap_off = [&](int t) { return (t / 3 - 1) * Wp + (t % 3 - 1); };
 
-  // iteration i: the MMAs of step j = i - (D - 1) (whose copies were issued D - 1 iterations ago), then
-  // the copies of step i into a stage whose MMAs were issued S - D + 1 iterations ago
+  // warp-specialised main loop, no CTA-wide barrier inside:
+  //   producers (warps 0-6): copies of step i into stage i % S once the MMAs of step i - S are done
+  //     (bar), then, D - 1 steps later, wait for their own copies of that step, make them visible to
+  //     the tensor core's (async) proxy and arrive on full[stage];
+  //   MMA issuer (warp 7, lane 0): waits on full[stage] of step j, issues its MMAs, commits to bar.
   bool ok = true;
-  for (int i = 0; i < nsteps + D - 1 && ok; ++i) {
-    const int j = i - (D - 1);
-    if (j >= 0 && j < nsteps) {
-      cp_async_wait<D - 2>();  // this thread's copies of step j (groups up to i - 1 are committed)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        // lean issue: a descriptor is linear in its start address ((start >> 4) in the low bits, no carry
-        // below 256 KB), so every MMA's descriptors are a base plus a constant; the issuing thread must
-        // keep ahead of the tensor pipe (~64-128 cycles per MMA)
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int st = j % S, chunk = j / taps, t = j % taps;
-        const uint32_t slab = slab0 + (uint32_t)(chunk & 1) * slab_bytes;
-        const uint32_t bs = bring + (uint32_t)(st * HC::B_STAGE);
-        const uint32_t first = j == 0 ? 0u : 1u;  // the first MMA of each accumulator overwrites it
-        if (pairs) {
-          // taps 2t and 2t + 1 (the ninth with the row after it, whose weights are zero)
-          const int ta = 2 * t, oa = tap_off(ta);
-          const int ob = ta + 1 < 9 ? tap_off(ta + 1) : oa + 1;
-          const uint64_t ad = make_desc(slab + (uint32_t)((W + 3 + oa) * 16), (uint32_t)((ob - oa) * 16), 128);
-          const uint64_t bd = make_desc(bs, (uint32_t)(N * 16), 128);
-#pragma unroll
-          for (int m = 0; m < T; ++m)
-            mma_bf16_acc(tmem + (uint32_t)(m * HC::NCOLS), ad + (uint64_t)(128 * m), bd, idesc, first);
-        } else if constexpr (SW) {
-          // rows X .. X + 127 of the slab, K in steps of 16 (32 bytes = 2 descriptor units along each row)
-          const uint64_t ad = make_desc_sw128(slab + (uint32_t)((W + 3 + tap_off(t)) * 128));
-          const uint64_t bd = make_desc_sw128(bs);
-#pragma unroll
-          for (int m = 0; m < T; ++m) {
-            const uint64_t am = ad + (uint64_t)(1024 * m);  // 128 rows of 128 bytes, in 16-byte units
-            const uint32_t acc = tmem + (uint32_t)(m * HC::NCOLS);
-            mma_bf16_acc(acc, am, bd, idesc, first);
-            mma_bf16_acc(acc, am + 2, bd + 2, idesc, 1u);
-            mma_bf16_acc(acc, am + 4, bd + 4, idesc, 1u);
-            mma_bf16_acc(acc, am + 6, bd + 6, idesc, 1u);
-          }
-        } else {
-          const uint64_t ad = make_desc(slab + (uint32_t)((W + 3 + tap_off(t)) * 16), (uint32_t)(R * 16), 128);
-          const uint64_t bd = make_desc(bs, (uint32_t)(N * 16), 128);
-#pragma unroll
-          for (int m = 0; m < T; ++m) {
-            const uint32_t acc = tmem + (uint32_t)(m * HC::NCOLS);
-            const uint64_t am = ad + (uint64_t)(128 * m);  // 128 rows of 16 bytes
-#pragma unroll 1
-            for (int q = 0; q < KG; q += 2)  // k groups q, q + 1: R rows of 16 bytes each further
-              mma_bf16_acc(acc, am + (uint64_t)(q * R), bd + (uint64_t)(q * N), idesc, q > 0 ? 1u : first);
-          }
+  if (tid < kHaloProducers) {
+    for (int i = 0; i < nsteps + D - 1 && ok; ++i) {
+      if (i < nsteps) {
+        const int st = i % S;
+        if (i >= S) ok = mbar_wait_bounded(&bar[st], (uint32_t)((i / S - 1) & 1));
+        const int chunk = i / taps;
+        if (ok && i % taps == 0 && chunk >= 2)  // the MMAs of chunk - 2 read this slab buffer
+          ok = mbar_wait_bounded(&sbar[chunk & 1], (uint32_t)(((chunk - 2) >> 1) & 1));
+        if (ok) {
+          if (i % taps == 0) stage_slab(chunk, slab0 + (uint32_t)(chunk & 1) * slab_bytes);
+          stage_b(i, bring + (uint32_t)(st * HC::B_STAGE));
         }
-        mma_commit(&bar[st]);
-        if (t == taps - 1) mma_commit(&sbar[chunk & 1]);
+      }
+      cp_async_commit();  // one group per iteration (possibly empty) keeps the group count aligned
+      const int j = i - (D - 1);
+      if (ok && j >= 0 && j < nsteps) {
+        cp_async_wait<D - 1>();  // this thread's copies of step j (groups up to i are committed)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&full[j % S]);
       }
     }
-    if (i < nsteps) {
-      const int st = i % S;
-      if (i >= S)  // the MMAs of step i - S read this stage (issued S - D + 1 iterations ago)
-        ok = __syncthreads_and(mbar_wait_bounded(&bar[st], (uint32_t)((i / S - 1) & 1)) ? 1 : 0) != 0;
-      const int chunk = i / taps;
-      if (ok && i % taps == 0 && chunk >= 2)  // the MMAs of chunk - 2 read this slab buffer
-        ok = __syncthreads_and(mbar_wait_bounded(&sbar[chunk & 1], (uint32_t)(((chunk - 2) >> 1) & 1)) ? 1 : 0) != 0;
-      if (ok) {
-        if (i % taps == 0) stage_slab(chunk, slab0 + (uint32_t)(chunk & 1) * slab_bytes);
-        stage_b(i, bring + (uint32_t)(st * HC::B_STAGE));
+    cp_async_wait<0>();
+  } else if (tid == kHaloProducers) {
+    for (int j = 0; j < nsteps && ok; ++j) {
+      ok = mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1));
+      if (!ok) break;
+      // lean issue: a descriptor is linear in its start address ((start >> 4) in the low bits, no carry
+      // below 256 KB), so every MMA's descriptors are a base plus a constant; the issuing thread must
+      // keep ahead of the tensor pipe (~64-128 cycles per MMA)
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int st = j % S, chunk = j / taps, t = j % taps;
+      const uint32_t slab = slab0 + (uint32_t)(chunk & 1) * slab_bytes;
+      const uint32_t bs = bring + (uint32_t)(st * HC::B_STAGE);
+      const uint32_t first = j == 0 ? 0u : 1u;  // the first MMA of each accumulator overwrites it
+      if (pairs) {
+        // taps 2t and 2t + 1 (the ninth with the row after it, whose weights are zero)
+        const int ta = 2 * t, oa = tap_off(ta);
+        const int ob = ta + 1 < 9 ? tap_off(ta + 1) : oa + 1;
+        const uint64_t ad = make_desc(slab + (uint32_t)((W + 3 + oa) * 16), (uint32_t)((ob - oa) * 16), 128);
+        const uint64_t bd = make_desc(bs, (uint32_t)(N * 16), 128);
+#pragma unroll
+        for (int m = 0; m < T; ++m)
+          mma_bf16_acc(tmem + (uint32_t)(m * HC::NCOLS), ad + (uint64_t)(128 * m), bd, idesc, first);
+      } else if constexpr (SW) {
+        // rows X .. X + 127 of the slab, K in steps of 16 (32 bytes = 2 descriptor units along each row)
+        const uint64_t ad = make_desc_sw128(slab + (uint32_t)((W + 3 + tap_off(t)) * 128));
+        const uint64_t bd = make_desc_sw128(bs);
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+          const uint64_t am = ad + (uint64_t)(1024 * m);  // 128 rows of 128 bytes, in 16-byte units
+          const uint32_t acc = tmem + (uint32_t)(m * HC::NCOLS);
+          mma_bf16_acc(acc, am, bd, idesc, first);
+          mma_bf16_acc(acc, am + 2, bd + 2, idesc, 1u);
+          mma_bf16_acc(acc, am + 4, bd + 4, idesc, 1u);
+          mma_bf16_acc(acc, am + 6, bd + 6, idesc, 1u);
+        }
+      } else {
+        const uint64_t ad = make_desc(slab + (uint32_t)((W + 3 + tap_off(t)) * 16), (uint32_t)(R * 16), 128);
+        const uint64_t bd = make_desc(bs, (uint32_t)(N * 16), 128);
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+          const uint32_t acc = tmem + (uint32_t)(m * HC::NCOLS);
+          const uint64_t am = ad + (uint64_t)(128 * m);  // 128 rows of 16 bytes
+#pragma unroll 1
+          for (int q = 0; q < KG; q += 2)  // k groups q, q + 1: R rows of 16 bytes each further
+            mma_bf16_acc(acc, am + (uint64_t)(q * R), bd + (uint64_t)(q * N), idesc, q > 0 ? 1u : first);
+        }
       }
+      mma_commit(&bar[st]);
+      if (t == taps - 1) mma_commit(&sbar[chunk & 1]);
     }
-    cp_async_commit();  // one group per iteration (possibly empty) keeps the group count aligned
   }
-  cp_async_wait<0>();
-  if (ok && nsteps > 0)
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (ok && nsteps > 0)  // the last step's commit covers every MMA issued before it
     ok = __syncthreads_and(mbar_wait_bounded(&bar[(nsteps - 1) % S], (uint32_t)(((nsteps - 1) / S) & 1)) ? 1 : 0) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!ok) {
