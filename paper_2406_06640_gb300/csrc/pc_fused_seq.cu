@@ -18,7 +18,9 @@
 //   memory written in pass 1, or propagated again when no stash is given):
 //     Psi'_k = R Psi_k;  psi'_k = inverse propagation;  dpsi_k = psi'_k - P_k o_n
 //     c_n   += conj(P_k) dpsi_k                 (TMEM; written once per position)
-//     pacc_k += conj(o_n) dpsi_k, dacc += |o_n|^2   (per-slot partials, no atomics)
+//     pacc_k += conj(o_n) dpsi_k, dacc += |o_n|^2   (per-slot partials: reductions at L2 into
+//                                                  the slot's own array, each element always
+//                                                  added to by the same thread, so in a fixed order)
 //
 // Cost against the cluster form: a store and a load of K - 1 detector fields per position (or,
 // without the stash, one more forward propagation for each), in exchange for no exchanges and all
@@ -39,8 +41,8 @@
 
 namespace ptycho {
 
-// L2 eviction policies: the per-slot probe partials are read and written once per position and mode
-// and must survive in L2 between those visits; the streamed data (sqrt I, c_n) must not push them out
+// L2 eviction policies: the per-slot probe partials are added to once per position and mode and
+// must survive in L2 between those visits; the streamed data (sqrt I, c_n) must not push them out
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -51,21 +53,25 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ float2 ld_hint(const float2* a, uint64_t pol) {
-  float2 v;
-  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
-  float v;
-  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
-  return v;
-}
 __device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
 }
-__device__ __forceinline__ void st_hint(float* a, float v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+// stores of the partials, which this kernel never reads back: no memory clobber, so the compiler may
+// move later loads above them
+__device__ __forceinline__ void st_part(float2* a, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol));
+}
+__device__ __forceinline__ void st_part(float* a, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol));
+}
+// fire-and-forget add at L2. A partial element is only ever added to by one thread of one CTA, and
+// reductions of one thread to one address take effect in program order, so the sums keep their order
+// (position by position) and stay bitwise reproducible; no register waits for the old value
+__device__ __forceinline__ void red_hint(float2* a, float2 v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol));
+}
+__device__ __forceinline__ void red_hint(float* a, float v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol));
 }
 // bring `bytes` (a multiple of 16, 16-byte aligned) into L2 ahead of use
 __device__ __forceinline__ void prefetch_l2(const void* a, uint32_t bytes, uint64_t pol) {
@@ -337,12 +343,6 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
     // ---- pass 2: mode K-1 from storage, then modes 0 .. K-2 propagated again
     for (int i = 0; i < K; ++i) {
       const int k = i == 0 ? K - 1 : i - 1;
-      // this mode's probe partial (and, for the first, the denominator partial) is read and written
-      // at the end of the mode: start moving it into L2 now
-      if (!first && tid == 0) {
-        prefetch_l2(a.pacc + ((size_t)slot * K + k) * M * M, (uint32_t)(M * M * 8), keep);
-        if (i == 0) prefetch_l2(a.dacc + (size_t)slot * M * M, (uint32_t)(M * M * 4), keep);
-      }
       if (i == 0) {
         if constexpr (TM) {
 #pragma unroll
@@ -401,15 +401,9 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
         const int ln = line[q];
 #pragma unroll
         for (int h = 0; h < E / 4; ++h) {
-          float2 p[4], po[4];
-          float dold[4];
+          float2 p[4];
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int x = tp[q] + G * (4 * h + jj);
-            p[jj] = __ldg(&Pk[ln * M + x]);
-            po[jj] = first ? make_float2(0.f, 0.f) : ld_hint(&pk[ln * M + x], keep);
-            dold[jj] = (first || i > 0) ? 0.f : ld_hint(&dk[ln * M + x], keep);
-          }
+          for (int jj = 0; jj < 4; ++jj) p[jj] = __ldg(&Pk[ln * M + tp[q] + G * (4 * h + jj)]);
           float2 o[4], c[4];
           if constexpr (TM) {
             float pr[8], ac[8];
@@ -436,8 +430,15 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
             if (!NEAR && ((ln + x) & 1)) psi_new = make_float2(-psi_new.x, -psi_new.y);
             const float2 dpsi = csub(psi_new, cmul(p[jj], o[jj]));
             c[jj] = cadd(c[jj], cconjmul(p[jj], dpsi));
-            st_hint(&pk[ln * M + x], cadd(po[jj], cconjmul(o[jj], dpsi)), keep);
-            if (i == 0) st_hint(&dk[ln * M + x], dold[jj] + cabs2(o[jj]), keep);
+            // the slot's first position sets its partials, the later ones add to them
+            const float2 dp = cconjmul(o[jj], dpsi);
+            if (first) {
+              st_part(&pk[ln * M + x], dp, keep);
+              if (i == 0) st_part(&dk[ln * M + x], cabs2(o[jj]), keep);
+            } else {
+              red_hint(&pk[ln * M + x], dp, keep);
+              if (i == 0) red_hint(&dk[ln * M + x], cabs2(o[jj]), keep);
+            }
           }
           if constexpr (TM) {
             float ac[8];
