@@ -445,10 +445,6 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   PT_CUDA(pl->alloc(&d_dacc, (size_t)pl->slots * MM), "alloc probe partials");
   const size_t nerr = pl->big ? (size_t)N * big_row_blocks(M) : (size_t)pl->slots * K;
   PT_CUDA(pl->alloc(&d_errpart, nerr), "alloc error partials");
-  // detector fields of modes 0 .. K-2 per slot, for the single-problem fused kernel's second pass
-  float2* d_stash = nullptr;
-  if (!pl->big && K > 1 && p.engine != PTYCHO_ENGINE_DM && pl->parts == 0)
-    PT_CUDA(pl->alloc(&d_stash, (size_t)pl->slots * (K - 1) * MM), "alloc detector-field stash");
   float2* d_W = nullptr;
   float* d_R = nullptr;
   if (pl->big) {
@@ -539,7 +535,6 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   fa.hq = d_hq;
   fa.cn = d_cn;
   fa.pacc = d_pacc;
-  fa.stash = d_stash;
   fa.dacc = d_dacc;
   fa.errpart = d_errpart;
 

@@ -44,10 +44,6 @@ struct FusedArgs {
   // pc-DM launches: exit-wave state N x K x M x M (updated in place); dm_init: start it at P o_n
   float2* psi;
   int dm_init;
-  // single-problem launches: the detector fields of modes 0 .. K-2 of the position in flight,
-  // slots x (K - 1) x M x M, so that the second pass reads them instead of propagating again;
-  // null: propagate again
-  float2* stash;
 };
 
 // single-problem fused launch (pc_fused_seq.cu: one CTA per position, modes in sequence) over

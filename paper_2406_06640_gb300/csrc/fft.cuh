@@ -246,21 +246,42 @@ struct Tile {
 // A CTA of T / V threads runs the tile: thread `tid` plays the V virtual
 // threads vtid = tid + v * (T / V), v in [0, V), and keeps V x E registers.
 
+// a[v][k2] *= W_M^(t k2) (INV: times the conjugate) for k2 = 1 .. E-1, t the part of virtual thread
+// v. When the CTA's thread count is a multiple of G every virtual thread of a thread has the same
+// part, and each twiddle is read from shared memory once for all V lines.
+template <int M, int V, bool INV>
+__device__ __forceinline__ void twiddle(float2 (&a)[V][Tile<M>::E], const float2* tw, int tid) {
+  using TL = Tile<M>;
+  constexpr int E = TL::E, G = TL::G, TR = TL::T / V, W = TL::LDW;
+  if constexpr (TR % G == 0) {
+    const int t = tid % G;
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) {
+      const float2 w = tw[t * W + k2];
+#pragma unroll
+      for (int v = 0; v < V; ++v) a[v][k2] = INV ? cmulc(a[v][k2], w) : cmul(a[v][k2], w);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int t = (tid + v * TR) % G;
+#pragma unroll
+      for (int k2 = 1; k2 < E; ++k2) a[v][k2] = INV ? cmulc(a[v][k2], tw[t * W + k2]) : cmul(a[v][k2], tw[t * W + k2]);
+    }
+  }
+}
+
 // ROW layout registers -> COL layout registers (forward 2-D DFT, unscaled).
 // tw: twiddle table, tw[t * (E + 1) + k2] = W_M^(t k2) for t < G.
 // The shared buffer must be free on entry; it is free again on return.
 template <int M, int V>
 __device__ __forceinline__ void fft2_forward(float2 (&a)[V][Tile<M>::E], float2* sm, const float2* tw, int tid) {
   using TL = Tile<M>;
-  constexpr int E = TL::E, G = TL::G, EG = TL::EG, TR = TL::T / V, W = TL::LDW;
+  constexpr int E = TL::E, G = TL::G, EG = TL::EG, TR = TL::T / V;
   // ---- rows: pass 1 (ROW mapping)
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int t = (tid + v * TR) % G;
-    dft<E, false>(a[v]);
-#pragma unroll
-    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmul(a[v][k2], tw[t * W + k2]);
-  }
+  for (int v = 0; v < V; ++v) dft<E, false>(a[v]);
+  twiddle<M, V, false>(a, tw, tid);
   if constexpr (G > 1) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -299,9 +320,8 @@ __device__ __forceinline__ void fft2_forward(float2 (&a)[V][Tile<M>::E], float2*
 #pragma unroll
     for (int j = 0; j < E; ++j) a[v][j] = sm[TL::idxB(t + G * j, c)];
     dft<E, false>(a[v]);
-#pragma unroll
-    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmul(a[v][k2], tw[t * W + k2]);
   }
+  twiddle<M, V, false>(a, tw, tid);
   if constexpr (G > 1) {
     __syncthreads();
 #pragma unroll
@@ -330,7 +350,7 @@ __device__ __forceinline__ void fft2_forward(float2 (&a)[V][Tile<M>::E], float2*
 template <int M, int V>
 __device__ __forceinline__ void fft2_inverse(float2 (&a)[V][Tile<M>::E], float2* sm, const float2* tw, int tid) {
   using TL = Tile<M>;
-  constexpr int E = TL::E, G = TL::G, EG = TL::EG, TR = TL::T / V, W = TL::LDW;
+  constexpr int E = TL::E, G = TL::G, EG = TL::EG, TR = TL::T / V;
   // ---- columns: undo pass 2
   if constexpr (G > 1) {
 #pragma unroll
@@ -353,11 +373,10 @@ __device__ __forceinline__ void fft2_inverse(float2 (&a)[V][Tile<M>::E], float2*
     __syncthreads();
   }
   // ---- columns: undo pass 1, then transpose back
+  twiddle<M, V, true>(a, tw, tid);
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int c = (tid + v * TR) / G, t = (tid + v * TR) % G;
-#pragma unroll
-    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmulc(a[v][k2], tw[t * W + k2]);
     dft<E, true>(a[v]);
 #pragma unroll
     for (int j = 0; j < E; ++j) sm[TL::idxB(t + G * j, c)] = a[v][j];
@@ -394,13 +413,9 @@ __device__ __forceinline__ void fft2_inverse(float2 (&a)[V][Tile<M>::E], float2*
     __syncthreads();
   }
   // ---- rows: undo pass 1
+  twiddle<M, V, true>(a, tw, tid);
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int t = (tid + v * TR) % G;
-#pragma unroll
-    for (int k2 = 1; k2 < E; ++k2) a[v][k2] = cmulc(a[v][k2], tw[t * W + k2]);
-    dft<E, true>(a[v]);
-  }
+  for (int v = 0; v < V; ++v) dft<E, true>(a[v]);
 }
 
 // frequency index of COL-layout register r = i2 * G + k1 for thread part t

@@ -14,17 +14,16 @@
 //             separable, zero padded
 //   R       = sqrt(I_n) / (A^G + eps)  or  sqrt(I_n) / sqrt(I_m + eps^2)     (Fig. 1 box 1)
 //   error  += sum (Ihat - I_n)^2 with I_n = (sqrt I_n)^2, Ihat = (A^G)^2 or I_m
-//   pass 2, k = K-1, 0, 1, .. K-2 (mode K-1 from TMEM, the others from a per-slot stash in global
-//   memory written in pass 1, or propagated again when no stash is given):
+//   pass 2, k = K-1, 0, 1, .. K-2 (mode K-1 from TMEM, the others propagated again):
 //     Psi'_k = R Psi_k;  psi'_k = inverse propagation;  dpsi_k = psi'_k - P_k o_n
 //     c_n   += conj(P_k) dpsi_k                 (TMEM; written once per position)
 //     pacc_k += conj(o_n) dpsi_k, dacc += |o_n|^2   (per-slot partials: reductions at L2 into
 //                                                  the slot's own array, each element always
 //                                                  added to by the same thread, so in a fixed order)
 //
-// Cost against the cluster form: a store and a load of K - 1 detector fields per position (or,
-// without the stash, one more forward propagation for each), in exchange for no exchanges and all
-// SMs busy. Persistent: CTA `slot` takes positions slot,
+// Cost against the cluster form: one more forward propagation for each of K - 1 modes (cheaper on
+// this GPU than a store and a load of their detector fields through L2 and HBM), in exchange for no
+// exchanges and all SMs busy. Persistent: CTA `slot` takes positions slot,
 // slot + slots, ... and owns partial `slot`, so every sum is taken in a fixed order and the
 // iteration is bitwise reproducible.
 //
@@ -52,9 +51,6 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
-}
-__device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
 }
 // stores of the partials, which this kernel never reads back: no memory clobber, so the compiler may
 // move later loads above them
@@ -257,21 +253,10 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
 
     // ---- pass 1: S = sum_k |Psi_k|^2 in Z, each thread on its own detector pixels; the last
     // mode's sum is turned into the blur's input (sqrt for the amplitude model) in place
-    // detector field of mode k of this slot's position in flight: thread-major, so a warp's stores
-    // and loads are contiguous (element (q, r) of thread tid at (q E + r) TR + tid); streamed
-    // (read back once, by this CTA, a few microseconds later)
-    auto stash_of = [&](int k) { return a.stash + ((size_t)slot * (K - 1) + k) * M * M; };
     for (int k = 0; k < K; ++k) {
       exit_wave(k);
       forward();
       const bool last = k == K - 1;
-      if (a.stash && !last) {
-        float2* st = stash_of(k);
-#pragma unroll
-        for (int q = 0; q < V; ++q)
-#pragma unroll
-          for (int r = 0; r < E; ++r) st_hint(&st[(q * E + r) * TR + tid], v[q][r], stream);
-      }
 #pragma unroll
       for (int q = 0; q < V; ++q)
 #pragma unroll
@@ -361,12 +346,6 @@ __global__ void __launch_bounds__(SeqShape<M>::TR, SeqShape<M>::MIN_BLOCKS) pc_s
 #pragma unroll
             for (int j = 0; j < E; ++j) v[q][j] = st_r[q][j];
         }
-      } else if (a.stash) {
-        const float2* st = stash_of(k);
-#pragma unroll
-        for (int q = 0; q < V; ++q)
-#pragma unroll
-          for (int r = 0; r < E; ++r) v[q][r] = __ldcs(&st[(q * E + r) * TR + tid]);
       } else {
         exit_wave(k);
         forward();
