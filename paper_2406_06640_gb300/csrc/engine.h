@@ -117,8 +117,14 @@ struct GemmArgs {
   // its partial product at D + z dsplit; 1 = no split
   int ksplit, kc;
   size_t dsplit;
+  // implicit convolutions: B packed by halo_pack (then the halo kernel runs), or null
+  const uint16_t* Bp;
 };
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
+// the halo kernel's weight order for convolution g (g.B packed into halo_pack_elems(g) bf16 at dst)
+bool halo_conv_supported(const GemmArgs& g);
+size_t halo_pack_elems(const GemmArgs& g);
+cudaError_t halo_pack(const GemmArgs& g, uint16_t* dst, cudaStream_t s);
 
 // update / reduction kernels (update.cu)
 struct UpdateArgs {

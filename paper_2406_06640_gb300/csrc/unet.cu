@@ -417,6 +417,7 @@ struct Conv {
   bool relu;
   float *w, *b, *mw, *vw, *mb, *vb, *gT;
   bf16 *wb, *wr;
+  bf16 *wbp, *wrp;  // wb and wr in the halo kernel's step order (forward and data-gradient convolutions)
 };
 
 }  // namespace
@@ -463,8 +464,8 @@ namespace {
     if (e_ != cudaSuccess) return capi_cuda_fail(e_, what);  \
   } while (0)
 
-cudaError_t gemm(ptycho_unet_s* u, const void* A, const void* B, void* D, int M, int N, int K, int ldd, int mode,
-                 const float* bias, int relu, const Conv* conv, Split sp = Split{1, 0}) {
+GemmArgs gemm_args(ptycho_unet_s* u, const void* A, const void* B, void* D, int M, int N, int K, int ldd, int mode,
+                   const float* bias, int relu, const Conv* conv, Split sp = Split{1, 0}, const bf16* Bp = nullptr) {
   GemmArgs g{};
   g.ksplit = sp.ks;
   g.kc = sp.kc;
@@ -487,7 +488,13 @@ cudaError_t gemm(ptycho_unet_s* u, const void* A, const void* B, void* D, int M,
     g.W = conv->W;
     g.Cin = conv->Cin;
   }
-  return launch_gemm_bf16(g, u->stream);
+  g.Bp = reinterpret_cast<const uint16_t*>(Bp);
+  return g;
+}
+
+cudaError_t gemm(ptycho_unet_s* u, const void* A, const void* B, void* D, int M, int N, int K, int ldd, int mode,
+                 const float* bias, int relu, const Conv* conv, Split sp = Split{1, 0}, const bf16* Bp = nullptr) {
+  return launch_gemm_bf16(gemm_args(u, A, B, D, M, N, K, ldd, mode, bias, relu, conv, sp, Bp), u->stream);
 }
 
 // weight-gradient contraction over the transposed shifted copies (GemmArgs::convT)
@@ -516,8 +523,8 @@ cudaError_t gemm_wgrad_T(ptycho_unet_s* u, const Conv& L, const bf16* XT3, const
 // forward of one convolution: out (n, H, W, Cp) bf16 with bias and ReLU, or fp32 without bias
 cudaError_t conv_forward(ptycho_unet_s* u, Conv& L, const bf16* in, bf16* out_bf16, float* out_f32) {
   const int M = u->nrun * L.H * L.W;
-  if (out_bf16) return gemm(u, in, L.wb, out_bf16, M, L.Cp, L.Kf, L.Cp, 2, L.b, L.relu ? 1 : 0, &L);
-  return gemm(u, in, L.wb, out_f32, M, L.Cp, L.Kf, L.Cp, 0, nullptr, 0, &L);
+  if (out_bf16) return gemm(u, in, L.wb, out_bf16, M, L.Cp, L.Kf, L.Cp, 2, L.b, L.relu ? 1 : 0, &L, Split{1, 0}, L.wbp);
+  return gemm(u, in, L.wb, out_f32, M, L.Cp, L.Kf, L.Cp, 0, nullptr, 0, &L, Split{1, 0}, L.wbp);
 }
 
 // backward of one convolution given dY (n, H, W, Cp) bf16: weight gradient (into L.gT) and, when dX != nullptr,
@@ -543,7 +550,7 @@ cudaError_t conv_backward(ptycho_unet_s* u, Conv& L, const bf16* in, const bf16*
   if (e != cudaSuccess || !dX) return e;
   Conv R = L;  // the data gradient gathers dY with Cp channels
   R.Cin = L.Cp;
-  return gemm(u, dY, L.wr, dX, M, L.Cin, L.Kd, L.Cin, 0, nullptr, 0, &R);
+  return gemm(u, dY, L.wr, dX, M, L.Cin, L.Kd, L.Cin, 0, nullptr, 0, &R, Split{1, 0}, L.wrp);
 }
 
 }  // namespace
@@ -563,6 +570,24 @@ static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev) {
       k_weights_bf16<<<grid_for((size_t)u->L[i].Cp * u->L[i].Kf + (size_t)u->L[i].Cin * u->L[i].Kd), 256, 0, s>>>(
           u->L[i].w, u->L[i].wb, i == 0 ? nullptr : u->L[i].wr, u->L[i].Cp, u->L[i].Cin, u->L[i].Kw, u->L[i].Kf,
           u->L[i].Kd);
+    // and in the halo kernel's step order (forward, and the data gradient's transposed taps)
+    for (int i = 0; i < 7; ++i) {
+      Conv& L = u->L[i];
+      const int M = u->nrun * L.H * L.W;
+      const GemmArgs gf = gemm_args(u, nullptr, L.wb, nullptr, M, L.Cp, L.Kf, L.Cp, 2, L.b, 1, &L);
+      if (halo_conv_supported(gf)) {
+        const cudaError_t e = halo_pack(gf, reinterpret_cast<uint16_t*>(L.wbp), s);
+        if (e != cudaSuccess) return e;
+      }
+      if (i == 0) continue;  // the input's gradient is not needed
+      Conv R = L;
+      R.Cin = L.Cp;
+      const GemmArgs gd = gemm_args(u, nullptr, L.wr, nullptr, M, L.Cin, L.Kd, L.Cin, 0, nullptr, 0, &R);
+      if (halo_conv_supported(gd)) {
+        const cudaError_t e = halo_pack(gd, reinterpret_cast<uint16_t*>(L.wrp), s);
+        if (e != cudaSuccess) return e;
+      }
+    }
     u->wb_fresh = true;
   }
   cudaError_t e;
@@ -719,7 +744,9 @@ ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t s
         (e = u->alloc(&L.vw, (size_t)L.Cp * L.Kw)) != cudaSuccess || (e = u->alloc(&L.mb, L.Cp)) != cudaSuccess ||
         (e = u->alloc(&L.vb, L.Cp)) != cudaSuccess || (e = u->alloc(&L.gT, (size_t)L.Kw * L.Cp)) != cudaSuccess ||
         (e = u->alloc(&L.wb, (size_t)L.Cp * L.Kf)) != cudaSuccess ||
-        (e = u->alloc(&L.wr, (size_t)L.Cin * L.Kd)) != cudaSuccess)
+        (e = u->alloc(&L.wr, (size_t)L.Cin * L.Kd)) != cudaSuccess ||
+        (e = u->alloc(&L.wbp, (size_t)L.Cp * L.Kf)) != cudaSuccess ||
+        (e = u->alloc(&L.wrp, (size_t)L.Cin * L.Kd)) != cudaSuccess)
       return fail_alloc(e);
     if (hs[i] % 8) colT_max = std::max(colT_max, (size_t)L.Kw * batch * hs[i] * hs[i]);
     else xt3_max = std::max(xt3_max, (size_t)3 * L.Cin * batch * hs[i] * hs[i]);

@@ -22,8 +22,10 @@
 // Every mbarrier wait is bounded (wall-clock limit via %globaltimer): on
 // timeout the kernel raises *status, waits once more (bounded), frees TMEM and
 // returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "engine.h"
@@ -364,36 +366,92 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_bf16(const GemmArgs g) {
 // ------------------------------------------------------------------ 3x3 convolution on a halo slab
 // The implicit GEMM of a 'same' 3x3 convolution, D[p, n] = sum_{tap, c} X[p + tap offset, c] W[n, tap Cin + c],
 // with the operand A read from one slab per chunk of up to 64 input channels instead of one gather per
-// tap. Output positions are indexed over the zero-padded grid, P = (b (H + 2) + y + 1) (W + 2) + x + 1,
-// so that tap (dy, dx) of every output lies at the fixed offset dy (W + 2) + dx: a CTA owning the
-// positions [P0, P0 + 128 T) (T accumulators of 128 rows in TMEM) copies the padded rows
-// [P0 - (W + 3), P0 + 128 T + W + 3] of its channel chunk once (zero outside the image, so the border
-// needs no masking) and every tap's MMA reads that slab through a descriptor shifted by the tap's
-// offset. Positions on the padding are computed and dropped by the epilogue (3 % of the work at
-// 128 x 128, 21 % at 16 x 16). The weights of each (chunk, tap) step feed all T accumulators.
+// tap. Output positions are indexed over a zero-padded grid whose rows hold Wp = (W + 2) rounded up to a
+// multiple of 8 positions, P = (b (H + 2) + y + 1) Wp + x + 1, so that tap (dy, dx) of every output lies
+// at the fixed offset dy Wp + dx: a tile of positions [P0, P0 + 128 T) (T accumulators of 128 rows in
+// TMEM) reads the whole padded rows holding positions [P0 - Wp - 1, P0 + 128 T + Wp + 1) of its channel
+// chunk once (zero outside the image, so the border needs no masking) and every tap's MMA reads that
+// slab through a descriptor shifted by the tap's offset. Positions on the padding are computed and
+// dropped by the epilogue. The weights of each (chunk, tap) step feed all T accumulators.
 //
-// Shared-memory layouts (canonical K-major, no swizzle; a core matrix = 8 rows x 16 bytes):
-//   slab  [k group g][row j]  16 bytes each: LBO (next k group) = R * 16, SBO (next 8 rows) = 128
-//   B     [k group g][n]      16 bytes each: LBO = N * 16, SBO = 128
+// Every copy is done by the tensor-memory-access engine: a slab is one box per padded row (Wp
+// positions x the chunk's channels, from a 4-D view (C, W, H, batch) of the NHWC input; the padding
+// columns and rows read as out-of-bounds zeros, and every box starts on a 1024-byte boundary of the
+// slab, rows being a multiple of 8 positions long). The weights arrive packed in step order
+// (halo_pack), one bulk copy per step. Each copy instruction costs its issuing thread a few hundred
+// cycles, so the slabs and the weights have a thread each and the boxes are as large as a row.
+//
+// Shared-memory layouts (canonical K-major):
+//   64-channel chunks: rows of 128 bytes, 16-byte chunk q of row j at q ^ (j % 8) (128-byte swizzle,
+//     written so by the copy engine), slab and weights alike
+//   narrower chunks (8, 16, 32 channels), no swizzle, a core matrix = 8 rows x 16 bytes:
+//     slab  [k group g][row j]  16 bytes each: LBO (next k group) = R * 16, SBO (next 8 rows) = 128
+//     B     [k group g][n]      16 bytes each: LBO = N * 16, SBO = 128
 // Cin = 8 (the network's input, one channel padded to 8) holds one k group per tap: an MMA then takes
 // taps t and t + 1 as its two k groups (LBO = the distance between their offsets), and the ninth tap
 // is paired with zero weight columns.
 namespace {
-constexpr int kHaloProducers = kThreads - 32;  // warps 0-6 copy, warp 7 issues the MMAs
+// roles: warp 0 lane 0 copies the slabs (and warp 0 owns the TMEM allocation), warp 1 lane 0 issues
+// the MMAs, warps 2-5 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31), warp 6
+// lane 0 copies the weights
+constexpr int kHaloThreads = 224;
+constexpr int kHaloLoader = 0;
+constexpr int kHaloIssuer = 32;
+constexpr int kHaloEpi0 = 64;
+constexpr int kHaloWeights = 192;
+constexpr int kHaloSMax = 8;  // weight stages at most
+constexpr int kHaloBufMax = 3;  // slab buffers at most
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> own shared memory by the bulk-copy engine; both addresses 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// one box of a 4-D tensor map into shared memory (coordinates innermost first; out-of-range elements
+// read as zero)
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
 
 template <int N, int T>
 struct HaloCfg {
-  // B ring: S stages; the copies of a step are issued D - 1 steps before its MMAs, so D - 1 steps of
-  // copies and S - D + 1 steps of MMAs are in flight at once (two of each at N >= 128, where one step is
-  // ~0.6 us of tensor work; three steps of copies below, where a step is shorter)
-  static constexpr int S = N >= 128 ? 4 : 6;
-  static constexpr int D = N >= 128 ? 3 : 4;
-  static constexpr uint32_t NCOLS = N < 32 ? 32 : N;           // TMEM columns per accumulator
-  static constexpr size_t B_STAGE = (size_t)N * 64 * 2;         // N rows x 64 k (the widest chunk)
-  __host__ __device__ static size_t rows(int W) { return (size_t)(128 * T + 2 * W + 8 + 7) / 8 * 8; }
+  static constexpr uint32_t NCOLS = N < 32 ? 32 : N;                 // TMEM columns per accumulator
+  static constexpr uint32_t ACC = NCOLS * T;                          // one accumulator set (a tile)
+  static constexpr uint32_t TMEM_COLS = 2 * ACC < 32 ? 32 : 2 * ACC;  // two sets: fill one, drain the other
+  static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
+  static constexpr size_t B_STAGE = (size_t)N * 64 * 2;  // N rows x 64 k (the widest chunk)
+  __host__ __device__ static int wp(int W) { return (W + 2 + 7) / 8 * 8; }
+  // whole padded rows covering positions [P0 - Wp - 1, P0 + 128 T + Wp + 2) for any P0 (a multiple of 8;
+  // the row holding P0 - Wp - 1 starts at P0 - 2 Wp at the earliest, and the ninth tap's pair partner
+  // reads one position past the last output's tap)
+  __host__ __device__ static int rows(int W) {
+    const int w = wp(W);
+    return ((128 * T + 3 * w + 2 + w - 1) / w) * w;
+  }
   // KG k groups (8 channels each) of 16 bytes per row
-  __host__ __device__ static size_t slab_bytes(int W, int KG) { return rows(W) * 16 * KG; }
-  __host__ __device__ static size_t smem(int W, int KG) { return 2 * slab_bytes(W, KG) + S * B_STAGE; }
+  __host__ __device__ static size_t slab_bytes(int W, int KG) { return (size_t)rows(W) * 16 * KG; }
+  // weight stages S and slab buffers nbuf within `budget` bytes: three buffers (the slab copies run two
+  // chunks ahead of the MMAs) when six weight stages still fit beside them (the weights' copies must
+  // run five steps ahead to hide their latency), else two
+  static bool plan(int W, int KG, size_t budget, int& S, int& nbuf) {
+    for (nbuf = kHaloBufMax; nbuf >= 2; --nbuf) {
+      const size_t sb = nbuf * slab_bytes(W, KG);
+      if (sb >= budget) continue;
+      const size_t n = (budget - sb) / B_STAGE;
+      S = n > (size_t)kHaloSMax ? kHaloSMax : (int)n;
+      if (S >= (nbuf == 3 ? 6 : 2)) return true;
+    }
+    return false;
+  }
 };
 
 __device__ __forceinline__ void mma_bf16_acc(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -402,157 +460,193 @@ __device__ __forceinline__ void mma_bf16_acc(uint32_t tmem_d, uint64_t adesc, ui
 }
 }  // namespace
 
-template <int N, int T, bool SW>
-__global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) {
+// PN (pixels as the MMA's N): for outputs of 128 channels per column block and 64-channel chunks the
+// operands swap, D^T[channel][position] = W . X^T: the packed weights are A (M = 128 channels) and the
+// slab is B (N = 256 positions), so that one instruction computes 128 x 256 x 16 (a 128 x 128 x 16
+// instruction issues at about half the FLOP rate of a 128 x 256 x 16 one). The tile geometry is that of
+// N = 128, T = 2 (256 positions, 256 TMEM columns); TMEM lane = channel, column = position.
+//
+// Persistent: CTA b takes tiles b, b + grid, ... (a tile = 128 T padded positions x N output channels;
+// consecutive tiles share the positions, so a slab is read from HBM once and from L2 by the other
+// column blocks). Steps (chunk, tap) run back to back across tiles; the copies of the next chunk's slab
+// (also when it is the next tile's first) overlap the current chunk's MMAs, and the MMAs of tile l + 1
+// fill one TMEM accumulator set while the epilogue warps drain tile l's.
+template <int N, int T, bool SW, bool PN>
+__global__ void __launch_bounds__(kHaloThreads, 1)
+    k_conv3x3_halo(const GemmArgs g, const __grid_constant__ CUtensorMap tmx, int ntiles_px, int S, int nbuf) {
   using HC = HaloCfg<N, T>;
-  constexpr int S = HC::S, D = HC::D;
+  static_assert(!PN || (N == 128 && T == 2 && SW), "swapped operands: 128 channels x 256 positions, 64-channel chunks");
   extern __shared__ __align__(1024) unsigned char smem[];
-  // full[st]: the producers' copies of the step in stage st landed (one arrival per producer thread);
-  // bar[st]: the MMAs reading stage st are done (tcgen05.commit); sbar[b]: those of slab buffer b
-  __shared__ uint64_t bar[S], full[S], sbar[2];
+  // bfull[st]: the weights of the step in stage st landed (transaction bytes); sfull[b]: the slab in
+  // buffer b landed; bar[st]: the MMAs reading stage st are done (tcgen05.commit); sbar[b]: those of
+  // slab buffer b; accf[a]: accumulator set a holds a finished tile; acce[a]: the epilogue has read
+  // set a; drain: every MMA issued has completed
+  __shared__ uint64_t bar[kHaloSMax], bfull[kHaloSMax], sfull[kHaloBufMax], sbar[kHaloBufMax], accf[2], acce[2],
+      drain;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int H = g.H, W = g.W, Cin = g.Cin;
-  const int Wp = W + 2, HWp = (H + 2) * Wp;
+  const int Wp = HC::wp(W), HWp = (H + 2) * Wp;
   const int nb = g.M / (H * W);
-  const long long Mp = (long long)nb * HWp;
-  const long long P0 = (long long)blockIdx.x * 128 * T;
-  const int n0 = blockIdx.y * N;
-  const int R = (int)HC::rows(W);
+  const int Mpi = nb * HWp;  // padded positions fit in 32 bits (checked at launch)
+  const int R = HC::rows(W);
   const int CC = Cin < 64 ? Cin : 64;   // channels per chunk
   const int KG = CC / 8;                // k groups per chunk
   const uint32_t slab_bytes = (uint32_t)HC::slab_bytes(W, KG);
   const int nchunks = Cin / CC;
   const bool pairs = Cin == 8;          // two taps per MMA
   const int taps = pairs ? 5 : 9;       // steps per chunk
-  const int nsteps = nchunks * taps;
-  const int Kw = g.K;                   // row length of the weights
-  constexpr uint32_t NCOLS_ALL = HC::NCOLS * T < 32 ? 32 : HC::NCOLS * T;
+  const int nsteps = nchunks * taps;    // steps per tile
+  const int nblk = g.Ntot / N;
+  const int ntiles = ntiles_px * nblk;
+  const int L = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total = L * nsteps;         // steps of this CTA
+  auto tile_of = [&](int l) { return (int)blockIdx.x + l * (int)gridDim.x; };
 
-  if (warp == 0) tm_alloc(&s_tmem, NCOLS_ALL);
+  if (warp == 0) tm_alloc(&s_tmem, HC::TMEM_COLS);
   if (tid == 0) {
-    for (int i = 0; i < S; ++i) {
+    for (int i = 0; i < kHaloSMax; ++i) {
       mbar_init(&bar[i], 1);
-      mbar_init(&full[i], kHaloProducers);
+      mbar_init(&bfull[i], 1);
     }
-    mbar_init(&sbar[0], 1);
-    mbar_init(&sbar[1], 1);
+    for (int i = 0; i < kHaloBufMax; ++i) {
+      mbar_init(&sfull[i], 1);
+      mbar_init(&sbar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 128);
+    }
+    mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = make_idesc(128, N);
+  const uint32_t idesc = PN ? make_idesc(128, 256) : make_idesc(128, N);
   const uint32_t base = smem_u32(smem);
-  const uint32_t slab0 = base, bring = base + 2 * slab_bytes;
-  const __nv_bfloat16* X = reinterpret_cast<const __nv_bfloat16*>(g.A);
-  const __nv_bfloat16* B = reinterpret_cast<const __nv_bfloat16*>(g.B) + (size_t)n0 * Kw;
+  const uint32_t slab0 = base, bring = base + (uint32_t)nbuf * slab_bytes;
+  // slab row j of a tile starting at P0 holds position S0 + j, S0 = the start of the padded row holding
+  // P0 - Wp - 1; output row r of accumulator m reads, for tap (dy, dx), slab row
+  // (P0 - S0) + 128 m + r + dy Wp + dx
+  auto slab_start = [&](int P0) {
+    const int P = P0 - Wp - 1;
+    return (P >= 0 ? P / Wp : -((-P + Wp - 1) / Wp)) * Wp;  // floor to a row start
+  };
 
-  // slab row j, k group q: [q][j] (no swizzle) or row j of 128 bytes with chunk q at q ^ (j % 8) (swizzled)
-  auto slab_at = [&](uint32_t buf, int j, int q) {
-    return SW ? buf + (uint32_t)(j * 128 + ((q ^ (j & 7)) << 4)) : buf + (uint32_t)((q * R + j) * 16);
-  };
-  // element offset in X of slab row j's pixel, or -1 on the padding / outside the tensor
-  const int P0i = (int)P0, Mpi = (int)Mp;  // padded positions fit in 32 bits (checked at launch)
-  auto row_off = [&](int j) -> long long {
-    const int P = P0i - (W + 3) + j;
-    if (P < 0 || P >= Mpi) return -1;
-    const int b = P / HWp, r = P - b * HWp;
-    const int yp = r / Wp, xp = r - yp * Wp;
-    if (yp < 1 || yp > H || xp < 1 || xp > W) return -1;
-    return (((long long)b * H + (yp - 1)) * W + (xp - 1)) * Cin;
-  };
-  // copies: the k groups of one row are adjacent threads (a warp reads whole 16 KG-byte pixel chunks)
-  auto stage_slab = [&](int chunk, uint32_t dst) {
-    const int c0 = chunk * CC;
-    for (int i = tid; i < R * KG; i += kHaloProducers) {
-      const int j = i / KG, q = i % KG;
-      const long long o = row_off(j);
-      cp_async16(slab_at(dst, j, q), o >= 0 ? X + o + c0 + q * 8 : X, o >= 0 ? 16u : 0u);
-    }
-  };
-  // weights of step st: k columns [k0, k0 + 8 KGB) -> [k group][n] (no swizzle) or swizzled rows of n
-  auto stage_b = [&](int st, uint32_t dst) {
-    const int chunk = st / taps, t = st % taps;
-    const int kgb = pairs ? 2 : KG;
-    const int k0 = pairs ? 16 * t : t * Cin + chunk * CC;
-    for (int i = tid; i < N * kgb; i += kHaloProducers) {
-      const int n = i / kgb, q = i % kgb;
-      const uint32_t d = SW ? dst + (uint32_t)(n * 128 + ((q ^ (n & 7)) << 4)) : dst + (uint32_t)((q * N + n) * 16);
-      cp_async16(d, B + (size_t)n * Kw + k0 + q * 8, 16u);
-    }
-  };
-  auto tap_off = [&](int t) { return (t / 3 - 1) * Wp + (t % 3 - 1); };
-
-  // warp-specialised main loop, no CTA-wide barrier inside:
-  //   producers (warps 0-6): copies of step i into stage i % S once the MMAs of step i - S are done
-  //     (bar), then, D - 1 steps later, wait for their own copies of that step, make them visible to
-  //     the tensor core's (async) proxy and arrive on full[stage];
-  //   MMA issuer (warp 7, lane 0): waits on full[stage] of step j, issues its MMAs, commits to bar.
   bool ok = true;
-  if (tid < kHaloProducers) {
-    for (int i = 0; i < nsteps + D - 1 && ok; ++i) {
-      if (i < nsteps) {
-        const int st = i % S;
-        if (i >= S) ok = mbar_wait_bounded(&bar[st], (uint32_t)((i / S - 1) & 1));
-        const int chunk = i / taps;
-        if (ok && i % taps == 0 && chunk >= 2)  // the MMAs of chunk - 2 read this slab buffer
-          ok = mbar_wait_bounded(&sbar[chunk & 1], (uint32_t)(((chunk - 2) >> 1) & 1));
-        if (ok) {
-          if (i % taps == 0) stage_slab(chunk, slab0 + (uint32_t)(chunk & 1) * slab_bytes);
-          stage_b(i, bring + (uint32_t)(st * HC::B_STAGE));
+  if (tid == kHaloLoader) {
+    // the slab of chunk gc of this CTA (tile gc / nchunks, channel chunk gc % nchunks) into buffer
+    // gc % nbuf, as soon as the MMAs of chunk gc - nbuf (the buffer's last reader) are done: one box per
+    // padded row (image row yp - 1 of image b, columns -1 .. Wp - 2; out of range = zeros)
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+    const int nchunks_all = L * nchunks;
+    const int rows_per = R / Wp;
+    int nslab = 0;  // slabs issued (chunks 0 .. nslab - 1)
+    for (int gc = 0; gc < nchunks_all && ok; ++gc) {
+      if (gc >= nbuf) ok = mbar_wait_bounded(&sbar[gc % nbuf], (uint32_t)(((gc - nbuf) / nbuf) & 1));
+      if (!ok) break;
+      const int l = gc / nchunks, c = gc - l * nchunks;
+      const int row0 = slab_start((tile_of(l) / nblk) * 128 * T) / Wp;  // padded row index (may be < 0)
+      const uint32_t buf = slab0 + (uint32_t)(gc % nbuf) * slab_bytes;
+      uint64_t* fb = &sfull[gc % nbuf];
+      mbar_expect_tx(fb, slab_bytes);
+      for (int r = 0; r < rows_per; ++r) {
+        const int pr = row0 + r;
+        const int b = pr >= 0 ? pr / (H + 2) : -1;  // before the first image: all zeros
+        const int yp = pr >= 0 ? pr - b * (H + 2) : 0;
+        if (SW) {
+          tma_load_4d(buf + (uint32_t)(r * Wp * 128), &tmx, c * 64, -1, yp - 1, b, fb);
+        } else {
+          for (int q = 0; q < KG; ++q)
+            tma_load_4d(buf + (uint32_t)((q * R + r * Wp) * 16), &tmx, c * CC + q * 8, -1, yp - 1, b, fb);
         }
       }
-      cp_async_commit();  // one group per iteration (possibly empty) keeps the group count aligned
-      const int j = i - (D - 1);
-      if (ok && j >= 0 && j < nsteps) {
-        cp_async_wait<D - 1>();  // this thread's copies of step j (groups up to i are committed)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&full[j % S]);
-      }
+      nslab = gc + 1;
     }
-    cp_async_wait<0>();
-  } else if (tid == kHaloProducers) {
-    for (int j = 0; j < nsteps && ok; ++j) {
-      ok = mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1));
+    // no copy may still be writing shared memory when the CTA ends (normally the MMAs consumed them all)
+    for (int gc = nslab - nbuf > 0 ? nslab - nbuf : 0; gc < nslab; ++gc)
+      if (!mbar_wait_bounded(&sfull[gc % nbuf], (uint32_t)((gc / nbuf) & 1))) ok = false;
+  } else if (tid == kHaloWeights) {
+    // weights: step gs's block of the packed weights (column block of its tile, step within the tile)
+    // into stage gs % S once the MMAs of step gs - S are done; one bulk copy, completing on bfull
+    const int kgb = pairs ? 2 : KG;
+    const uint32_t bbytes = (uint32_t)(N * kgb * 16);
+    int issued = 0;
+    for (int gs = 0; gs < total && ok; ++gs) {
+      const int st = gs % S;
+      if (gs >= S) ok = mbar_wait_bounded(&bar[st], (uint32_t)((gs / S - 1) & 1));
+      if (!ok) break;
+      const int l = gs / nsteps, i = gs - l * nsteps;
+      const int nbk = tile_of(l) % nblk;
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(g.Bp) + ((size_t)nbk * nsteps + i) * bbytes;
+      mbar_expect_tx(&bfull[st], bbytes);
+      bulk_g2s(bring + (uint32_t)(st * HC::B_STAGE), src, bbytes, &bfull[st]);
+      issued = gs + 1;
+    }
+    for (int gs = issued - S > 0 ? issued - S : 0; gs < issued; ++gs)
+      if (!mbar_wait_bounded(&bfull[gs % S], (uint32_t)((gs / S) & 1))) ok = false;
+  } else if (tid == kHaloIssuer) {
+    // MMA issuer: at a tile's first step waits for the epilogue to have read the accumulator set it is
+    // about to overwrite, at a chunk's first step for its slab, at every step for its weights; issues the
+    // step's MMAs and commits them to bar (and to sbar / accf at a chunk's / tile's last step)
+    for (int gs = 0; gs < total && ok; ++gs) {
+      const int l = gs / nsteps, i = gs - l * nsteps;
+      const int chunk = i / taps, t = i - chunk * taps;
+      const int gc = l * nchunks + chunk;
+      const int st = gs % S;
+      if (i == 0 && l >= 2) ok = mbar_wait_bounded(&acce[l & 1], (uint32_t)(((l >> 1) - 1) & 1));
+      if (ok && t == 0) ok = mbar_wait_bounded(&sfull[gc % nbuf], (uint32_t)((gc / nbuf) & 1));
+      if (ok) ok = mbar_wait_bounded(&bfull[st], (uint32_t)((gs / S) & 1));
       if (!ok) break;
       // lean issue: a descriptor is linear in its start address ((start >> 4) in the low bits, no carry
       // below 256 KB), so every MMA's descriptors are a base plus a constant; the issuing thread must
       // keep ahead of the tensor pipe (~64-128 cycles per MMA)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int st = j % S, chunk = j / taps, t = j % taps;
-      const uint32_t slab = slab0 + (uint32_t)(chunk & 1) * slab_bytes;
+      const uint32_t slab = slab0 + (uint32_t)(gc % nbuf) * slab_bytes;
       const uint32_t bs = bring + (uint32_t)(st * HC::B_STAGE);
-      const uint32_t first = j == 0 ? 0u : 1u;  // the first MMA of each accumulator overwrites it
-      if (pairs) {
+      const uint32_t acc0 = tmem + (uint32_t)(l & 1) * HC::ACC;
+      const uint32_t first = i == 0 ? 0u : 1u;  // the first MMA of each accumulator overwrites it
+      const int P0 = (tile_of(l) / nblk) * 128 * T;
+      const int off0 = P0 - slab_start(P0);
+      auto tap_row = [&](int tp) { return off0 + (tp / 3 - 1) * Wp + (tp % 3 - 1); };
+      if constexpr (PN) {
+        // A = the weights (128 channel rows), B = 256 slab rows from the tap's offset; K in steps of 16
+        const uint64_t aw = make_desc_sw128(bs);
+        const uint64_t bp = make_desc_sw128(slab + (uint32_t)(tap_row(t) * 128));
+        mma_bf16_acc(acc0, aw, bp, idesc, first);
+        mma_bf16_acc(acc0, aw + 2, bp + 2, idesc, 1u);
+        mma_bf16_acc(acc0, aw + 4, bp + 4, idesc, 1u);
+        mma_bf16_acc(acc0, aw + 6, bp + 6, idesc, 1u);
+      } else if (pairs) {
         // taps 2t and 2t + 1 (the ninth with the row after it, whose weights are zero)
-        const int ta = 2 * t, oa = tap_off(ta);
-        const int ob = ta + 1 < 9 ? tap_off(ta + 1) : oa + 1;
-        const uint64_t ad = make_desc(slab + (uint32_t)((W + 3 + oa) * 16), (uint32_t)((ob - oa) * 16), 128);
+        const int ta = 2 * t, ra = tap_row(ta);
+        const int rb = ta + 1 < 9 ? tap_row(ta + 1) : ra + 1;
+        const uint64_t ad = make_desc(slab + (uint32_t)(ra * 16), (uint32_t)((rb - ra) * 16), 128);
         const uint64_t bd = make_desc(bs, (uint32_t)(N * 16), 128);
 #pragma unroll
         for (int m = 0; m < T; ++m)
-          mma_bf16_acc(tmem + (uint32_t)(m * HC::NCOLS), ad + (uint64_t)(128 * m), bd, idesc, first);
+          mma_bf16_acc(acc0 + (uint32_t)(m * HC::NCOLS), ad + (uint64_t)(128 * m), bd, idesc, first);
       } else if constexpr (SW) {
         // rows X .. X + 127 of the slab, K in steps of 16 (32 bytes = 2 descriptor units along each row)
-        const uint64_t ad = make_desc_sw128(slab + (uint32_t)((W + 3 + tap_off(t)) * 128));
+        const uint64_t ad = make_desc_sw128(slab + (uint32_t)(tap_row(t) * 128));
         const uint64_t bd = make_desc_sw128(bs);
 #pragma unroll
         for (int m = 0; m < T; ++m) {
           const uint64_t am = ad + (uint64_t)(1024 * m);  // 128 rows of 128 bytes, in 16-byte units
-          const uint32_t acc = tmem + (uint32_t)(m * HC::NCOLS);
+          const uint32_t acc = acc0 + (uint32_t)(m * HC::NCOLS);
           mma_bf16_acc(acc, am, bd, idesc, first);
           mma_bf16_acc(acc, am + 2, bd + 2, idesc, 1u);
           mma_bf16_acc(acc, am + 4, bd + 4, idesc, 1u);
           mma_bf16_acc(acc, am + 6, bd + 6, idesc, 1u);
         }
       } else {
-        const uint64_t ad = make_desc(slab + (uint32_t)((W + 3 + tap_off(t)) * 16), (uint32_t)(R * 16), 128);
+        const uint64_t ad = make_desc(slab + (uint32_t)(tap_row(t) * 16), (uint32_t)(R * 16), 128);
         const uint64_t bd = make_desc(bs, (uint32_t)(N * 16), 128);
 #pragma unroll
         for (int m = 0; m < T; ++m) {
-          const uint32_t acc = tmem + (uint32_t)(m * HC::NCOLS);
+          const uint32_t acc = acc0 + (uint32_t)(m * HC::NCOLS);
           const uint64_t am = ad + (uint64_t)(128 * m);  // 128 rows of 16 bytes
 #pragma unroll 1
           for (int q = 0; q < KG; q += 2)  // k groups q, q + 1: R rows of 16 bytes each further
@@ -560,93 +654,193 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_halo(const GemmArgs g) 
         }
       }
       mma_commit(&bar[st]);
-      if (t == taps - 1) mma_commit(&sbar[chunk & 1]);
+      if (t == taps - 1) mma_commit(&sbar[gc % nbuf]);
+      if (i == nsteps - 1) mma_commit(&accf[l & 1]);
     }
-  }
-  ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  if (ok && nsteps > 0)  // the last step's commit covers every MMA issued before it
-    ok = __syncthreads_and(mbar_wait_bounded(&bar[(nsteps - 1) % S], (uint32_t)(((nsteps - 1) / S) & 1)) ? 1 : 0) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok) {
-    if (tid == 0) atomicExch(g.status, 1);
-    for (int st = 0; st < S; ++st) mbar_wait_bounded(&bar[st], 0u), mbar_wait_bounded(&bar[st], 1u);
-    for (int b2 = 0; b2 < 2; ++b2) mbar_wait_bounded(&sbar[b2], 0u), mbar_wait_bounded(&sbar[b2], 1u);
-  } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of every accumulator, every other group of 16
-    // columns starting at 16 (w / 4); positions on the padding are dropped
-    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    long long pix[T];
-#pragma unroll
-    for (int m = 0; m < T; ++m) {
-      const int P = P0i + 128 * m + (warp & 3) * 32 + lane;
-      pix[m] = -1;
-      if (P < Mpi) {
-        const int b = P / HWp, r = P - b * HWp;
-        const int yp = r / Wp, xp = r - yp * Wp;
-        if (yp >= 1 && yp <= H && xp >= 1 && xp <= W) pix[m] = ((long long)b * H + (yp - 1)) * W + (xp - 1);
-      }
-    }
+    mma_commit(&drain);  // completes once every MMA this thread issued has
+    if (!mbar_wait_bounded(&drain, 0u)) ok = false;
+  } else if (tid >= kHaloEpi0 && tid < kHaloEpi0 + 128) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of every accumulator of the finished tile;
+    // positions on the padding are dropped
+    const int eq = warp & 3;
+    const uint32_t tl = tmem + ((uint32_t)(eq * 32) << 16);
+    for (int l = 0; l < L && ok; ++l) {
+      // one decision per warp: the TMEM loads below are warp-collective
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf[l & 1], (uint32_t)((l >> 1) & 1)));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int tile = tile_of(l);
+      const int P0i = (tile / nblk) * 128 * T, n0 = (tile % nblk) * N;
+      const uint32_t ta = tl + (uint32_t)(l & 1) * HC::ACC;
+      if constexpr (PN) {
+        // lane = channel n0 + 32 eq + lane, column = position P0i + column; 32 columns at a time, lane j
+        // decoding the position of column j for the warp
+        const int n = n0 + eq * 32 + lane;
+        const float bn = (g.mode == 2 && g.bias) ? g.bias[n] : 0.f;
 #pragma unroll 1
-    for (int c0 = (warp >> 2) * 16; c0 < N; c0 += 32) {
-      float bias[16];
-#pragma unroll
-      for (int jj = 0; jj < 16; ++jj) bias[jj] = (g.mode == 2 && g.bias) ? g.bias[n0 + c0 + jj] : 0.f;
-#pragma unroll
-      for (int m = 0; m < T; ++m) {
-        float v[16];
-        tm_ld16(tl + (uint32_t)(m * HC::NCOLS + c0), v);
-        if (pix[m] < 0) continue;
-        if (g.mode == 2) {
-          float o[16];
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const float x = v[jj] + bias[jj];
-            o[jj] = g.relu ? fmaxf(x, 0.f) : x;
+        for (int cb = 0; cb < 256; cb += 32) {
+          long long mypix = -1;
+          const int P = P0i + cb + lane;
+          if (P < Mpi) {
+            const int b = P / HWp, r = P - b * HWp;
+            const int yp = r / Wp, xp = r - yp * Wp;
+            if (yp >= 1 && yp <= H && xp >= 1 && xp <= W) mypix = ((long long)b * H + (yp - 1)) * W + (xp - 1);
           }
-          uint4 w0, w1;
-          __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&w0);
-          __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&w1);
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            h0[jj] = __floats2bfloat162_rn(o[2 * jj], o[2 * jj + 1]);
-            h1[jj] = __floats2bfloat162_rn(o[8 + 2 * jj], o[8 + 2 * jj + 1]);
-          }
-          uint4* out = reinterpret_cast<uint4*>(g.Dh + (size_t)pix[m] * g.ldd + n0 + c0);
-          out[0] = w0;
-          out[1] = w1;
-        } else {
-          float4* out = reinterpret_cast<float4*>(g.D + (size_t)pix[m] * g.ldd + n0 + c0);
+          for (int h = 0; h < 2; ++h) {
+            float v[16];
+            tm_ld16(ta + (uint32_t)(cb + 16 * h), v);
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            float4 o = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
-            if (g.mode == 1) {
-              const float4 d = out[jj];
-              o.x += d.x, o.y += d.y, o.z += d.z, o.w += d.w;
+            for (int jj = 0; jj < 16; ++jj) {
+              const long long pix = __shfl_sync(0xffffffffu, mypix, 16 * h + jj);
+              if (pix < 0) continue;
+              if (g.mode == 2) {
+                const float x = v[jj] + bn;
+                reinterpret_cast<__nv_bfloat16*>(g.Dh)[(size_t)pix * g.ldd + n] = __float2bfloat16(g.relu ? fmaxf(x, 0.f) : x);
+              } else {
+                float* o = g.D + (size_t)pix * g.ldd + n;
+                *o = g.mode == 1 ? *o + v[jj] : v[jj];
+              }
             }
-            out[jj] = o;
+          }
+        }
+      } else {
+        long long pix[T];
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+          const int P = P0i + 128 * m + eq * 32 + lane;
+          pix[m] = -1;
+          if (P < Mpi) {
+            const int b = P / HWp, r = P - b * HWp;
+            const int yp = r / Wp, xp = r - yp * Wp;
+            if (yp >= 1 && yp <= H && xp >= 1 && xp <= W) pix[m] = ((long long)b * H + (yp - 1)) * W + (xp - 1);
+          }
+        }
+  #pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float bias[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) bias[jj] = (g.mode == 2 && g.bias) ? g.bias[n0 + c0 + jj] : 0.f;
+#pragma unroll
+          for (int m = 0; m < T; ++m) {
+            float v[16];
+            tm_ld16(ta + (uint32_t)(m * HC::NCOLS + c0), v);
+            if (pix[m] < 0) continue;
+            if (g.mode == 2) {
+              float o[16];
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const float x = v[jj] + bias[jj];
+                o[jj] = g.relu ? fmaxf(x, 0.f) : x;
+              }
+              uint4 w0, w1;
+              __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&w0);
+              __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&w1);
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) {
+                h0[jj] = __floats2bfloat162_rn(o[2 * jj], o[2 * jj + 1]);
+                h1[jj] = __floats2bfloat162_rn(o[8 + 2 * jj], o[8 + 2 * jj + 1]);
+              }
+              uint4* out = reinterpret_cast<uint4*>(g.Dh + (size_t)pix[m] * g.ldd + n0 + c0);
+              out[0] = w0;
+              out[1] = w1;
+            } else {
+              float4* out = reinterpret_cast<float4*>(g.D + (size_t)pix[m] * g.ldd + n0 + c0);
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) {
+                float4 o = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
+                if (g.mode == 1) {
+                  const float4 d = out[jj];
+                  o.x += d.x, o.y += d.y, o.z += d.z, o.w += d.w;
+                }
+                out[jj] = o;
+              }
+            }
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acce[l & 1]);  // this set may be overwritten
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!ok && tid == 0) atomicExch(g.status, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) tm_dealloc(tmem, NCOLS_ALL);
+  if (warp == 0) tm_dealloc(tmem, HC::TMEM_COLS);
 }
 
-template <int N, int T, bool SW>
+// The weights of a halo convolution in the order the kernel consumes them: for column block nb and
+// step st (chunk, tap) one block of N rows x kgb k groups of 16 bytes, laid out as the B stage in
+// shared memory (swizzled rows of 128 bytes, or [k group][n]), so that a step's weights arrive by one
+// bulk copy. Redone only when the weights change.
+template <int N, bool SW>
+__global__ void k_halo_pack(const GemmArgs g, uint16_t* dst) {
+  const int Cin = g.Cin, CC = Cin < 64 ? Cin : 64, KG = CC / 8;
+  const bool pairs = Cin == 8;
+  const int taps = pairs ? 5 : 9, nsteps = (Cin / CC) * taps, kgb = pairs ? 2 : KG;
+  const size_t per_blk = (size_t)N * kgb;  // 16-byte units per block
+  const size_t total = (size_t)(g.Ntot / N) * nsteps * per_blk;
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = u / per_blk;
+    const int r = (int)(u - b * per_blk);
+    const int nbk = (int)(b / nsteps), st = (int)(b % nsteps);
+    const int n = r / kgb, q = r - n * kgb;
+    const int chunk = st / taps, t = st % taps;
+    const int k0 = pairs ? 16 * t : t * Cin + chunk * CC;
+    const uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)(nbk * N + n) * g.K + k0 + q * 8);
+    const size_t off = SW ? (size_t)n * 128 + (size_t)((q ^ (n & 7)) << 4) : (size_t)(q * N + n) * 16;
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(dst) + b * per_blk * 16 + off) = v;
+  }
+}
+
+// the driver's tensor-map encoder, looked up once through the runtime (no link-time libcuda dependence)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+template <int N, int T, bool SW, bool PN = false>
 static cudaError_t launch_halo_sw(const GemmArgs& g, cudaStream_t s) {
   using HC = HaloCfg<N, T>;
-  const size_t smem = HC::smem(g.W, (g.Cin < 64 ? g.Cin : 64) / 8);
-  if (smem + 1024 > 232448) return cudaErrorInvalidValue;  // dynamic + the static barriers (1 KB aligned)
-  auto kern = k_conv3x3_halo<N, T, SW>;
+  const int CC = g.Cin < 64 ? g.Cin : 64, KG = CC / 8;
+  int S = 0, nbuf = 0;
+  if (!HC::plan(g.W, KG, 232448 - 1024, S, nbuf)) return cudaErrorInvalidValue;  // + the static barriers
+  const size_t smem = nbuf * HC::slab_bytes(g.W, KG) + S * HC::B_STAGE;
+  auto kern = k_conv3x3_halo<N, T, SW, PN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long Mp = (long long)(g.M / (g.H * g.W)) * (g.H + 2) * (g.W + 2);
-  if (Mp + 128LL * T + 2LL * g.W + 16 >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit positions
-  const long long grid = (Mp + 128LL * T - 1) / (128LL * T);
-  kern<<<dim3((unsigned)grid, g.Ntot / N), kThreads, smem, s>>>(g);
+  const int nb = g.M / (g.H * g.W);
+  const long long Mp = (long long)nb * (g.H + 2) * HC::wp(g.W);
+  if (Mp + 128LL * T + 2LL * HC::wp(g.W) + 64 >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit positions
+  // the NHWC input as a 4-D tensor (C, W, H, batch); a box = the chunk's channels (a k group without the
+  // swizzle) x the Wp columns -1 .. Wp - 2 of one row of one image
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.Cin, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)nb};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.Cin * 2, (cuuint64_t)g.W * g.Cin * 2, (cuuint64_t)g.H * g.W * g.Cin * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)(SW ? 64 : 8), (cuuint32_t)HC::wp(g.W), 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(g.A), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const long long ntp = (Mp + 128LL * T - 1) / (128LL * T);
+  const long long ntiles = ntp * (g.Ntot / N);
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);  // one persistent CTA per SM
+  kern<<<grid, kHaloThreads, smem, s>>>(g, map, (int)ntp, S, nbuf);
   return cudaGetLastError();
 }
 
@@ -658,19 +852,70 @@ static cudaError_t launch_halo(const GemmArgs& g, cudaStream_t s) {
 }
 
 // halo path: Cin in {8, 16, 32} or a multiple of 64; K = the weights' row length (>= 9 Cin, and >= 80 for Cin =
-// 8, whose ninth tap pairs with zero columns); images of at most 256 columns
-static bool halo_supported(const GemmArgs& g) {
+// 8, whose ninth tap pairs with zero columns); images of at most 254 columns (a padded row is one box)
+bool halo_conv_supported(const GemmArgs& g) {
   const bool cin_ok = g.Cin == 8 || g.Cin == 16 || g.Cin == 32 || (g.Cin % 64 == 0 && g.Cin > 0);
-  return g.conv && cin_ok && g.W <= 256 && g.K >= 9 * g.Cin && (g.Cin != 8 || g.K >= 80) && g.ksplit <= 1 &&
-         g.M % (g.H * g.W) == 0 && g.ldd % 16 == 0;
+  return g.conv && cin_ok && g.W <= 254 && g.K >= 9 * g.Cin && (g.Cin != 8 || g.K >= 80) && g.ksplit <= 1 &&
+         g.M % (g.H * g.W) == 0 && g.ldd % 16 == 0 && g.K % 8 == 0;
+}
+
+// the column block of the halo kernel: 128 channels with swapped operands (PN) where the output width
+// is an odd multiple of 128 and the input has at least two 64-channel chunks (the transposed epilogue
+// costs about one 64-channel chunk of MMAs per tile), else the widest of 256/128/64/32/16 dividing it
+// (0 stands for PN)
+static int halo_n(const GemmArgs& g) {
+  const int Ntot = g.Ntot;
+  if (Ntot % 128 == 0 && Ntot % 256 != 0 && g.Cin % 64 == 0 && g.Cin >= 128) return 0;
+  return Ntot % 256 == 0 ? 256 : Ntot % 128 == 0 ? 128 : Ntot % 64 == 0 ? 64 : Ntot % 32 == 0 ? 32 : 16;
 }
 
 static cudaError_t launch_halo_n(const GemmArgs& g, cudaStream_t s) {
-  if (g.Ntot % 256 == 0) return launch_halo<256, 2>(g, s);
-  if (g.Ntot % 128 == 0) return launch_halo<128, 4>(g, s);
-  if (g.Ntot % 64 == 0) return launch_halo<64, 4>(g, s);
-  if (g.Ntot % 32 == 0) return launch_halo<32, 4>(g, s);
-  return launch_halo<16, 4>(g, s);
+  switch (halo_n(g)) {
+    case 0: return launch_halo_sw<128, 2, true, true>(g, s);
+    case 256: return launch_halo<256, 1>(g, s);
+    case 128: return launch_halo<128, 2>(g, s);
+    case 64: return launch_halo<64, 4>(g, s);
+    case 32: return launch_halo<32, 4>(g, s);
+    default: return launch_halo<16, 4>(g, s);
+  }
+}
+
+// whether the slab buffers and weight stages of the halo kernel for g fit in shared memory
+template <int N, int T>
+static bool halo_fits(const GemmArgs& g) {
+  int S = 0, nbuf = 0;
+  return HaloCfg<N, T>::plan(g.W, (g.Cin < 64 ? g.Cin : 64) / 8, 232448 - 1024, S, nbuf);
+}
+static bool halo_fits_n(const GemmArgs& g) {
+  switch (halo_n(g)) {
+    case 0: return halo_fits<128, 2>(g);
+    case 256: return halo_fits<256, 1>(g);
+    case 128: return halo_fits<128, 2>(g);
+    case 64: return halo_fits<64, 4>(g);
+    case 32: return halo_fits<32, 4>(g);
+    default: return halo_fits<16, 4>(g);
+  }
+}
+
+template <int N>
+static cudaError_t pack_n(const GemmArgs& g, uint16_t* dst, cudaStream_t s) {
+  if (g.Cin % 64 == 0) k_halo_pack<N, true><<<304, 256, 0, s>>>(g, dst);
+  else k_halo_pack<N, false><<<304, 256, 0, s>>>(g, dst);
+  return cudaGetLastError();
+}
+
+size_t halo_pack_elems(const GemmArgs& g) { return (size_t)g.Ntot * (g.Cin == 8 ? 80 : 9 * g.Cin); }
+
+cudaError_t halo_pack(const GemmArgs& g, uint16_t* dst, cudaStream_t s) {
+  if (!halo_conv_supported(g) || !dst) return cudaErrorInvalidValue;
+  switch (halo_n(g)) {
+    case 0: return pack_n<128>(g, dst, s);  // 128-row blocks, the A operand's layout is the same
+    case 256: return pack_n<256>(g, dst, s);
+    case 128: return pack_n<128>(g, dst, s);
+    case 64: return pack_n<64>(g, dst, s);
+    case 32: return pack_n<32>(g, dst, s);
+    default: return pack_n<16>(g, dst, s);
+  }
 }
 
 template <int N>
@@ -689,7 +934,7 @@ cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (g.ksplit > 1 && (g.mode != 0 || g.kc % KC || g.kc <= 0 || (long long)(g.ksplit - 1) * g.kc >= g.K ||
                        (long long)g.ksplit * g.kc < g.K || g.ksplit > 65535))
     return cudaErrorInvalidValue;  // every split must own at least one chunk
-  if (halo_supported(g)) return launch_halo_n(g, s);
+  if (g.Bp && halo_conv_supported(g) && halo_fits_n(g)) return launch_halo_n(g, s);
   if (g.Ntot % 256 == 0) return launch_n<256>(g, s);
   if (g.Ntot % 128 == 0) return launch_n<128>(g, s);
   if (g.Ntot % 64 == 0) return launch_n<64>(g, s);
