@@ -102,6 +102,9 @@ WORKLOADS = {
                       dict(mono=(MONO_WHITE32, MONO_WHITE32_W, 25))),
     "batch64": (3, "64 independent reconstructions of uneven sizes (probe 64-256, 100-1600 positions, K 1-4, "
                    "far/near 50/50, sigma 0.5-3), one CUDA graph launch per iteration"),
+    "unet128": (None, "warm-start U-Net forward (inference) over 64 synthetic 128^2 patterns, C = 32, random-"
+                      "initialised weights: one step = one estimate (the network's seven 3x3 convolutions on "
+                      "tcgen05, pooling, upsampling, the sigma head, the stitch into a 256^2 object, the median)"),
     "warmstart": (4, "time to intensity NRMSE <= 0.05 against the noise-free patterns: flat start with the true "
                      "sigma vs the learned warm start (U-Net trained on 200k forward-model patterns, 64 sampled "
                      "patterns stitched, median sigma); electron-like crystal, probe 128^2, 64x64 raster step 2 px, "
@@ -234,6 +237,36 @@ def oracle_rate(prob, params, n_positions, iterations=1):
     return n_positions * prob.K * iterations / dt, dt
 
 
+# ---- the oracle on every host core: independent replicas of one bounded oracle iteration, one per
+# worker process (spawned, so no worker inherits a CUDA context); the rate is all units / wall time
+_CPU_PROB = None
+
+
+def _cpu_worker_init(cfg):
+    global _CPU_PROB
+    from synth import make_problem
+
+    _CPU_PROB = make_problem(cfg)
+
+
+def _cpu_worker(job):
+    n_pos, params = job
+    return oracle_rate(_CPU_PROB, params, n_pos)[1]
+
+
+def oracle_rate_all_cores(cfg, params, n_pos, workers):
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_cpu_worker_init, initargs=(cfg,)) as pool:
+        pool.map(_cpu_worker, [(4, params)] * workers, chunksize=1)  # imports and a first small call
+        t0 = time.perf_counter()
+        pool.map(_cpu_worker, [(n_pos, params)] * workers, chunksize=1)
+        wall = time.perf_counter() - t0
+    K = params["K"]
+    return workers * n_pos * K / wall, wall
+
+
 def traffic_record(kernel_tag, name="fused_kernel_traffic.json", workload="far128x4"):
     """DRAM bytes per launch of a kernel from a committed ncu summary, if it was taken on the current
     kernel source (hash match) and this workload; None otherwise."""
@@ -282,6 +315,8 @@ def run_reference(args):
 
         scales, weights, k = WORKLOADS[_WORKLOAD][2]["mono"]
         return run_reference_mono(args, make_problem(WORKLOADS[_WORKLOAD][0]), scales, weights, k)
+    if _WORKLOAD == "unet128":
+        return run_reference_unet(args)
     prob, params = workload()
     n_pos = 100
     for _ in range(args.warmup):
@@ -312,6 +347,33 @@ def mono_flops(M, J, k):
     (a multiply and an add each), applied 2 k + 1 times, plus 10 M^2 per step for the vector updates
     and norms."""
     return (2 * k + 1) * 8.0 * J * M * M + 10.0 * k * M * M
+
+
+def run_reference_unet(args):
+    """The oracle's network forward (FP64 numpy) on one 128^2 pattern per step."""
+    from oracle import unet
+
+    params = unet.init_params(32, seed=1)
+    x = np.random.default_rng(0).random((1, 128, 128, 1)) * 10
+    for _ in range(args.warmup):
+        unet.forward(params, x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        unet.forward(params, x)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {"metric": "warm-start estimate patterns/s", "value": value, "unit": "patterns/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOADS[_WORKLOAD][1], "sample": "each step: the network forward on one pattern"},
+            "cpu_baseline": {"value": value, "unit": "patterns/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} oracle network forwards of one 128^2 pattern (numpy, FP64)"},
+            "e2e": {"value": value, "unit": "patterns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference_mono(args, prob, scales, weights, k):
@@ -721,6 +783,83 @@ def warmstart_record(args, dev, local, with_clocks=True):
     return rec
 
 
+def run_ours_unet(args):
+    """The warm-start network's inference alone: estimates per second over 64 patterns of 128^2."""
+    ws, rank, local = dist_setup(args)
+    import torch
+
+    from paper_2406_06640_gb300.warmstart import LatticeSpec, WarmStart, WarmStartConfig
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    M, n, C = 128, 64, 32
+    P0 = torch.ones(M, M, dtype=torch.complex64, device=dev)
+    net = WarmStart(P0, WarmStartConfig(S=M, C=C, batch=n, dose=2e4, target_scale=1.0, lattice=LatticeSpec(peak=1.0),
+                                        seed=1))
+    gen = torch.Generator().manual_seed(0)
+    hI = (torch.rand(n, M, M, generator=gen) * 10).pin_memory()
+    I = hI.to(dev)
+    pos = np.stack(np.meshgrid(np.arange(8) * 16, np.arange(8) * 16, indexing="ij"), -1).reshape(-1, 2).astype(np.int32)
+    obj = 7 * 16 + M
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        net.estimate(I, pos, obj, obj)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(ws)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        net.estimate(I, pos, obj, obj)
+        ev[k][1].record()
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_max = max_over_ranks(ws, sum(step_ms), dev)
+    value = ws * n * args.steps / (t_max / 1e3)
+    # end to end: the patterns from pinned host memory, the stitched object back every step
+    hO = torch.empty(obj, obj, dtype=torch.complex64).pin_memory()
+    t_e2e = 0.0
+    for k in range(args.steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Ow, _ = net.estimate(hI.to(dev, non_blocking=True), pos, obj, obj)
+        hO.copy_(Ow, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if k > 0:
+            t_e2e += time.perf_counter() - t0
+    t_e2e = max_over_ranks(ws, t_e2e, dev)
+    net.close()
+    flops = conv_forward_flops(M, C) * n
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        peak_src = "measured bf16 burst (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 1900.0, "fallback bf16 burst"
+    avg_s = t_max / args.steps / 1e3
+    if rank == 0:
+        line = {"metric": "warm-start estimate patterns/s", "value": value, "unit": "patterns/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS[_WORKLOAD][1], "patterns": n, "S": M, "C": C,
+                           "l2": "flushed before each timed step (256 MiB write)"},
+                "roofline": {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": flops / avg_s / 1e12 / peak, "traffic": None, "peak_basis": peak_src,
+                             "kernel": "the seven convolutions' FLOPs over the whole estimate (all launches)",
+                             "flops_per_launch": flops},
+                "cpu_baseline": None,
+                "e2e": {"value": n * args.steps / t_e2e, "unit": "patterns/s", "h2d_bytes_per_step": hI.numel() * 4,
+                        "d2h_bytes_per_step": hO.numel() * 8},
+                "gpu_launches": None, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours_warmstart(args):
     """Learned warm start vs flat start: time to NRMSE <= 0.05 (one GPU; replicas only for N > 1)."""
     ws, rank, local = dist_setup(args)
@@ -751,6 +890,8 @@ def run_ours(args):
         return run_ours_mono(args)
     if _WORKLOAD == "warmstart":
         return run_ours_warmstart(args)
+    if _WORKLOAD == "unet128":
+        return run_ours_unet(args)
     ws, rank, local = dist_setup(args)
     import torch
 
@@ -833,9 +974,20 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, dt = oracle_rate(prob, params, prob.N)
-        cpu = {"value": rate, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"one FP64 oracle iteration of the full workload ({prob.N} positions x {prob.K} modes, "
-                         f"{dt:.1f} s, numpy/scipy single-threaded)"}
+        single = {"value": rate, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
+                  "sample": f"one FP64 oracle iteration of the full workload ({prob.N} positions x {prob.K} modes, "
+                            f"{dt:.1f} s, numpy/scipy single-threaded)"}
+        workers = os.cpu_count() or 1
+        n_pos = prob.N // 4
+        try:
+            rate_all, wall = oracle_rate_all_cores(WORKLOADS[_WORKLOAD][0], params, n_pos, workers)
+            cpu = {"value": rate_all, "unit": METRIC, "cores": workers * cpu_threads(), "kind": "oracle",
+                   "sample": f"{workers} worker processes, each one FP64 oracle iteration over {n_pos} of the "
+                             f"{prob.N} positions x {prob.K} modes (independent replicas, {wall:.1f} s wall, "
+                             f"numpy/scipy single-threaded per worker)",
+                   "single_core": single}
+        except Exception as exc:  # the single-core figure stands alone
+            cpu = dict(single, all_cores_error=f"{type(exc).__name__}: {exc}")
     # the metric's second half: time to NRMSE <= 0.05, plain engine against warm start + batching
     ttn = None
     if rank == 0 and ws == 1 and _WORKLOAD == "far128x4" and not args.no_time_to_nrmse:
