@@ -374,10 +374,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_bf16(const GemmArgs g) {
 // slab through a descriptor shifted by the tap's offset. Positions on the padding are computed and
 // dropped by the epilogue. The weights of each (chunk, tap) step feed all T accumulators.
 //
-// Every copy is done by the tensor-memory-access engine: a slab is one box per padded row (Wp
-// positions x the chunk's channels, from a 4-D view (C, W, H, batch) of the NHWC input; the padding
-// columns and rows read as out-of-bounds zeros, and every box starts on a 1024-byte boundary of the
-// slab, rows being a multiple of 8 positions long). The weights arrive packed in step order
+// Every copy is done by the tensor-memory-access engine: a slab is one box of all its padded rows
+// when they lie in one image, else one box per padded row (Wp positions x the chunk's channels, from
+// a 4-D view (C, W, H, batch) of the NHWC input; the padding columns and rows read as out-of-bounds
+// zeros, and every box starts on a 1024-byte boundary of the slab, rows being a multiple of 8
+// positions long). The weights arrive packed in step order
 // (halo_pack), one bulk copy per step. Each copy instruction costs its issuing thread a few hundred
 // cycles, so the slabs and the weights have a thread each and the boxes are as large as a row.
 //
@@ -473,7 +474,8 @@ __device__ __forceinline__ void mma_bf16_acc(uint32_t tmem_d, uint64_t adesc, ui
 // fill one TMEM accumulator set while the epilogue warps drain tile l's.
 template <int N, int T, bool SW, bool PN>
 __global__ void __launch_bounds__(kHaloThreads, 1)
-    k_conv3x3_halo(const GemmArgs g, const __grid_constant__ CUtensorMap tmx, int ntiles_px, int S, int nbuf) {
+    k_conv3x3_halo(const GemmArgs g, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmr,
+                   int ntiles_px, int S, int nbuf, int whole) {
   using HC = HaloCfg<N, T>;
   static_assert(!PN || (N == 128 && T == 2 && SW), "swapped operands: 128 channels x 256 positions, 64-channel chunks");
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -541,6 +543,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     // gc % nbuf, as soon as the MMAs of chunk gc - nbuf (the buffer's last reader) are done: one box per
     // padded row (image row yp - 1 of image b, columns -1 .. Wp - 2; out of range = zeros)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+    if (whole) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmr)) : "memory");
     const int nchunks_all = L * nchunks;
     const int rows_per = R / Wp;
     int nslab = 0;  // slabs issued (chunks 0 .. nslab - 1)
@@ -552,6 +555,18 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
       const uint32_t buf = slab0 + (uint32_t)(gc % nbuf) * slab_bytes;
       uint64_t* fb = &sfull[gc % nbuf];
       mbar_expect_tx(fb, slab_bytes);
+      // all rows_per rows inside one image's padded rows (0 .. H + 1): one box of rows_per rows (tmr)
+      const int b0 = row0 >= 0 ? row0 / (H + 2) : -1;
+      const int yp0 = row0 - b0 * (H + 2);
+      if (whole && row0 >= 0 && yp0 + rows_per <= H + 2) {
+        if (SW) {
+          tma_load_4d(buf, &tmr, c * 64, -1, yp0 - 1, b0, fb);
+        } else {
+          for (int q = 0; q < KG; ++q) tma_load_4d(buf + (uint32_t)(q * R * 16), &tmr, c * CC + q * 8, -1, yp0 - 1, b0, fb);
+        }
+        nslab = gc + 1;
+        continue;
+      }
       for (int r = 0; r < rows_per; ++r) {
         const int pr = row0 + r;
         const int b = pr >= 0 ? pr / (H + 2) : -1;  // before the first image: all zeros
@@ -825,22 +840,33 @@ static cudaError_t launch_halo_sw(const GemmArgs& g, cudaStream_t s) {
   // swizzle) x the Wp columns -1 .. Wp - 2 of one row of one image
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return cudaErrorNotSupported;
-  alignas(64) CUtensorMap map;
+  // and a second map whose box is a whole slab (rows_per rows) for slabs inside one image
+  alignas(64) CUtensorMap map, mapr;
+  const int rows_per = HC::rows(g.W) / HC::wp(g.W);
   const cuuint64_t dims[4] = {(cuuint64_t)g.Cin, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)nb};
   const cuuint64_t strides[3] = {(cuuint64_t)g.Cin * 2, (cuuint64_t)g.W * g.Cin * 2, (cuuint64_t)g.H * g.W * g.Cin * 2};
   const cuuint32_t box[4] = {(cuuint32_t)(SW ? 64 : 8), (cuuint32_t)HC::wp(g.W), 1, 1};
+  const cuuint32_t boxr[4] = {(cuuint32_t)(SW ? 64 : 8), (cuuint32_t)HC::wp(g.W), (cuuint32_t)rows_per, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapSwizzle swz = SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE;
   if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(g.A), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
+  int whole = rows_per <= g.H && rows_per <= 256;
+  if (!whole || encode(&mapr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(g.A), dims, strides, boxr, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    whole = 0;
+    mapr = map;
+  }
   const long long ntp = (Mp + 128LL * T - 1) / (128LL * T);
   const long long ntiles = ntp * (g.Ntot / N);
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int grid = (int)(ntiles < sms ? ntiles : sms);  // one persistent CTA per SM
-  kern<<<grid, kHaloThreads, smem, s>>>(g, map, (int)ntp, S, nbuf);
+  kern<<<grid, kHaloThreads, smem, s>>>(g, map, mapr, (int)ntp, S, nbuf, whole);
   return cudaGetLastError();
 }
 
