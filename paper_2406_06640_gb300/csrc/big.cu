@@ -321,6 +321,16 @@ __global__ void __launch_bounds__(256) k_big_modulus(const BigArgs b) {
   if (threadIdx.x == 0) b.errpart[(size_t)n * (BL / RB) + blockIdx.x] = s_red[0];
 }
 
+// fire-and-forget adds at L2 for the probe partials: within one launch every element is added to by
+// one thread only, and launches are ordered, so each sum keeps its position order (bitwise
+// reproducible) while no thread waits for the old value
+__device__ __forceinline__ void red_add(float2* a, float2 v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void red_add(float* a, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(a), "f"(v));
+}
+
 // ---- final inverse row DFT of every mode, dpsi, contributions
 template <int BL, bool NEAR>
 __global__ void __launch_bounds__(BigShape<BL>::LROW * BT) k_big_final(const BigArgs b) {
@@ -368,7 +378,8 @@ __global__ void __launch_bounds__(BigShape<BL>::LROW * BT) k_big_final(const Big
       cacc[j] = cadd(cacc[j], cconjmul(p, dpsi));
       if (!St) {
         const float2 pc = cconjmul(o, dpsi);
-        pacc[x] = first ? pc : cadd(pacc[x], pc);
+        if (first) pacc[x] = pc;
+        else red_add(&pacc[x], pc);
       }
     }
   }
@@ -379,7 +390,8 @@ __global__ void __launch_bounds__(BigShape<BL>::LROW * BT) k_big_final(const Big
     const int x = t + 16 * j;
     cn[x] = cacc[j];
     const float o2 = cabs2(On[x]);
-    dacc[x] = first ? o2 : dacc[x] + o2;
+    if (first) dacc[x] = o2;
+    else red_add(&dacc[x], o2);
   }
 }
 

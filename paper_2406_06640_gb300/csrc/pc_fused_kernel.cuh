@@ -11,6 +11,16 @@
 
 namespace ptycho {
 
+// fire-and-forget adds at L2 for the per-slot partials: every element is added to by one thread of one
+// CTA only, and one thread's adds to one address take effect in program order, so each sum keeps its
+// position order (bitwise reproducible) while no thread waits for the old value
+__device__ __forceinline__ void red_add_l2(float2* a, float2 v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void red_add_l2(float* a, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(a), "f"(v));
+}
+
 // set when a bounded device wait of the fused kernel gave up (one flag per translation unit that
 // instantiates the kernel; read and cleared by fused_timed_out)
 static __device__ int g_fused_timeout;
@@ -400,9 +410,6 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
 #pragma unroll
         for (int j = 0; j < E; ++j) o[j] = On[(size_t)ln * a.obj_w + tp[q] + G * j];
         const bool own = ln >= r0 && ln < r1;
-        float dold[E];
-#pragma unroll
-        for (int j = 0; j < E; ++j) dold[j] = (!DM && own && !first) ? dacc[ln * M + tp[q] + G * j] : 0.f;
 #pragma unroll
         for (int h = 0; h < E / 4; ++h) {
           float pr[8], ac[8];
@@ -428,7 +435,10 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
               const float2 pc = cconjmul(o[j], dpsi);
               ac[2 * jj] = first ? pc.x : ac[2 * jj] + pc.x;
               ac[2 * jj + 1] = first ? pc.y : ac[2 * jj + 1] + pc.y;
-              if (own) dacc[ln * M + x] = dold[j] + cabs2(o[j]);
+              if (own) {
+                if (first) dacc[ln * M + x] = cabs2(o[j]);
+                else red_add_l2(&dacc[ln * M + x], cabs2(o[j]));
+              }
             }
           }
           if constexpr (!DM) tmem_st8(t_lane + colA + 2 * (q * E + 4 * h), ac);
@@ -453,8 +463,12 @@ __global__ void __launch_bounds__(FusedShape<M>::TR, 1) pc_fused_kernel(const Fu
           if constexpr (!DM) {
             const int qi = ln * M + x;
             const float2 pc = cconjmul(o, dpsi);
-            pacc[qi] = first ? pc : cadd(pacc[qi], pc);
-            if (ln >= r0 && ln < r1) dacc[qi] = first ? cabs2(o) : dacc[qi] + cabs2(o);
+            if (first) pacc[qi] = pc;
+            else red_add_l2(&pacc[qi], pc);
+            if (ln >= r0 && ln < r1) {
+              if (first) dacc[qi] = cabs2(o);
+              else red_add_l2(&dacc[qi], cabs2(o));
+            }
           }
         }
       }
