@@ -109,6 +109,9 @@ struct GemmArgs {
   // pixel p of the NHWC tensor A (batch x H x W x Cin), k = tap * Cin + c,
   // tap = 3 (dy + 1) + (dx + 1); K may exceed 9 Cin (zero columns)
   int conv, H, W, Cin;
+  // with conv: a 1 x 1 contraction over the Cin channels of each pixel instead of the 3x3 neighbourhood
+  // (the input is an explicit neighbourhood already; halo kernel only)
+  int taps1;
   // transposed implicit operand of a weight gradient: row k = tap * Cin + c of A over pixels p is
   // XT3[dx + 1][c][p + dy W] (zero where row y + dy leaves the image; zero for k >= 9 Cin), XT3 the
   // three x-shifted channel-major copies of the NHWC activation (Mpix pixels, W % 8 == 0)

@@ -48,6 +48,35 @@ constexpr int pad_to(int v, int m) { return (v + m - 1) / m * m; }
 constexpr int kMaxBatch = 1024;  // samples per call (the sigma head keeps one value per sample in shared memory)
 
 // ---------------------------------------------------------------- elementwise kernels
+// the explicit 3x3 neighbourhood of the network's input for the first layer's 1 x 1 form: channel t of
+// pixel (b, y, x) = x(b, y + dy, x + dx), t = 3 (dy + 1) + dx + 1, zero outside the image; channels 9 .. 15
+// zero (the same bf16 rounding as the 8-channel copy)
+__global__ void k_input_nbhd(const float* x, bf16* out, int n, int S) {
+  const size_t npix = (size_t)n * S * S;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(i % S), yy = (int)((i / S) % S);
+    const size_t img = i - (size_t)yy * S - xx;
+    __nv_bfloat16 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int y2 = yy + t / 3 - 1, x2 = xx + t % 3 - 1;
+      const bool in = t < 9 && y2 >= 0 && y2 < S && x2 >= 0 && x2 < S;
+      v[t] = __float2bfloat16(in ? x[img + (size_t)y2 * S + x2] : 0.f);
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + i * 16);
+    o[0] = *reinterpret_cast<const uint4*>(&v[0]);
+    o[1] = *reinterpret_cast<const uint4*>(&v[8]);
+  }
+}
+
+// the first layer's weights for the 1 x 1 form: w0n[o][t] = wb[o][8 t] (channel 0 of tap t), t < 9
+__global__ void k_w0_nbhd(const bf16* wb, bf16* w0n, int Cp, int Kf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Cp * 16; i += gridDim.x * blockDim.x) {
+    const int o = i / 16, t = i % 16;
+    w0n[i] = t < 9 ? wb[(size_t)o * Kf + 8 * t] : __float2bfloat16(0.f);
+  }
+}
+
 __global__ void k_input(const float* x, bf16* out, size_t npix) {
   // x (n, S, S) -> (n, S, S, 8) with the value in channel 0; one pixel (16 bytes) per thread
   uint4* out4 = reinterpret_cast<uint4*>(out);
@@ -432,6 +461,9 @@ struct ptycho_unet_s {
   float *w7, *b7, *gw7, *gb7, *mw7, *vw7, *mb7, *vb7;
   // activations (bf16) and buffers
   bf16 *x, *a0, *p0, *a1, *p1, *a2, *p2, *a3, *q2, *a4, *q1, *a5;
+  // the first layer as a 1 x 1 contraction over the explicit neighbourhood: input (n, S, S, 16), weights
+  // (Cp, 16) and their packed copy
+  bf16 *xn, *w0n, *w0np;
   float *out, *g, *sigma, *extra, *loss_part, *loss_s;
   bf16 *d_out, *dY, *dYT, *colT, *xt3;
   float *dX, *skip1, *skip2;
@@ -521,6 +553,17 @@ cudaError_t gemm_wgrad_T(ptycho_unet_s* u, const Conv& L, const bf16* XT3, const
 }
 
 // forward of one convolution: out (n, H, W, Cp) bf16 with bias and ReLU, or fp32 without bias
+// the first layer: the 1 x 1 form over the explicit neighbourhood (bias, ReLU, bf16 out)
+GemmArgs input_layer_args(ptycho_unet_s* u, bf16* out) {
+  const Conv& L = u->L[0];
+  Conv R = L;
+  R.Cin = 16;
+  GemmArgs g = gemm_args(u, u->xn, u->w0n, out, u->nrun * L.H * L.W, L.Cp, 16, L.Cp, 2, L.b, L.relu ? 1 : 0, &R,
+                         Split{1, 0}, u->w0np);
+  g.taps1 = 1;
+  return g;
+}
+
 cudaError_t conv_forward(ptycho_unet_s* u, Conv& L, const bf16* in, bf16* out_bf16, float* out_f32) {
   const int M = u->nrun * L.H * L.W;
   if (out_bf16) return gemm(u, in, L.wb, out_bf16, M, L.Cp, L.Kf, L.Cp, 2, L.b, L.relu ? 1 : 0, &L, Split{1, 0}, L.wbp);
@@ -560,16 +603,28 @@ __global__ void k_add_bias16(float* out, const float* b, int Mo) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Mo * 16; i += gridDim.x * blockDim.x) out[i] += b[i % 16];
 }
 
-static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev) {
+// infer: the first layer as the 1 x 1 form over the explicit neighbourhood (one K = 16 MMA per
+// accumulator instead of five tap pairs); training keeps the tap-pair form, so that the trained network
+// does not depend on which form inference uses (the two differ in FP32 summation order only)
+static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev, bool infer) {
   cudaStream_t s = u->stream;
   const int n = u->nrun, S = u->S, C = u->C;
   const size_t npx = (size_t)n * S * S;
-  k_input<<<grid_for(npx), 256, 0, s>>>(x_dev, u->x, npx);
+  // inference reads only the explicit neighbourhood, training only the 8-channel copy
+  if (infer) k_input_nbhd<<<grid_for(npx), 256, 0, s>>>(x_dev, u->xn, n, S);
+  else k_input<<<grid_for(npx), 256, 0, s>>>(x_dev, u->x, npx);
   if (!u->wb_fresh) {  // bf16 copies of the FP32 master weights, redone only after the weights changed
     for (int i = 0; i < 7; ++i)
       k_weights_bf16<<<grid_for((size_t)u->L[i].Cp * u->L[i].Kf + (size_t)u->L[i].Cin * u->L[i].Kd), 256, 0, s>>>(
           u->L[i].w, u->L[i].wb, i == 0 ? nullptr : u->L[i].wr, u->L[i].Cp, u->L[i].Cin, u->L[i].Kw, u->L[i].Kf,
           u->L[i].Kd);
+    // the first layer's 1 x 1 form over the explicit neighbourhood
+    {
+      const Conv& L = u->L[0];
+      k_w0_nbhd<<<grid_for((size_t)L.Cp * 16), 256, 0, s>>>(L.wb, u->w0n, L.Cp, L.Kf);
+      const cudaError_t e = halo_pack(input_layer_args(u, nullptr), reinterpret_cast<uint16_t*>(u->w0np), s);
+      if (e != cudaSuccess) return e;
+    }
     // and in the halo kernel's step order (forward, and the data gradient's transposed taps)
     for (int i = 0; i < 7; ++i) {
       Conv& L = u->L[i];
@@ -591,7 +646,11 @@ static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev) {
     u->wb_fresh = true;
   }
   cudaError_t e;
-  if ((e = conv_forward(u, u->L[0], u->x, u->a0, nullptr)) != cudaSuccess) return e;
+  if (infer) {
+    if ((e = launch_gemm_bf16(input_layer_args(u, u->a0), u->stream)) != cudaSuccess) return e;
+  } else if ((e = conv_forward(u, u->L[0], u->x, u->a0, nullptr)) != cudaSuccess) {
+    return e;
+  }
   k_avgpool2<<<grid_for(npx * C / 32), 256, 0, s>>>(u->a0, u->p0, n, S, S, C);
   if ((e = conv_forward(u, u->L[1], u->p0, u->a1, nullptr)) != cudaSuccess) return e;
   k_avgpool2<<<grid_for(npx * C / 64), 256, 0, s>>>(u->a1, u->p1, n, S / 2, S / 2, 2 * C);
@@ -641,7 +700,7 @@ static cudaError_t unet_backward(ptycho_unet_s* u, const float* target, const fl
 
 // forward pass and heads without synchronising: out2 (first nvalid samples) and sigma (nvalid) on the device
 static cudaError_t unet_infer(ptycho_unet_s* u, const float* x, float* out2, float* sigma, int nvalid) {
-  cudaError_t e = unet_forward(u, x);
+  cudaError_t e = unet_forward(u, x, true);
   if (e != cudaSuccess) return e;
   k_sigma_pool<<<u->nrun, 1024, 0, u->stream>>>(u->a3, u->g, (u->S / 8) * (u->S / 8), 8 * u->C);
   k_sigma_head<<<1, kMaxBatch, 0, u->stream>>>(u->w7, u->b7, nullptr, 0.f, u->sigma, u->g, u->extra, u->gw7,
@@ -774,6 +833,9 @@ ptycho_status ptycho_unet_create(int32_t S, int32_t C, int32_t batch, uint64_t s
   UA(mb7, 1);
   UA(vb7, 1);
   UA(x, px * 8);
+  UA(xn, px * 16);
+  UA(w0n, (size_t)16 * 16 * ((C + 15) / 16));
+  UA(w0np, (size_t)16 * 16 * ((C + 15) / 16));
   UA(a0, px * C);
   UA(p0, px * C / 4);
   UA(a1, px * 2 * C / 4);
@@ -877,7 +939,7 @@ ptycho_status ptycho_unet_gradients(ptycho_unet_t u, const float* x, const float
   if (!u || !x || !target || !sigma_t) return capi_fail(PTYCHO_EINVAL, "NULL argument");
   UN_CUDA(cudaMemsetAsync(u->status, 0, sizeof(int), u->stream), "clear status");
   u->nrun = u->n;
-  UN_CUDA(unet_forward(u, x), "unet forward");
+  UN_CUDA(unet_forward(u, x, false), "unet forward");
   UN_CUDA(unet_backward(u, target, sigma_t, lam), "unet backward");
   ptycho_status st = read_loss(u, loss);
   if (st != PTYCHO_OK || !grads_host) return st;
@@ -903,7 +965,7 @@ ptycho_status ptycho_unet_train_step(ptycho_unet_t u, const float* x, const floa
   if (!u || !x || !target || !sigma_t) return capi_fail(PTYCHO_EINVAL, "NULL argument");
   UN_CUDA(cudaMemsetAsync(u->status, 0, sizeof(int), u->stream), "clear status");
   u->nrun = u->n;
-  UN_CUDA(unet_forward(u, x), "unet forward");
+  UN_CUDA(unet_forward(u, x, false), "unet forward");
   UN_CUDA(unet_backward(u, target, sigma_t, lam), "unet backward");
   u->step++;
   u->wb_fresh = false;  // Adam changes the FP32 masters below

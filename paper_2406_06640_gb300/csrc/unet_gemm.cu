@@ -496,8 +496,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
   const int KG = CC / 8;                // k groups per chunk
   const uint32_t slab_bytes = (uint32_t)HC::slab_bytes(W, KG);
   const int nchunks = Cin / CC;
-  const bool pairs = Cin == 8;          // two taps per MMA
-  const int taps = pairs ? 5 : 9;       // steps per chunk
+  const bool pairs = Cin == 8 && !g.taps1;  // two taps per MMA
+  const int taps = g.taps1 ? 1 : pairs ? 5 : 9;  // steps per chunk
   const int nsteps = nchunks * taps;    // steps per tile
   const int nblk = g.Ntot / N;
   const int ntiles = ntiles_px * nblk;
@@ -625,7 +625,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
       const uint32_t first = i == 0 ? 0u : 1u;  // the first MMA of each accumulator overwrites it
       const int P0 = (tile_of(l) / nblk) * 128 * T;
       const int off0 = P0 - slab_start(P0);
-      auto tap_row = [&](int tp) { return off0 + (tp / 3 - 1) * Wp + (tp % 3 - 1); };
+      // (a 1 x 1 contraction reads the centre tap only)
+      auto tap_row = [&](int tp) { return g.taps1 ? off0 : off0 + (tp / 3 - 1) * Wp + (tp % 3 - 1); };
       if constexpr (PN) {
         // A = the weights (128 channel rows), B = 256 slab rows from the tap's offset; K in steps of 16
         const uint64_t aw = make_desc_sw128(bs);
@@ -791,8 +792,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
 template <int N, bool SW>
 __global__ void k_halo_pack(const GemmArgs g, uint16_t* dst) {
   const int Cin = g.Cin, CC = Cin < 64 ? Cin : 64, KG = CC / 8;
-  const bool pairs = Cin == 8;
-  const int taps = pairs ? 5 : 9, nsteps = (Cin / CC) * taps, kgb = pairs ? 2 : KG;
+  const bool pairs = Cin == 8 && !g.taps1;
+  const int taps = g.taps1 ? 1 : pairs ? 5 : 9, nsteps = (Cin / CC) * taps, kgb = pairs ? 2 : KG;
   const size_t per_blk = (size_t)N * kgb;  // 16-byte units per block
   const size_t total = (size_t)(g.Ntot / N) * nsteps * per_blk;
   for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += (size_t)gridDim.x * blockDim.x) {
@@ -878,10 +879,12 @@ static cudaError_t launch_halo(const GemmArgs& g, cudaStream_t s) {
 }
 
 // halo path: Cin in {8, 16, 32} or a multiple of 64; K = the weights' row length (>= 9 Cin, and >= 80 for Cin =
-// 8, whose ninth tap pairs with zero columns); images of at most 254 columns (a padded row is one box)
+// 8, whose ninth tap pairs with zero columns; >= Cin for the 1 x 1 form); images of at most 254 columns (a
+// padded row is one box)
 bool halo_conv_supported(const GemmArgs& g) {
   const bool cin_ok = g.Cin == 8 || g.Cin == 16 || g.Cin == 32 || (g.Cin % 64 == 0 && g.Cin > 0);
-  return g.conv && cin_ok && g.W <= 254 && g.K >= 9 * g.Cin && (g.Cin != 8 || g.K >= 80) && g.ksplit <= 1 &&
+  const bool k_ok = g.taps1 ? g.K >= g.Cin : g.K >= 9 * g.Cin && (g.Cin != 8 || g.K >= 80);
+  return g.conv && cin_ok && g.W <= 254 && k_ok && g.ksplit <= 1 &&
          g.M % (g.H * g.W) == 0 && g.ldd % 16 == 0 && g.K % 8 == 0;
 }
 
@@ -930,7 +933,9 @@ static cudaError_t pack_n(const GemmArgs& g, uint16_t* dst, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t halo_pack_elems(const GemmArgs& g) { return (size_t)g.Ntot * (g.Cin == 8 ? 80 : 9 * g.Cin); }
+size_t halo_pack_elems(const GemmArgs& g) {
+  return (size_t)g.Ntot * (g.taps1 ? g.Cin : g.Cin == 8 ? 80 : 9 * g.Cin);
+}
 
 cudaError_t halo_pack(const GemmArgs& g, uint16_t* dst, cudaStream_t s) {
   if (!halo_conv_supported(g) || !dst) return cudaErrorInvalidValue;
@@ -955,7 +960,12 @@ static cudaError_t launch_n(const GemmArgs& g, cudaStream_t s) {
 
 // N tile chosen from the output width: the widest of 256/128/64/32/16 dividing it
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
-  if (g.M % 128 || g.K % KC || g.Ntot % 16 || g.M <= 0 || g.K <= 0 || g.Ntot <= 0) return cudaErrorInvalidValue;
+  if (g.M <= 0 || g.K <= 0 || g.Ntot <= 0 || g.Ntot % 16) return cudaErrorInvalidValue;
+  if (g.taps1) {  // the 1 x 1 form exists on the halo kernel only
+    if (!(g.Bp && halo_conv_supported(g) && halo_fits_n(g))) return cudaErrorInvalidValue;
+    return launch_halo_n(g, s);
+  }
+  if (g.M % 128 || g.K % KC) return cudaErrorInvalidValue;
   if (g.convT && (g.W % 8 || g.Mpix != g.K || g.conv)) return cudaErrorInvalidValue;
   if (g.ksplit > 1 && (g.mode != 0 || g.kc % KC || g.kc <= 0 || (long long)(g.ksplit - 1) * g.kc >= g.K ||
                        (long long)g.ksplit * g.kc < g.K || g.ksplit > 65535))
