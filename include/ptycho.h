@@ -336,7 +336,9 @@ ptycho_status ptycho_generate(const ptycho_gen_spec* spec, const void* probe, co
  * Hann window into object_out (device complex64 obj_h x obj_w; 1 where no box
  * covers a pixel) and write the median predicted sigma to *sigma_out (host).
  * positions: host or device, N (row, col) int32 box corners; every box of side S
- * must lie inside the object. Runs on the network's stream and synchronises. */
+ * must lie inside the object. Runs on the network's stream and synchronises. Its scratch
+ * (patches, sigmas, tile lists) is a buffer kept by the network and grown when a call needs
+ * more, so repeated calls of the same size allocate nothing. */
 ptycho_status ptycho_warmstart(ptycho_unet_t net, const float* intensities, const int32_t* positions, int32_t N,
                                int32_t obj_h, int32_t obj_w, double target_scale, void* object_out,
                                double* sigma_out);

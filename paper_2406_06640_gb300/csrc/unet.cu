@@ -470,6 +470,10 @@ struct ptycho_unet_s {
   float* wpart;  // split-K partial weight gradients
   int* status;
   bool wb_fresh = false;  // the bf16 weight copies match the FP32 masters
+  // the warm start's scratch (patches, sigmas, inputs, tile lists): grown on demand, kept across calls so
+  // that a warmed-up estimate allocates nothing (an allocation synchronises the device)
+  void* ws_buf = nullptr;
+  size_t ws_bytes = 0;
   long long step = 0;
 
   template <class T>
@@ -485,6 +489,7 @@ struct ptycho_unet_s {
   }
   ~ptycho_unet_s() {
     for (void* q : allocs) cudaFree(q);
+    if (ws_buf) cudaFree(ws_buf);
   }
 };
 
@@ -713,24 +718,6 @@ static cudaError_t unet_infer(ptycho_unet_s* u, const float* x, float* out2, flo
   }
   return cudaGetLastError();
 }
-
-namespace {
-// scratch of one warm-start call, freed on every return path
-struct WsScratch {
-  std::vector<void*> p;
-  template <class T>
-  cudaError_t alloc(T** q, size_t count) {
-    void* v = nullptr;
-    const cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
-    if (e == cudaSuccess) p.push_back(v);
-    *q = static_cast<T*>(v);
-    return e;
-  }
-  ~WsScratch() {
-    for (void* v : p) cudaFree(v);
-  }
-};
-}  // namespace
 
 static ptycho_status read_loss(ptycho_unet_s* u, double* loss) {
   float part[64 + 1];
@@ -1021,17 +1008,27 @@ ptycho_status ptycho_warmstart(ptycho_unet_t u, const float* intensities, const 
   start.back() = (int)entries.size();
   int npad = 1;
   while (npad < N) npad <<= 1;
-  WsScratch w;
-  float *patches, *sig, *x;
-  int* d_start;
-  int4* d_entries;
-  double* d_med;
-  UN_CUDA(w.alloc(&patches, (size_t)N * Q * Q * 2), "warm-start scratch");
-  UN_CUDA(w.alloc(&sig, npad), "warm-start scratch");
-  UN_CUDA(w.alloc(&x, (size_t)u->n * S * S), "warm-start scratch");
-  UN_CUDA(w.alloc(&d_start, start.size()), "warm-start scratch");
-  UN_CUDA(w.alloc(&d_entries, entries.size()), "warm-start scratch");
-  UN_CUDA(w.alloc(&d_med, 1), "warm-start scratch");
+  // scratch carved from the network's kept buffer (256-byte aligned pieces)
+  auto al = [](size_t b) { return (std::max<size_t>(b, 1) + 255) / 256 * 256; };
+  const size_t b_patches = al(sizeof(float) * (size_t)N * Q * Q * 2), b_sig = al(sizeof(float) * npad),
+               b_x = al(sizeof(float) * (size_t)u->n * S * S), b_start = al(sizeof(int) * start.size()),
+               b_entries = al(sizeof(int4) * entries.size()), b_med = al(sizeof(double));
+  const size_t need = b_patches + b_sig + b_x + b_start + b_entries + b_med;
+  if (need > u->ws_bytes) {
+    UN_CUDA(cudaStreamSynchronize(s), "stream sync");  // the old buffer may still be read
+    if (u->ws_buf) cudaFree(u->ws_buf);
+    u->ws_buf = nullptr;
+    u->ws_bytes = 0;
+    UN_CUDA(cudaMalloc(&u->ws_buf, need), "warm-start scratch");
+    u->ws_bytes = need;
+  }
+  unsigned char* wp = static_cast<unsigned char*>(u->ws_buf);
+  float* patches = reinterpret_cast<float*>(wp);
+  float* sig = reinterpret_cast<float*>(wp + b_patches);
+  float* x = reinterpret_cast<float*>(wp + b_patches + b_sig);
+  int* d_start = reinterpret_cast<int*>(wp + b_patches + b_sig + b_x);
+  int4* d_entries = reinterpret_cast<int4*>(wp + b_patches + b_sig + b_x + b_start);
+  double* d_med = reinterpret_cast<double*>(wp + b_patches + b_sig + b_x + b_start + b_entries);
   UN_CUDA(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, s), "CSR");
   if (!entries.empty())
     UN_CUDA(cudaMemcpyAsync(d_entries, entries.data(), sizeof(int4) * entries.size(), cudaMemcpyHostToDevice, s),
