@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <array>
 #include <vector>
 
 #include "engine.h"
@@ -158,6 +159,25 @@ struct ptycho_plan_s {
   std::vector<cudaEvent_t> ev;  // 2 * kProfSlots
   int prof_count = 0;
   static constexpr int kProfSlots = 1024;
+  // single plans: an iteration's launches replayed as one CUDA graph once the same key (object,
+  // probe, probe step on, constraint window, pc-DM state start) has run eagerly kGraphAfter times:
+  // capturing costs host time while the stream may be idle, which short runs should not pay. Each key
+  // has a ring of kRing graphs, captured together, each recording the fused kernel's start and end as
+  // event nodes; with profiling on, a replay's times are read back before its graph replays again.
+  struct SingleGraph {
+    std::array<uintptr_t, 3> key{};
+    int slot = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool pending = false;
+  };
+  static constexpr int kGraphAfter = 2, kRing = 4;
+  std::vector<SingleGraph> sgraphs;
+  std::vector<std::pair<std::array<uintptr_t, 3>, int>> eager_runs;
+  cudaStream_t gstream = nullptr;
+  int ring = 0;
+  double prof_graph_ms = 0.0;
+  int prof_graph_n = 0;
 
   template <class T>
   cudaError_t alloc(T** ptr, size_t count) {
@@ -169,6 +189,12 @@ struct ptycho_plan_s {
   }
   ~ptycho_plan_s() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : sgraphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.e0) cudaEventDestroy(g.e0);
+      if (g.e1) cudaEventDestroy(g.e1);
+    }
+    if (gstream) cudaStreamDestroy(gstream);
     for (cudaEvent_t e : branch_ev) cudaEventDestroy(e);
     for (cudaStream_t s : branch) cudaStreamDestroy(s);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -667,7 +693,10 @@ ptycho_status ptycho_plan(const ptycho_params* p, const float* intensities, cons
 }
 
 // Enqueue one iteration (number t) of plan pl on stream s.
-static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* probe, long long t, cudaStream_t s) {
+// pe0 / pe1 (graph capture with profiling): events recorded as graph nodes around the fused kernel
+// instead of the plan's event ring
+static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* probe, long long t, cudaStream_t s,
+                                       cudaEvent_t pe0 = nullptr, cudaEvent_t pe1 = nullptr) {
   FusedArgs fa = pl->fa;
   UpdateArgs ua = pl->ua;
   ConstraintArgs ca = pl->ca;
@@ -677,7 +706,8 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
   ua.P = static_cast<float2*>(probe);
   ca.O = static_cast<float2*>(object);
   const int ps = pl->prof_count % ptycho_plan_s::kProfSlots;
-  if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], s), "profile event");
+  if (pe0) PT_CUDA(cudaEventRecordWithFlags(pe0, s, cudaEventRecordExternal), "profile event");
+  else if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], s), "profile event");
   if (pl->mb > 0) {
     // mini-batch engine: the batches in this iteration's order, each a fused launch over its own
     // positions followed by its update; the error accumulates over the batches
@@ -757,7 +787,9 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
   } else {
     PT_CUDA(launch_fused(pl->p.M, fa, pl->slots, s), "fused kernel launch");
   }
-  if (pl->profiling) {
+  if (pe1) {
+    PT_CUDA(cudaEventRecordWithFlags(pe1, s, cudaEventRecordExternal), "profile event");
+  } else if (pl->profiling) {
     PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], s), "profile event");
     pl->prof_count++;
   }
@@ -811,6 +843,91 @@ static ptycho_status enqueue_update(ptycho_plan_s* pl, void* object, void* probe
   return PTYCHO_OK;
 }
 
+// the fused kernel's time of a profiled graph's last replay, once its end event has been reached
+static ptycho_status harvest(ptycho_plan_s* pl, ptycho_plan_s::SingleGraph& g) {
+  if (!g.pending) return PTYCHO_OK;
+  g.pending = false;
+  PT_CUDA(cudaEventSynchronize(g.e1), "profile event sync");
+  float ms = 0.f;
+  PT_CUDA(cudaEventElapsedTime(&ms, g.e0, g.e1), "cudaEventElapsedTime");
+  pl->prof_graph_ms += ms;
+  pl->prof_graph_n++;
+  return PTYCHO_OK;
+}
+
+// one iteration of a single plan as a graph replay (capturing the key's graphs first when it qualifies);
+// *used = false when the iteration is to run eagerly (the key has not run kGraphAfter times yet, the
+// mini-batch engine, or a capture that failed)
+static ptycho_status iterate_graph(ptycho_plan_s* pl, void* object, void* probe, bool* used) {
+  *used = false;
+  if (pl->mb > 0) return PTYCHO_OK;  // the visiting order changes every iteration
+  const long long t = pl->iter;
+  const uintptr_t flags = (t >= pl->p.probe_update_start ? 1u : 0u) | (pl->in_window(t) ? 2u : 0u) |
+                          (pl->d_psi && pl->dm_fresh ? 4u : 0u);
+  const std::array<uintptr_t, 3> key = {(uintptr_t)object, (uintptr_t)probe, flags};
+  int* count = nullptr;
+  for (auto& e : pl->eager_runs)
+    if (e.first == key) count = &e.second;
+  if (!count) {
+    pl->eager_runs.emplace_back(key, 0);
+    count = &pl->eager_runs.back().second;
+  }
+  if (*count < 0) return PTYCHO_OK;  // this key failed to capture: eager from now on
+  if (*count < ptycho_plan_s::kGraphAfter) {
+    ++*count;
+    return PTYCHO_OK;
+  }
+  const int slot = pl->ring++ % ptycho_plan_s::kRing;
+  size_t gi = pl->sgraphs.size();
+  for (size_t x = 0; x < pl->sgraphs.size(); ++x)
+    if (pl->sgraphs[x].key == key && pl->sgraphs[x].slot == slot) gi = x;
+  if (gi == pl->sgraphs.size()) {
+    // capture the key's whole ring
+    if (!pl->gstream) PT_CUDA(cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking), "graph stream");
+    const bool fresh = pl->dm_fresh;
+    const bool prof = pl->profiling;
+    pl->profiling = false;  // the ring's own events, not the eager event ring
+    std::vector<ptycho_plan_s::SingleGraph> ring;
+    bool ok = true;
+    for (int r = 0; r < ptycho_plan_s::kRing && ok; ++r) {
+      ptycho_plan_s::SingleGraph ng;
+      ng.key = key;
+      ng.slot = r;
+      ok = cudaEventCreate(&ng.e0) == cudaSuccess && cudaEventCreate(&ng.e1) == cudaSuccess;
+      cudaGraph_t graph = nullptr;
+      if (ok) ok = cudaStreamBeginCapture(pl->gstream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      if (ok) {
+        const ptycho_status st = enqueue_iteration(pl, object, probe, t, pl->gstream, ng.e0, ng.e1);
+        const cudaError_t ee = cudaStreamEndCapture(pl->gstream, &graph);
+        ok = st == PTYCHO_OK && ee == cudaSuccess && graph && cudaGraphInstantiate(&ng.exec, graph, 0) == cudaSuccess;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      pl->dm_fresh = fresh;  // a replay starts the state; the caller marks it started
+      ring.push_back(ng);
+    }
+    pl->profiling = prof;
+    if (!ok) {
+      cudaGetLastError();  // a failed capture launched nothing: this key runs eagerly
+      for (auto& g : ring) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.e0) cudaEventDestroy(g.e0);
+        if (g.e1) cudaEventDestroy(g.e1);
+      }
+      *count = -1;
+      return PTYCHO_OK;
+    }
+    gi = pl->sgraphs.size() + (size_t)slot;
+    for (auto& g : ring) pl->sgraphs.push_back(g);
+  }
+  ptycho_plan_s::SingleGraph& g = pl->sgraphs[gi];
+  const ptycho_status hs = harvest(pl, g);
+  if (hs != PTYCHO_OK) return hs;
+  PT_CUDA(cudaGraphLaunch(g.exec, pl->stream), "graph launch");
+  g.pending = pl->profiling;
+  *used = true;
+  return PTYCHO_OK;
+}
+
 ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_t n_iter) {
   if (!pl) return fail(PTYCHO_EINVAL, "plan is NULL");
   if (!pl->members.empty()) return fail(PTYCHO_EINVAL, "batch plans run through ptycho_iterate_batch");
@@ -818,8 +935,15 @@ ptycho_status ptycho_iterate(ptycho_plan_t pl, void* object, void* probe, int32_
   if (n_iter < 0) return fail(PTYCHO_EINVAL, "n_iter must be >= 0");
   PT_CUDA(cudaSetDevice(pl->device), "cudaSetDevice");
   for (int i = 0; i < n_iter; ++i) {
-    const ptycho_status st = enqueue_iteration(pl, object, probe, pl->iter, pl->stream);
+    bool graphed = false;
+    ptycho_status st = iterate_graph(pl, object, probe, &graphed);
     if (st != PTYCHO_OK) return st;
+    if (graphed) {
+      if (pl->d_psi) pl->dm_fresh = false;
+    } else {
+      st = enqueue_iteration(pl, object, probe, pl->iter, pl->stream);
+      if (st != PTYCHO_OK) return st;
+    }
     pl->iter++;
     pl->runs++;
   }
@@ -1265,6 +1389,9 @@ ptycho_status ptycho_profile(ptycho_plan_t pl, int32_t enable) {
   }
   pl->profiling = enable != 0;
   pl->prof_count = 0;
+  for (auto& g : pl->sgraphs) g.pending = false;  // earlier replays' times are dropped
+  pl->prof_graph_ms = 0.0;
+  pl->prof_graph_n = 0;
   return PTYCHO_OK;
 }
 
@@ -1278,9 +1405,16 @@ ptycho_status ptycho_profile_read(ptycho_plan_t pl, double* fused_ms, int32_t* l
     PT_CUDA(cudaEventElapsedTime(&ms, pl->ev[2 * i], pl->ev[2 * i + 1]), "cudaEventElapsedTime");
     tot += ms;
   }
-  *fused_ms = tot;
-  *launches = c;
+  // and the iterations that ran as graph replays
+  for (auto& g : pl->sgraphs) {
+    const ptycho_status hs = harvest(pl, g);
+    if (hs != PTYCHO_OK) return hs;
+  }
+  *fused_ms = tot + pl->prof_graph_ms;
+  *launches = c + pl->prof_graph_n;
   pl->prof_count = 0;
+  pl->prof_graph_ms = 0.0;
+  pl->prof_graph_n = 0;
   return PTYCHO_OK;
 }
 
