@@ -1074,7 +1074,7 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
     delete pl;
     return cuda_fail(e, "cudaGetDevice");
   }
-  // shape classes of the work-queue launches: members with M in {32, 64, 128} sharing K, geometry
+  // shape classes of the work-queue launches: members with M in {8, ..., 128} sharing K, geometry
   // and kernel width class are drained together; the others keep their own launches
   std::vector<int> member_class(B, -1);
   for (int b = 0; b < B; ++b) {

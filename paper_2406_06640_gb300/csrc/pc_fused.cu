@@ -137,12 +137,14 @@ static cudaError_t launch_queue_t(const FusedArgs& a, int slots, cudaStream_t s)
   return a.kh == 5 ? launch_kh<M, NEAR, 5, true>(a, slots, s) : launch_kh<M, NEAR, 15, true>(a, slots, s);
 }
 
-bool fused_queue_supported(int M) { return M == 32 || M == 64 || M == 128; }
+bool fused_queue_supported(int M) { return M == 8 || M == 16 || M == 32 || M == 64 || M == 128; }
 
 cudaError_t launch_fused_queue(int M, const FusedArgs& a, int slots, cudaStream_t s) {
   if (!a.probs || !a.chunks || !a.queue || a.nchunks < 0) return cudaErrorInvalidValue;
   const bool nf = a.near_field != 0;
   switch (M) {
+    case 8: return nf ? launch_queue_t<8, true>(a, slots, s) : launch_queue_t<8, false>(a, slots, s);
+    case 16: return nf ? launch_queue_t<16, true>(a, slots, s) : launch_queue_t<16, false>(a, slots, s);
     case 32: return nf ? launch_queue_t<32, true>(a, slots, s) : launch_queue_t<32, false>(a, slots, s);
     case 64: return nf ? launch_queue_t<64, true>(a, slots, s) : launch_queue_t<64, false>(a, slots, s);
     case 128: return nf ? launch_queue_t<128, true>(a, slots, s) : launch_queue_t<128, false>(a, slots, s);
@@ -168,6 +170,8 @@ static cudaError_t queue_slots_t(int K, int* slots) {
 
 cudaError_t fused_queue_max_slots(int M, int K, int* slots) {
   switch (M) {
+    case 8: return queue_slots_t<8>(K, slots);
+    case 16: return queue_slots_t<16>(K, slots);
     case 32: return queue_slots_t<32>(K, slots);
     case 64: return queue_slots_t<64>(K, slots);
     case 128: return queue_slots_t<128>(K, slots);
