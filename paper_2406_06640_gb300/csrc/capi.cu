@@ -171,11 +171,16 @@ struct ptycho_plan_s {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     bool pending = false;
   };
-  static constexpr int kGraphAfter = 2, kRing = 4;
+  static constexpr int kGraphAfter = 2, kRing = 4, kMaxGraphKeys = 32;  // beyond: eager
   std::vector<SingleGraph> sgraphs;
   std::vector<std::pair<std::array<uintptr_t, 3>, int>> eager_runs;
   cudaStream_t gstream = nullptr;
   int ring = 0;
+  // mini-batch plans: one graph per batch (its fused launch or staged passes and its update), keyed
+  // by (batch, probe step on, object, probe) and replayed in each iteration's visiting order
+  std::vector<std::pair<std::array<uintptr_t, 4>, cudaGraphExec_t>> bgraphs;
+  std::vector<std::pair<std::array<uintptr_t, 4>, int>> beager;
+  static constexpr int kMaxBatchGraphs = 1024;
   double prof_graph_ms = 0.0;
   int prof_graph_n = 0;
 
@@ -189,6 +194,7 @@ struct ptycho_plan_s {
   }
   ~ptycho_plan_s() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : bgraphs) cudaGraphExecDestroy(g.second);
     for (auto& g : sgraphs) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
       if (g.e0) cudaEventDestroy(g.e0);
@@ -693,6 +699,96 @@ ptycho_status ptycho_plan(const ptycho_params* p, const float* intensities, cons
 }
 
 // Enqueue one iteration (number t) of plan pl on stream s.
+// batch b of a mini-batch iteration: its fused launch (or staged passes) over its positions and its
+// update, the error partials added to the iteration's running sum
+static ptycho_status enqueue_batch(ptycho_plan_s* pl, const FusedArgs& fa, const UpdateArgs& ua, int b,
+                                   cudaStream_t s) {
+  const size_t MM = (size_t)pl->p.M * pl->p.M;
+  const int s0 = b * pl->mb, len = std::min(pl->mb, pl->p.N - s0);
+  UpdateArgs ub = ua;
+  ub.tile_start = pl->d_starts + (size_t)b * (pl->tiles + 1);
+  if (pl->big) {
+    // staged passes over the batch's positions; the probe partials restart at its first chunk
+    BigArgs ba = pl->ba;
+    ba.O = fa.O;
+    ba.P = fa.P;
+    ba.n_first = s0;
+    for (int n0 = s0; n0 < s0 + len; n0 += pl->chunk) {
+      ba.n0 = n0;
+      PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, s0 + len - n0), s), "staged pass launch");
+    }
+    ub.slots = std::min(pl->chunk, len);
+    ub.errpart = ua.errpart + (size_t)s0 * big_row_blocks(pl->p.M);
+    ub.nerr = len * big_row_blocks(pl->p.M);
+  } else {
+    FusedArgs fb = fa;
+    fb.I = fa.I + (size_t)s0 * MM;
+    fb.sqrtI = fa.sqrtI + (size_t)s0 * MM;
+    fb.pos = fa.pos + s0;
+    fb.N = len;
+    fb.cn = fa.cn + (size_t)s0 * MM;
+    // a batch with fewer positions than one-CTA slots fills more SMs as clusters of K CTAs
+    const bool clustered = pl->p.K > 1 && len < pl->slots && pl->cluster_slots > 0;
+    const int slots = std::min(clustered ? pl->cluster_slots : pl->slots, len);
+    if (clustered) PT_CUDA(launch_fused_cluster(pl->p.M, fb, slots, s), "fused kernel launch");
+    else PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
+    ub.slots = slots;
+    ub.nerr = slots * pl->p.K;
+  }
+  ub.err_mode = 1;
+  ub.err_acc = pl->d_err_acc;
+  PT_CUDA(launch_update(ub, s), "update launch");
+  return PTYCHO_OK;
+}
+
+// batch b as a graph replay once its key has run eagerly kGraphAfter times; *used = false: run it
+// eagerly (a failed capture marks the key eager for good)
+static ptycho_status batch_graph(ptycho_plan_s* pl, const FusedArgs& fa, const UpdateArgs& ua, void* object,
+                                 void* probe, int b, bool* used) {
+  *used = false;
+  const std::array<uintptr_t, 4> key = {(uintptr_t)b, (uintptr_t)(ua.update_probe ? 1 : 0), (uintptr_t)object,
+                                        (uintptr_t)probe};
+  for (auto& g : pl->bgraphs)
+    if (g.first == key) {
+      PT_CUDA(cudaGraphLaunch(g.second, pl->stream), "graph launch");
+      *used = true;
+      return PTYCHO_OK;
+    }
+  int* count = nullptr;
+  for (auto& e : pl->beager)
+    if (e.first == key) count = &e.second;
+  if (!count) {
+    if (pl->beager.size() >= (size_t)ptycho_plan_s::kMaxBatchGraphs) return PTYCHO_OK;
+    pl->beager.emplace_back(key, 0);
+    count = &pl->beager.back().second;
+  }
+  if (*count < 0) return PTYCHO_OK;
+  if (*count < ptycho_plan_s::kGraphAfter) {
+    ++*count;
+    return PTYCHO_OK;
+  }
+  if (!pl->gstream) PT_CUDA(cudaStreamCreateWithFlags(&pl->gstream, cudaStreamNonBlocking), "graph stream");
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(pl->gstream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  if (ok) {
+    const ptycho_status st = enqueue_batch(pl, fa, ua, b, pl->gstream);
+    const cudaError_t ee = cudaStreamEndCapture(pl->gstream, &graph);
+    ok = st == PTYCHO_OK && ee == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();  // nothing was launched: this batch runs eagerly
+    if (exec) cudaGraphExecDestroy(exec);
+    *count = -1;
+    return PTYCHO_OK;
+  }
+  pl->bgraphs.emplace_back(key, exec);
+  PT_CUDA(cudaGraphLaunch(exec, pl->stream), "graph launch");
+  *used = true;
+  return PTYCHO_OK;
+}
+
 // pe0 / pe1 (graph capture with profiling): events recorded as graph nodes around the fused kernel
 // instead of the plan's event ring
 static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* probe, long long t, cudaStream_t s,
@@ -710,46 +806,20 @@ static ptycho_status enqueue_iteration(ptycho_plan_s* pl, void* object, void* pr
   else if (pl->profiling) PT_CUDA(cudaEventRecord(pl->ev[2 * ps], s), "profile event");
   if (pl->mb > 0) {
     // mini-batch engine: the batches in this iteration's order, each a fused launch over its own
-    // positions followed by its update; the error accumulates over the batches
-    const size_t MM = (size_t)pl->p.M * pl->p.M;
+    // positions followed by its update (a graph replay once it has run eagerly twice); the error
+    // accumulates over the batches and one more launch finishes it
     const std::vector<int> visit = philox_permutation(pl->nb, pl->p.order_seed, 4u, (uint32_t)t);
     ua.update_probe = t >= pl->p.probe_update_start;
     for (int j = 0; j < pl->nb; ++j) {
-      const int b = visit[j];
-      const int s0 = b * pl->mb, len = std::min(pl->mb, pl->p.N - s0);
-      UpdateArgs ub = ua;
-      ub.tile_start = pl->d_starts + (size_t)b * (pl->tiles + 1);
-      if (pl->big) {
-        // staged passes over the batch's positions; the probe partials restart at its first chunk
-        BigArgs ba = pl->ba;
-        ba.O = static_cast<const float2*>(object);
-        ba.P = static_cast<const float2*>(probe);
-        ba.n_first = s0;
-        for (int n0 = s0; n0 < s0 + len; n0 += pl->chunk) {
-          ba.n0 = n0;
-          PT_CUDA(launch_big_chunk(ba, std::min(pl->chunk, s0 + len - n0), s), "staged pass launch");
-        }
-        ub.slots = std::min(pl->chunk, len);
-        ub.errpart = ua.errpart + (size_t)s0 * big_row_blocks(pl->p.M);
-        ub.nerr = len * big_row_blocks(pl->p.M);
-      } else {
-        FusedArgs fb = fa;
-        fb.I = fa.I + (size_t)s0 * MM;
-        fb.sqrtI = fa.sqrtI + (size_t)s0 * MM;
-        fb.pos = fa.pos + s0;
-        fb.N = len;
-        fb.cn = fa.cn + (size_t)s0 * MM;
-        // a batch with fewer positions than one-CTA slots fills more SMs as clusters of K CTAs
-        const bool clustered = pl->p.K > 1 && len < pl->slots && pl->cluster_slots > 0;
-        const int slots = std::min(clustered ? pl->cluster_slots : pl->slots, len);
-        if (clustered) PT_CUDA(launch_fused_cluster(pl->p.M, fb, slots, s), "fused kernel launch");
-        else PT_CUDA(launch_fused(pl->p.M, fb, slots, s), "fused kernel launch");
-        ub.slots = slots;
-        ub.nerr = slots * pl->p.K;
-      }
-      ub.err_mode = j + 1 < pl->nb ? 1 : 2;
-      ub.err_acc = pl->d_err_acc;
-      PT_CUDA(launch_update(ub, s), "update launch");
+      bool used = false;
+      ptycho_status st = batch_graph(pl, fa, ua, object, probe, visit[j], &used);
+      if (st == PTYCHO_OK && !used) st = enqueue_batch(pl, fa, ua, visit[j], s);
+      if (st != PTYCHO_OK) return st;
+    }
+    {
+      UpdateArgs uf = ua;
+      uf.err_acc = pl->d_err_acc;
+      PT_CUDA(launch_err_finish(uf, s), "error launch");
     }
     if (pl->profiling) {
       PT_CUDA(cudaEventRecord(pl->ev[2 * ps + 1], s), "profile event");
@@ -869,6 +939,7 @@ static ptycho_status iterate_graph(ptycho_plan_s* pl, void* object, void* probe,
   for (auto& e : pl->eager_runs)
     if (e.first == key) count = &e.second;
   if (!count) {
+    if (pl->eager_runs.size() >= (size_t)ptycho_plan_s::kMaxGraphKeys) return PTYCHO_OK;  // many buffers: eager
     pl->eager_runs.emplace_back(key, 0);
     count = &pl->eager_runs.back().second;
   }
@@ -1425,8 +1496,8 @@ int32_t ptycho_launches_per_iteration(ptycho_plan_t pl, int32_t in_window) {
   // pc-DM: the estimate sweep stops after the modulus pass (3 far, 4 near)
   const int dm_extra = pl->p.geometry == PTYCHO_NEARFIELD ? 4 : 3;
   if (pl->big) fft = (pl->p.N + pl->chunk - 1) / pl->chunk * (pl->d_psi ? passes + dm_extra : passes);
-  if (pl->mb > 0) {  // per batch: its fused launch or staged passes, and the 4 update kernels
-    fft = -4;
+  if (pl->mb > 0) {  // per batch: its fused launch or staged passes, and the 4 update kernels; the error
+    fft = -4 + 1;    // finish after the batches
     for (int b = 0; b < pl->nb; ++b) {
       const int len = std::min(pl->mb, pl->p.N - b * pl->mb);
       fft += (pl->big ? (len + pl->chunk - 1) / pl->chunk * passes : 1) + 4;

@@ -167,6 +167,8 @@ struct UpdateArgs {
 cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s);
 cudaError_t launch_update_object(const UpdateArgs& u, cudaStream_t s);
 cudaError_t launch_update_probe(const UpdateArgs& u, cudaStream_t s);
+// finishes E of a mini-batch iteration from *err_acc (every batch ran with err_mode 1)
+cudaError_t launch_err_finish(const UpdateArgs& u, cudaStream_t s);
 
 // numerical monochromatisation by CGLS (mono.cu): x_n = k CGLS steps on min ||C x - b_n|| from 0,
 // C = sum_j w[j] T_j, T_j sampling at c + (i - c) inv_a[j] (c = M / 2) with linear interpolation and

@@ -409,4 +409,21 @@ cudaError_t launch_update(const UpdateArgs& u, cudaStream_t s) {
   return e != cudaSuccess ? e : launch_update_probe(u, s);
 }
 
+// E of a mini-batch iteration whose batches all added their partials to *err_acc (err_mode 1): the
+// same sum as a last batch in err_mode 2, so the result does not depend on which form ran
+__global__ void k_err_finish(const UpdateArgs u) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double e = *u.err_acc;
+  const unsigned long long r = *u.run_counter;
+  u.errhist[r % kErrHistory] = sqrt(e / u.errden);
+  *u.run_counter = r + 1;
+  *u.err_acc = 0.0;
+}
+
+cudaError_t launch_err_finish(const UpdateArgs& u, cudaStream_t s) {
+  if (!u.err_acc) return cudaErrorInvalidValue;
+  k_err_finish<<<1, 32, 0, s>>>(u);
+  return cudaGetLastError();
+}
+
 }  // namespace ptycho
