@@ -102,6 +102,18 @@ __device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// the same for the 64-byte swizzled K-major layout: rows of 64 bytes (32 bf16), chunk c of row r at
+// c ^ ((r >> 1) % 4), 8-row groups 512 bytes apart (SBO); layout type 4 in [61,64)
+__device__ __forceinline__ uint64_t make_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // instruction descriptor for kind::f16: D f32 (bits [4,6) = 1), A and B bf16
 // (bits [7,10) = 1, [10,13) = 1), both K-major, N >> 3 in [17,23), M >> 4 in [24,29)
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
@@ -472,12 +484,14 @@ __device__ __forceinline__ void mma_bf16_acc(uint32_t tmem_d, uint64_t adesc, ui
 // column blocks). Steps (chunk, tap) run back to back across tiles; the copies of the next chunk's slab
 // (also when it is the next tile's first) overlap the current chunk's MMAs, and the MMAs of tile l + 1
 // fill one TMEM accumulator set while the epilogue warps drain tile l's.
-template <int N, int T, bool SW, bool PN>
+// SW: the operands' row layout: 0 unswizzled core matrices (k-group planes), 1 rows of 128 bytes with the
+// 128-byte swizzle (64-channel chunks), 2 rows of 64 bytes with the 64-byte swizzle (32-channel inputs)
+template <int N, int T, int SW, bool PN>
 __global__ void __launch_bounds__(kHaloThreads, 1)
     k_conv3x3_halo(const GemmArgs g, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmr,
                    int ntiles_px, int S, int nbuf, int whole) {
   using HC = HaloCfg<N, T>;
-  static_assert(!PN || (N == 128 && T == 2 && SW), "swapped operands: 128 channels x 256 positions, 64-channel chunks");
+  static_assert(!PN || (N == 128 && T == 2 && SW == 1), "swapped operands: 128 channels x 256 positions, 64-channel chunks");
   extern __shared__ __align__(1024) unsigned char smem[];
   // bfull[st]: the weights of the step in stage st landed (transaction bytes); sfull[b]: the slab in
   // buffer b landed; bar[st]: the MMAs reading stage st are done (tcgen05.commit); sbar[b]: those of
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
       const int yp0 = row0 - b0 * (H + 2);
       if (whole && row0 >= 0 && yp0 + rows_per <= H + 2) {
         if (SW) {
-          tma_load_4d(buf, &tmr, c * 64, -1, yp0 - 1, b0, fb);
+          tma_load_4d(buf, &tmr, c * CC, -1, yp0 - 1, b0, fb);
         } else {
           for (int q = 0; q < KG; ++q) tma_load_4d(buf + (uint32_t)(q * R * 16), &tmr, c * CC + q * 8, -1, yp0 - 1, b0, fb);
         }
@@ -572,7 +586,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
         const int b = pr >= 0 ? pr / (H + 2) : -1;  // before the first image: all zeros
         const int yp = pr >= 0 ? pr - b * (H + 2) : 0;
         if (SW) {
-          tma_load_4d(buf + (uint32_t)(r * Wp * 128), &tmx, c * 64, -1, yp - 1, b, fb);
+          tma_load_4d(buf + (uint32_t)(r * Wp * CC * 2), &tmx, c * CC, -1, yp - 1, b, fb);
         } else {
           for (int q = 0; q < KG; ++q)
             tma_load_4d(buf + (uint32_t)((q * R + r * Wp) * 16), &tmx, c * CC + q * 8, -1, yp - 1, b, fb);
@@ -644,7 +658,18 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
 #pragma unroll
         for (int m = 0; m < T; ++m)
           mma_bf16_acc(acc0 + (uint32_t)(m * HC::NCOLS), ad + (uint64_t)(128 * m), bd, idesc, first);
-      } else if constexpr (SW) {
+      } else if constexpr (SW == 2) {
+        // rows of 64 bytes: two K steps of 16 per tap (32 bytes = 2 descriptor units along each row)
+        const uint64_t ad = make_desc_sw64(slab + (uint32_t)(tap_row(t) * 64));
+        const uint64_t bd = make_desc_sw64(bs);
+#pragma unroll
+        for (int m = 0; m < T; ++m) {
+          const uint64_t am = ad + (uint64_t)(512 * m);  // 128 rows of 64 bytes, in 16-byte units
+          const uint32_t acc = acc0 + (uint32_t)(m * HC::NCOLS);
+          mma_bf16_acc(acc, am, bd, idesc, first);
+          mma_bf16_acc(acc, am + 2, bd + 2, idesc, 1u);
+        }
+      } else if constexpr (SW == 1) {
         // rows X .. X + 127 of the slab, K in steps of 16 (32 bytes = 2 descriptor units along each row)
         const uint64_t ad = make_desc_sw128(slab + (uint32_t)(tap_row(t) * 128));
         const uint64_t bd = make_desc_sw128(bs);
@@ -789,7 +814,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
 // step st (chunk, tap) one block of N rows x kgb k groups of 16 bytes, laid out as the B stage in
 // shared memory (swizzled rows of 128 bytes, or [k group][n]), so that a step's weights arrive by one
 // bulk copy. Redone only when the weights change.
-template <int N, bool SW>
+template <int N, int SW>
 __global__ void k_halo_pack(const GemmArgs g, uint16_t* dst) {
   const int Cin = g.Cin, CC = Cin < 64 ? Cin : 64, KG = CC / 8;
   const bool pairs = Cin == 8 && !g.taps1;
@@ -804,7 +829,9 @@ __global__ void k_halo_pack(const GemmArgs g, uint16_t* dst) {
     const int chunk = st / taps, t = st % taps;
     const int k0 = pairs ? 16 * t : t * Cin + chunk * CC;
     const uint4 v = *reinterpret_cast<const uint4*>(g.B + (size_t)(nbk * N + n) * g.K + k0 + q * 8);
-    const size_t off = SW ? (size_t)n * 128 + (size_t)((q ^ (n & 7)) << 4) : (size_t)(q * N + n) * 16;
+    const size_t off = SW == 1   ? (size_t)n * 128 + (size_t)((q ^ (n & 7)) << 4)
+                       : SW == 2 ? (size_t)n * 64 + (size_t)((q ^ ((n >> 1) & 3)) << 4)
+                                 : (size_t)(q * N + n) * 16;
     *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(dst) + b * per_blk * 16 + off) = v;
   }
 }
@@ -824,7 +851,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-template <int N, int T, bool SW, bool PN = false>
+template <int N, int T, int SW, bool PN = false>
 static cudaError_t launch_halo_sw(const GemmArgs& g, cudaStream_t s) {
   using HC = HaloCfg<N, T>;
   const int CC = g.Cin < 64 ? g.Cin : 64, KG = CC / 8;
@@ -846,10 +873,12 @@ static cudaError_t launch_halo_sw(const GemmArgs& g, cudaStream_t s) {
   const int rows_per = HC::rows(g.W) / HC::wp(g.W);
   const cuuint64_t dims[4] = {(cuuint64_t)g.Cin, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)nb};
   const cuuint64_t strides[3] = {(cuuint64_t)g.Cin * 2, (cuuint64_t)g.W * g.Cin * 2, (cuuint64_t)g.H * g.W * g.Cin * 2};
-  const cuuint32_t box[4] = {(cuuint32_t)(SW ? 64 : 8), (cuuint32_t)HC::wp(g.W), 1, 1};
-  const cuuint32_t boxr[4] = {(cuuint32_t)(SW ? 64 : 8), (cuuint32_t)HC::wp(g.W), (cuuint32_t)rows_per, 1};
+  const cuuint32_t cb = SW == 1 ? 64 : SW == 2 ? 32 : 8;  // channels per box row
+  const cuuint32_t box[4] = {cb, (cuuint32_t)HC::wp(g.W), 1, 1};
+  const cuuint32_t boxr[4] = {cb, (cuuint32_t)HC::wp(g.W), (cuuint32_t)rows_per, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUtensorMapSwizzle swz = SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const CUtensorMapSwizzle swz = SW == 1 ? CU_TENSOR_MAP_SWIZZLE_128B : SW == 2 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                                                : CU_TENSOR_MAP_SWIZZLE_NONE;
   if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(g.A), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -871,11 +900,17 @@ static cudaError_t launch_halo_sw(const GemmArgs& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// chunks of 64 channels use the 128-byte swizzled layouts; narrower inputs (8, 16, 32 channels) the
-// unswizzled core-matrix layout
+// chunks of 64 channels use the 128-byte swizzled layouts, 32-channel inputs the 64-byte swizzled ones;
+// narrower inputs (8, 16 channels) the unswizzled core-matrix layout
+static int halo_swizzle(const GemmArgs& g) { return g.Cin % 64 == 0 ? 1 : g.Cin == 32 && !g.taps1 ? 2 : 0; }
+
 template <int N, int T>
 static cudaError_t launch_halo(const GemmArgs& g, cudaStream_t s) {
-  return g.Cin % 64 == 0 ? launch_halo_sw<N, T, true>(g, s) : launch_halo_sw<N, T, false>(g, s);
+  switch (halo_swizzle(g)) {
+    case 1: return launch_halo_sw<N, T, 1>(g, s);
+    case 2: return launch_halo_sw<N, T, 2>(g, s);
+    default: return launch_halo_sw<N, T, 0>(g, s);
+  }
 }
 
 // halo path: Cin in {8, 16, 32} or a multiple of 64; K = the weights' row length (>= 9 Cin, and >= 80 for Cin =
@@ -900,7 +935,7 @@ static int halo_n(const GemmArgs& g) {
 
 static cudaError_t launch_halo_n(const GemmArgs& g, cudaStream_t s) {
   switch (halo_n(g)) {
-    case 0: return launch_halo_sw<128, 2, true, true>(g, s);
+    case 0: return launch_halo_sw<128, 2, 1, true>(g, s);
     case 256: return launch_halo<256, 1>(g, s);
     case 128: return launch_halo<128, 2>(g, s);
     case 64: return launch_halo<64, 4>(g, s);
@@ -928,8 +963,11 @@ static bool halo_fits_n(const GemmArgs& g) {
 
 template <int N>
 static cudaError_t pack_n(const GemmArgs& g, uint16_t* dst, cudaStream_t s) {
-  if (g.Cin % 64 == 0) k_halo_pack<N, true><<<304, 256, 0, s>>>(g, dst);
-  else k_halo_pack<N, false><<<304, 256, 0, s>>>(g, dst);
+  switch (halo_swizzle(g)) {
+    case 1: k_halo_pack<N, 1><<<304, 256, 0, s>>>(g, dst); break;
+    case 2: k_halo_pack<N, 2><<<304, 256, 0, s>>>(g, dst); break;
+    default: k_halo_pack<N, 0><<<304, 256, 0, s>>>(g, dst); break;
+  }
   return cudaGetLastError();
 }
 
