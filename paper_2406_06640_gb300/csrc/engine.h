@@ -220,9 +220,10 @@ struct GenArgs {
 cudaError_t launch_gen(int S, const GenArgs& a, cudaStream_t s);
 size_t gen_smem_bytes(int S);
 cudaError_t launch_log_input(const float* I, float* x, size_t count, cudaStream_t s);
+constexpr int kStitchMaxQ = 256;  // stitch: patch side at most
 struct StitchArgs {
   const float* patches;   // N x patch x patch x 2 network outputs
-  int patch;              // patch side
+  int patch;              // patch side (<= kStitchMaxQ)
   float scale;            // patch value = exp(scale (out0 + i out1))
   const int* tile_start;  // CSR over kObjTile x kObjTile object tiles
   const int4* tile_pos;   // (n, corner row, corner col, 0), increasing n

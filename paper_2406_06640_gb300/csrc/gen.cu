@@ -242,13 +242,18 @@ __global__ void k_log_input(const float* I, float* x, size_t count) {
 }
 
 // one block per 32 x 32 object tile; entries (n, corner row, corner col) in increasing n
+// blockIdx.y of gridDim.y blocks share a tile's pixels; the window's factors sin(pi (l + 1/2) / Q) come
+// from a table (the same values and products as computed per sample)
 __global__ void __launch_bounds__(256) k_stitch(const StitchArgs s) {
+  __shared__ float s_sin[kStitchMaxQ];
   const int tile = blockIdx.x;
   const int ty = tile / s.tiles_x, tx = tile % s.tiles_x;
   const int beg = s.tile_start[tile], end = s.tile_start[tile + 1];
   const int Q = s.patch;
   const float pi_q = 3.14159265358979f / (float)Q;
-  for (int e = threadIdx.x; e < kObjTile * kObjTile; e += blockDim.x) {
+  for (int l = threadIdx.x; l < Q; l += blockDim.x) s_sin[l] = __sinf(pi_q * (l + 0.5f));
+  __syncthreads();
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < kObjTile * kObjTile; e += blockDim.x * gridDim.y) {
     const int y = ty * kObjTile + e / kObjTile, x = tx * kObjTile + e % kObjTile;
     if (y >= s.obj_h || x >= s.obj_w) continue;
     float ar = 0.f, ai = 0.f, wsum = 0.f;
@@ -256,7 +261,7 @@ __global__ void __launch_bounds__(256) k_stitch(const StitchArgs s) {
       const int4 t = s.tile_pos[i];
       const int ly = y - t.y, lx = x - t.z;
       if (ly < 0 || ly >= Q || lx < 0 || lx >= Q) continue;
-      const float sy = __sinf(pi_q * (ly + 0.5f)), sx = __sinf(pi_q * (lx + 0.5f));
+      const float sy = s_sin[ly], sx = s_sin[lx];
       const float w = sy * sy * sx * sx;
       const float* pv = s.patches + (((size_t)t.x * Q + ly) * Q + lx) * 2;
       const float amp = expf(s.scale * pv[0]);
@@ -327,7 +332,8 @@ cudaError_t launch_log_input(const float* I, float* x, size_t count, cudaStream_
 }
 
 cudaError_t launch_stitch(const StitchArgs& a, cudaStream_t s) {
-  k_stitch<<<a.tiles_x * a.tiles_y, 256, 0, s>>>(a);
+  if (a.patch < 1 || a.patch > kStitchMaxQ) return cudaErrorInvalidValue;
+  k_stitch<<<dim3(a.tiles_x * a.tiles_y, 4), 256, 0, s>>>(a);  // four blocks per tile: 256 pixels each
   return cudaGetLastError();
 }
 

@@ -348,8 +348,18 @@ __global__ void k_sigma_head(const float* w7, const float* b7, const float* sigm
                              int C8, int backward) {
   __shared__ float ds[kMaxBatch];
   for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    // the sum in channel order; 16-byte loads (C8 % 4 == 0), several in flight
     float s = b7[0];
-    for (int c = 0; c < C8; ++c) s += g[b * C8 + c] * w7[c];
+    const float4* gr = reinterpret_cast<const float4*>(g + (size_t)b * C8);
+    const float4* wr = reinterpret_cast<const float4*>(w7);
+#pragma unroll 8
+    for (int c4 = 0; c4 < C8 / 4; ++c4) {
+      const float4 gv = gr[c4], wv = wr[c4];
+      s += gv.x * wv.x;
+      s += gv.y * wv.y;
+      s += gv.z * wv.z;
+      s += gv.w * wv.w;
+    }
     sigma[b] = s;
     ds[b] = sigma_t ? 2.f * lam * (s - sigma_t[b]) / n : 0.f;
   }
