@@ -139,7 +139,13 @@ ptycho_status ptycho_plan(const ptycho_params* p, const float* intensities, cons
  *   probe   device, K * M * M complex64, read and written
  * The iteration counter continues across calls (windows and
  * probe_update_start refer to it). Do not touch object or probe until the
- * stream has been synchronised (ptycho_error does that). */
+ * stream has been synchronised (ptycho_error does that).
+ * Launch path: an iteration whose key (object and probe pointers, probe step on,
+ * constraint window active, pc-DM state start) has run twice is captured once
+ * as CUDA graphs (a ring of four) and replayed from then on, one graph launch
+ * per iteration (mini-batch plans: one graph per batch); the results are those
+ * of the eager launches. The first capture of a key costs host time in that
+ * call. Up to 32 keys are kept per plan; further keys run eagerly. */
 ptycho_status ptycho_iterate(ptycho_plan_t plan, void* object, void* probe, int32_t n_iter);
 
 /* Synchronise the plan's stream and return E of the last iteration run
@@ -223,9 +229,12 @@ int ptycho_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int 
  * a CUDA event pair on the plan's stream around every launch of the fused
  * per-position kernel (the dominant kernel of an iteration); for M = 256 and 512 the
  * pair brackets the staged FFT / modulus passes of the iteration.
+ * Graph replays record the pair as graph nodes; their times are read back
+ * before a graph replays again and at ptycho_profile_read. For mini-batch
+ * plans the pair brackets all batches of the iteration with their updates.
  * ptycho_profile_read synchronises the stream, returns the summed device time
  * of those launches in milliseconds and their count, and resets both. At most
- * 1024 launches are kept between reads (older ones are dropped from the sum). */
+ * 1024 eager launches are kept between reads (older ones are dropped from the sum). */
 ptycho_status ptycho_profile(ptycho_plan_t plan, int32_t enable);
 ptycho_status ptycho_profile_read(ptycho_plan_t plan, double* fused_ms, int32_t* launches);
 
