@@ -102,7 +102,8 @@ struct GemmArgs {
   const uint16_t* A; const uint16_t* B;
   float* D; uint16_t* Dh; const float* bias;
   int M, Ntot, K, ldd;
-  int mode;   // 0: D = AB^T (fp32); 1: D += AB^T (fp32); 2: Dh = act(AB^T + bias) (bf16)
+  int mode;   // 0: D = AB^T (+ bias) (fp32); 1: D += AB^T (+ bias) (fp32); 2: Dh = act(AB^T + bias) (bf16);
+              // bias optional (null: none), not with split-K
   int relu;
   int* status;  // set to 1 when a bounded wait gave up
   // implicit 3x3 convolution: row p of A is the zero-padded 3x3 neighbourhood of

@@ -582,7 +582,7 @@ GemmArgs input_layer_args(ptycho_unet_s* u, bf16* out) {
 cudaError_t conv_forward(ptycho_unet_s* u, Conv& L, const bf16* in, bf16* out_bf16, float* out_f32) {
   const int M = u->nrun * L.H * L.W;
   if (out_bf16) return gemm(u, in, L.wb, out_bf16, M, L.Cp, L.Kf, L.Cp, 2, L.b, L.relu ? 1 : 0, &L, Split{1, 0}, L.wbp);
-  return gemm(u, in, L.wb, out_f32, M, L.Cp, L.Kf, L.Cp, 0, nullptr, 0, &L, Split{1, 0}, L.wbp);
+  return gemm(u, in, L.wb, out_f32, M, L.Cp, L.Kf, L.Cp, 0, L.b, 0, &L, Split{1, 0}, L.wbp);  // FP32 + bias
 }
 
 // backward of one convolution given dY (n, H, W, Cp) bf16: weight gradient (into L.gT) and, when dX != nullptr,
@@ -613,10 +613,6 @@ cudaError_t conv_backward(ptycho_unet_s* u, Conv& L, const bf16* in, const bf16*
 
 }  // namespace
 
-// bias added to the fp32 head output (the GEMM's fp32 mode carries no bias)
-__global__ void k_add_bias16(float* out, const float* b, int Mo) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Mo * 16; i += gridDim.x * blockDim.x) out[i] += b[i % 16];
-}
 
 // infer: the first layer as the 1 x 1 form over the explicit neighbourhood (one K = 16 MMA per
 // accumulator instead of five tap pairs); training keeps the tap-pair form, so that the trained network
@@ -676,9 +672,7 @@ static cudaError_t unet_forward(ptycho_unet_s* u, const float* x_dev, bool infer
   if ((e = conv_forward(u, u->L[4], u->q2, u->a4, nullptr)) != cudaSuccess) return e;
   k_up2_concat<<<grid_for(npx * 6 * C / 32), 256, 0, s>>>(u->a4, u->a1, u->q1, n, S / 2, S / 2, 4 * C, 2 * C);
   if ((e = conv_forward(u, u->L[5], u->q1, u->a5, nullptr)) != cudaSuccess) return e;
-  if ((e = conv_forward(u, u->L[6], u->a5, nullptr, u->out)) != cudaSuccess) return e;
-  const int Mo = n * (S / 2) * (S / 2);
-  k_add_bias16<<<grid_for((size_t)Mo * 16), 256, 0, s>>>(u->out, u->L[6].b, Mo);
+  if ((e = conv_forward(u, u->L[6], u->a5, nullptr, u->out)) != cudaSuccess) return e;  // bias in its epilogue
   return cudaGetLastError();
 }
 

@@ -364,6 +364,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_bf16(const GemmArgs g) {
         }
       } else {
         float* out = g.D + (g.ksplit > 1 ? (size_t)blockIdx.z * g.dsplit : 0) + (size_t)row * g.ldd + n0 + c0;
+        if (g.bias)  // mode 0 / 1 with a bias: the bias added to the product (one add per element)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] += g.bias[n0 + c0 + j];
 #pragma unroll
         for (int j = 0; j < 16; ++j) out[j] = g.mode == 1 ? out[j] + v[j] : v[j];
       }
@@ -717,7 +720,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
         // lane = channel n0 + 32 eq + lane, column = position P0i + column; 32 columns at a time, lane j
         // decoding the position of column j for the warp
         const int n = n0 + eq * 32 + lane;
-        const float bn = (g.mode == 2 && g.bias) ? g.bias[n] : 0.f;
+        const float bn = g.bias ? g.bias[n] : 0.f;
 #pragma unroll 1
         for (int cb = 0; cb < 256; cb += 32) {
           long long mypix = -1;
@@ -740,7 +743,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
                 reinterpret_cast<__nv_bfloat16*>(g.Dh)[(size_t)pix * g.ldd + n] = __float2bfloat16(g.relu ? fmaxf(x, 0.f) : x);
               } else {
                 float* o = g.D + (size_t)pix * g.ldd + n;
-                *o = g.mode == 1 ? *o + v[jj] : v[jj];
+                const float x = g.bias ? v[jj] + bn : v[jj];
+                *o = g.mode == 1 ? *o + x : x;
               }
             }
           }
@@ -761,7 +765,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
         for (int c0 = 0; c0 < N; c0 += 16) {
           float bias[16];
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) bias[jj] = (g.mode == 2 && g.bias) ? g.bias[n0 + c0 + jj] : 0.f;
+          for (int jj = 0; jj < 16; ++jj) bias[jj] = g.bias ? g.bias[n0 + c0 + jj] : 0.f;
 #pragma unroll
           for (int m = 0; m < T; ++m) {
             float v[16];
@@ -790,6 +794,9 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
 #pragma unroll
               for (int jj = 0; jj < 4; ++jj) {
                 float4 o = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
+                if (g.bias) {  // the bias added to the product (one add per element)
+                  o.x += bias[4 * jj], o.y += bias[4 * jj + 1], o.z += bias[4 * jj + 2], o.w += bias[4 * jj + 3];
+                }
                 if (g.mode == 1) {
                   const float4 d = out[jj];
                   o.x += d.x, o.y += d.y, o.z += d.z, o.w += d.w;
@@ -1005,6 +1012,7 @@ cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   }
   if (g.M % 128 || g.K % KC) return cudaErrorInvalidValue;
   if (g.convT && (g.W % 8 || g.Mpix != g.K || g.conv)) return cudaErrorInvalidValue;
+  if (g.ksplit > 1 && g.bias) return cudaErrorInvalidValue;  // a bias would be added once per split
   if (g.ksplit > 1 && (g.mode != 0 || g.kc % KC || g.kc <= 0 || (long long)(g.ksplit - 1) * g.kc >= g.K ||
                        (long long)g.ksplit * g.kc < g.K || g.ksplit > 65535))
     return cudaErrorInvalidValue;  // every split must own at least one chunk
