@@ -287,6 +287,13 @@ static bool is_device_pointer(const void* ptr) {
 // device for each candidate over one pass of all positions (object and probe from scratch buffers
 // of ones -- the passes only read them; they write the scratch, contributions and partials, which
 // the first real iteration overwrites), best of two after a warm-up.
+// Host vector -> plan buffer: ordered on the plan's stream and complete when it returns (a blocking
+// copy on the legacy stream is not ordered against a non-blocking caller stream).
+static cudaError_t h2d(cudaStream_t s, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
 static ptycho_status tune_staged_chunk(ptycho_plan_s* pl, int* best) {
   cudaStream_t s = pl->stream;
   const ptycho_params& p = pl->p;
@@ -296,8 +303,8 @@ static ptycho_status tune_staged_chunk(ptycho_plan_s* pl, int* best) {
   PT_CUDA(pl->alloc(&d_p, (size_t)p.K * MM), "alloc tuning probe");
   {
     std::vector<float2> ones(std::max((size_t)p.obj_h * p.obj_w, (size_t)p.K * MM), make_float2(1.f, 0.f));
-    PT_CUDA(cudaMemcpy(d_o, ones.data(), sizeof(float2) * p.obj_h * p.obj_w, cudaMemcpyHostToDevice), "tuning data");
-    PT_CUDA(cudaMemcpy(d_p, ones.data(), sizeof(float2) * p.K * MM, cudaMemcpyHostToDevice), "tuning data");
+    PT_CUDA(h2d(pl->stream, d_o, ones.data(), sizeof(float2) * p.obj_h * p.obj_w), "tuning data");
+    PT_CUDA(h2d(pl->stream, d_p, ones.data(), sizeof(float2) * p.K * MM), "tuning data");
   }
   BigArgs ba = pl->ba;
   ba.O = d_o;
@@ -497,9 +504,9 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
   int4* d_list;
   PT_CUDA(pl->alloc(&d_start, start.size()), "alloc tile lists");
   PT_CUDA(pl->alloc(&d_list, flat.size()), "alloc tile lists");
-  PT_CUDA(cudaMemcpy(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice), "copy tiles");
+  PT_CUDA(h2d(pl->stream, d_start, start.data(), sizeof(int) * start.size()), "copy tiles");
   if (!flat.empty())
-    PT_CUDA(cudaMemcpy(d_list, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice), "copy tiles");
+    PT_CUDA(h2d(pl->stream, d_list, flat.data(), sizeof(int4) * flat.size()), "copy tiles");
   pl->d_starts = d_start;
   if (p.engine == PTYCHO_ENGINE_DM) {
     PT_CUDA(pl->alloc(&pl->d_psi, (size_t)N * K * MM), "alloc exit-wave state");
@@ -539,8 +546,8 @@ static ptycho_status build_plan(ptycho_plan_s* pl, const float* intensities, con
     int4* dl;
     PT_CUDA(pl->alloc(&ds, cs.size()), "alloc constraint tile lists");
     PT_CUDA(pl->alloc(&dl, cl.size()), "alloc constraint tile lists");
-    PT_CUDA(cudaMemcpy(ds, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice), "copy tiles");
-    PT_CUDA(cudaMemcpy(dl, cl.data(), sizeof(int4) * cl.size(), cudaMemcpyHostToDevice), "copy tiles");
+    PT_CUDA(h2d(pl->stream, ds, cs.data(), sizeof(int) * cs.size()), "copy tiles");
+    PT_CUDA(h2d(pl->stream, dl, cl.data(), sizeof(int4) * cl.size()), "copy tiles");
     d_cstart = ds;
     d_clist = dl;
   }
@@ -1033,12 +1040,12 @@ static std::vector<int4> chunk_list(ptycho_plan_s* pl, ptycho_plan_s::QueueClass
   return chunks;
 }
 
-static void st_apply_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueClass& qc, int L, int max_slots) {
+static cudaError_t st_apply_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueClass& qc, int L, int max_slots) {
   const std::vector<int4> chunks = chunk_list(pl, qc, L);
   qc.chunk_len = L;
   qc.nchunks = (int)chunks.size();
   qc.slots = std::min(max_slots, qc.nchunks);
-  cudaMemcpy(qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice);
+  const cudaError_t e = h2d(pl->stream, qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size());
   for (int b : qc.members) {
     ptycho_plan_s* m = pl->members[b];
     m->parts = (m->p.N + L - 1) / L;
@@ -1046,6 +1053,7 @@ static void st_apply_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueClass& 
     m->ua.slots = m->parts;
     m->ua.nerr = m->parts * m->p.K;
   }
+  return e;
 }
 
 // Autotuner: time the class's work-queue launch for every candidate chunk length (object and probe
@@ -1067,8 +1075,8 @@ static ptycho_status tune_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueCl
   PT_CUDA(pl->alloc(&d_desc, qc.members.size()), "alloc tuning arguments");
   {
     std::vector<float2> ones(std::max(obj_max, probe_max), make_float2(1.f, 0.f));
-    PT_CUDA(cudaMemcpy(d_o, ones.data(), sizeof(float2) * obj_max, cudaMemcpyHostToDevice), "tuning object");
-    PT_CUDA(cudaMemcpy(d_p, ones.data(), sizeof(float2) * probe_max, cudaMemcpyHostToDevice), "tuning probe");
+    PT_CUDA(h2d(pl->stream, d_o, ones.data(), sizeof(float2) * obj_max), "tuning object");
+    PT_CUDA(h2d(pl->stream, d_p, ones.data(), sizeof(float2) * probe_max), "tuning probe");
     std::vector<FusedArgs> h;
     for (int b : qc.members) {
       FusedArgs f = pl->members[b]->fa;
@@ -1076,7 +1084,7 @@ static ptycho_status tune_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueCl
       f.P = d_p;
       h.push_back(f);
     }
-    PT_CUDA(cudaMemcpy(d_desc, h.data(), sizeof(FusedArgs) * h.size(), cudaMemcpyHostToDevice), "tuning arguments");
+    PT_CUDA(h2d(pl->stream, d_desc, h.data(), sizeof(FusedArgs) * h.size()), "tuning arguments");
   }
   cudaEvent_t e0, e1;
   PT_CUDA(cudaEventCreate(&e0), "event");
@@ -1086,7 +1094,7 @@ static ptycho_status tune_chunk_length(ptycho_plan_s* pl, ptycho_plan_s::QueueCl
   ptycho_status st = PTYCHO_OK;
   for (int L : kChunkCandidates) {
     const std::vector<int4> chunks = chunk_list(pl, qc, L);
-    cudaError_t ce = cudaMemcpy(qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice);
+    cudaError_t ce = h2d(pl->stream, qc.d_chunks, chunks.data(), sizeof(int4) * chunks.size());
     FusedArgs fa = pl->members[qc.members[0]]->fa;
     fa.probs = d_desc;
     fa.chunks = qc.d_chunks;
@@ -1222,8 +1230,7 @@ ptycho_status ptycho_plan_batch(int32_t B, const ptycho_params* const* params, c
       std::lock_guard<std::mutex> lock(g_tune_mutex);
       g_tune_cache[key] = L;
     }
-    st_apply_chunk_length(pl, qc, L, max_slots);
-    PT_CUDA(cudaGetLastError(), "chunk list");
+    PT_CUDA(st_apply_chunk_length(pl, qc, L, max_slots), "chunk list");
   }
   const int S = std::min(B, 8);
   pl->branch.resize(S);
@@ -1278,7 +1285,7 @@ ptycho_status ptycho_iterate_batch(ptycho_plan_t pl, void* const* objects, void*
         }
         FusedArgs* d = nullptr;
         PT_CUDA(pl->alloc(&d, h.size()), "alloc work-queue arguments");
-        PT_CUDA(cudaMemcpy(d, h.data(), sizeof(FusedArgs) * h.size(), cudaMemcpyHostToDevice), "copy arguments");
+        PT_CUDA(h2d(pl->stream, d, h.data(), sizeof(FusedArgs) * h.size()), "copy arguments");
         descs.push_back(d);
       }
       PT_CUDA(cudaStreamBeginCapture(pl->origin, cudaStreamCaptureModeRelaxed), "begin capture");

@@ -886,9 +886,11 @@ ptycho_status ptycho_unet_set_params(ptycho_unet_t u, const float* host, int64_t
     UN_CUDA(cudaMemcpyAsync(L.b, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice, u->stream), "params");
     UN_CUDA(cudaStreamSynchronize(u->stream), "sync");
   }
-  UN_CUDA(cudaMemcpy(u->w7, host + off, sizeof(float) * 8 * u->C, cudaMemcpyHostToDevice), "params");
+  // the sigma head's weights, ordered after any forward still reading them on the network's stream
+  UN_CUDA(cudaMemcpyAsync(u->w7, host + off, sizeof(float) * 8 * u->C, cudaMemcpyHostToDevice, u->stream), "params");
   off += 8 * u->C;
-  UN_CUDA(cudaMemcpy(u->b7, host + off, sizeof(float), cudaMemcpyHostToDevice), "params");
+  UN_CUDA(cudaMemcpyAsync(u->b7, host + off, sizeof(float), cudaMemcpyHostToDevice, u->stream), "params");
+  UN_CUDA(cudaStreamSynchronize(u->stream), "sync");
   return PTYCHO_OK;
 }
 
