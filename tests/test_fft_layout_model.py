@@ -11,7 +11,9 @@ index), the model checks:
   * every half-warp of one 8-byte access touches 16 distinct bank pairs, or shares an address
     (broadcast): no bank conflicts.
 Configurations: the fused kernels and the generator (M = 8 ... 64 with one line per thread,
-M = 128 with 512 threads x 2 lines) and M = 256 at 512 threads.
+M = 128 with 512 threads x 2 lines) and M = 256 at 512 threads. The staged passes of big.cu
+(256- and 512-point lines, 16 threads per line) are modelled the same way: their line swap, twiddle
+table and the column passes' staged tile.
 """
 import pathlib
 import re
@@ -154,3 +156,73 @@ def test_model_sees_a_conflicting_stride():
     conf = sum(_conflicts(sl[w:w + 32]) for kind, _, sl in _accesses(tl, 2, 512) if kind.startswith("A")
                for w in range(0, 512, 32))
     assert conf > 0
+
+
+# ---------------------------------------------------------------- staged line transforms (csrc/big.cu)
+BIG = FFT.parent / "big.cu"
+
+
+def _big_shape(BL):
+    """LINES and TWS of BigShape<BL>, and the swap row stride BS = BT + 1, read from big.cu."""
+    src = BIG.read_text()
+    bt = int(re.search(r"constexpr int BT = (\d+);", src).group(1))
+    bs = bt + 1
+    m = re.search(r"struct BigShape<" + str(BL) + r"> \{\s*static constexpr int (.*?);", src, re.S)
+    fields = dict(f.strip().split(" = ") for f in m.group(1).split(","))
+    tws = fields["TWS"].strip()
+    return int(fields["LINES"]), (bs if tws == "BS" else int(tws)), bt, bs
+
+
+def _line_freq(BL, t, r):
+    return t + 16 * r if BL == 256 else 2 * t + (r >> 4) + 32 * (r & 15)
+
+
+def _big_accesses(BL):
+    """Per 16-thread line (one half-warp): (access, [slot of lane t]) for the swap, the twiddles and the
+    column passes' staged tile (natural and frequency order)."""
+    LINES, TWS, BT, BS = _big_shape(BL)
+    E = 16 if BL == 256 else 32
+    TP = LINES + 1
+    out = []
+    if BL == 256:
+        for k2 in range(16):
+            out.append(("swap-write", [k2 * BS + t for t in range(BT)]))
+        for tt in range(16):
+            out.append(("swap-read", [t * BS + tt for t in range(BT)]))
+    else:
+        for k2 in range(32):
+            out.append(("swap-write", [(k2 & 1) * 16 * BS + (k2 >> 1) * BS + t for t in range(BT)]))
+        for i2 in range(2):
+            for tt in range(16):
+                out.append(("swap-read", [i2 * 16 * BS + t * BS + tt for t in range(BT)]))
+    for k2 in range(1, E):
+        out.append(("twiddle", [t * TWS + k2 for t in range(BT)]))
+    for cl in range(LINES):
+        for j in range(E):
+            out.append(("tile-natural", [(t + 16 * j) * TP + cl for t in range(BT)]))
+            out.append(("tile-frequency", [_line_freq(BL, t, j) * TP + cl for t in range(BT)]))
+    return out
+
+
+@pytest.mark.parametrize("BL", [256, 512])
+def test_staged_line_swaps_are_bijections(BL):
+    LINES, TWS, BT, BS = _big_shape(BL)
+    acc = _big_accesses(BL)
+    w = [s for kind, sl in acc if kind == "swap-write" for s in sl]
+    r = [s for kind, sl in acc if kind == "swap-read" for s in sl]
+    assert len(set(w)) == len(w) == BL and set(r) == set(w)
+    # the frequencies a line holds after the forward transform are each frequency once
+    E = 16 if BL == 256 else 32
+    assert sorted(_line_freq(BL, t, q) for t in range(BT) for q in range(E)) == list(range(BL))
+
+
+@pytest.mark.parametrize("BL", [256, 512])
+def test_staged_exchanges_bank_conflicts(BL):
+    worst = {}
+    for kind, sl in _big_accesses(BL):
+        worst[kind] = max(worst.get(kind, 0), _conflicts(sl))
+    for kind in ("swap-write", "swap-read", "twiddle", "tile-natural"):
+        assert worst[kind] == 0, (BL, kind)
+    # frequency order: rows t + 16 r at 256 (conflict-free); rows 2t + i at 512, where lanes t and
+    # t + 8 share a bank pair in any [BL][LINES + 1] tile: exactly a 2-way conflict (8 extra per access)
+    assert worst["tile-frequency"] == (0 if BL == 256 else 8)
