@@ -388,6 +388,17 @@ ptycho_status ptycho_monochromatise(int32_t M, int32_t J, const double* scale, c
  * one small device buffer. PTYCHO_EINVAL for NULL outputs, PTYCHO_ENOMEM, PTYCHO_ECUDA. */
 ptycho_status ptycho_measure_fp32_peak(double* tflops, double* ms, void* cuda_stream);
 
+/* Failure-detection self-test (no counterpart in the paper): runs, on cuda_stream, one bounded
+ * mbarrier wait of the kind the cluster-form fused kernels use on their copy barriers, with a
+ * budget of budget_ns nanoseconds (0 ... 2e9, the kernels' own budget being 2 s). With signal != 0
+ * the barrier is completed before the wait, which then succeeds (PTYCHO_OK); with signal == 0
+ * nothing ever completes it, the wait gives up after the budget and sets the device flag that
+ * ptycho_error reads, and this call reports it: PTYCHO_ETIMEOUT, the flag cleared and the context
+ * still usable. Synchronises the stream. A timeout left pending by an earlier launch is reported
+ * (and cleared) before the test runs, as PTYCHO_ETIMEOUT. PTYCHO_EINVAL for a budget out of
+ * range (checked before any device work), PTYCHO_ECUDA. */
+ptycho_status ptycho_wait_selftest(int64_t budget_ns, int32_t signal, void* cuda_stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ptycho_last_error(void);
 

@@ -26,7 +26,8 @@ EXPORTED = ("ptycho_plan", "ptycho_iterate", "ptycho_error", "ptycho_error_histo
             "ptycho_profile", "ptycho_profile_read", "ptycho_launches_per_iteration", "ptycho_last_error",
             "ptycho_version", "ptycho_set_batch_chunk", "ptycho_batch_classes", "ptycho_batch_launches", "ptycho_set_staged_chunk", "ptycho_staged_chunk", "ptycho_permutation", "ptycho_unet_create", "ptycho_unet_param_count", "ptycho_unet_set_params",
             "ptycho_unet_get_params", "ptycho_unet_forward", "ptycho_unet_gradients", "ptycho_unet_train_step",
-            "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart", "ptycho_monochromatise")
+            "ptycho_unet_destroy", "ptycho_generate", "ptycho_warmstart", "ptycho_monochromatise",
+            "ptycho_measure_fp32_peak", "ptycho_wait_selftest")
 
 
 class PtychoError(RuntimeError):
@@ -135,6 +136,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ptycho_version.restype = ctypes.c_char_p
     lib.ptycho_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]
     lib.ptycho_measure_fp32_peak.restype = st
+    lib.ptycho_wait_selftest.argtypes = [ctypes.c_int64, ctypes.c_int32, P]
+    lib.ptycho_wait_selftest.restype = st
     F32 = ctypes.c_float
     lib.ptycho_unet_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P,
                                        ctypes.POINTER(P)]

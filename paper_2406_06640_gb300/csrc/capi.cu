@@ -1559,6 +1559,20 @@ ptycho_status ptycho_monochromatise(int32_t M, int32_t J, const double* scale, c
 
 const char* ptycho_last_error(void) { return g_last_error.c_str(); }
 
+ptycho_status ptycho_wait_selftest(int64_t budget_ns, int32_t signal, void* cuda_stream) {
+  if (budget_ns < 0 || budget_ns > 2000000000LL) return fail(PTYCHO_EINVAL, "budget_ns must be in [0, 2e9]");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  bool pending = false;
+  PT_CUDA(fused_timed_out(&pending), "read wait status");
+  if (pending) return fail(PTYCHO_ETIMEOUT, "a bounded device wait of an earlier launch had given up");
+  PT_CUDA(launch_wait_selftest((unsigned long long)budget_ns, signal != 0, s), "self-test launch");
+  PT_CUDA(cudaStreamSynchronize(s), "stream sync");
+  bool timed_out = false;
+  PT_CUDA(fused_timed_out(&timed_out), "read wait status");
+  if (timed_out) return fail(PTYCHO_ETIMEOUT, "the self-test wait gave up after its budget");
+  return PTYCHO_OK;
+}
+
 const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -67,6 +67,9 @@ bool fused_queue_supported(int M);
 size_t fused_smem_bytes(int M);
 // true if a bounded device wait of the fused kernel gave up since the last call (clears the flag; synchronous)
 cudaError_t fused_timed_out(bool* out);
+// one bounded mbarrier wait of the fused kernels' kind on a barrier that `signal` completes (or
+// nothing does), giving up after budget_ns; its timeout shows in fused_timed_out
+cudaError_t launch_wait_selftest(unsigned long long budget_ns, bool signal, cudaStream_t s);
 
 // staged path for M = 256 and 512 (big.cu): a chunk of C positions x K modes in the scratch W
 struct BigArgs {

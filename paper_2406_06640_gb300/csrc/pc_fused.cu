@@ -33,6 +33,24 @@
 
 namespace ptycho {
 
+// Self-test of the bounded wait above (the one the cluster kernels use on their copy barriers):
+// one thread waits for phase 0 of a fresh mbarrier with the given budget. With `signal` it arrives
+// first and the wait succeeds at once; otherwise nothing ever arrives, the wait gives up after
+// `budget_ns` and sets the flag fused_timed_out reads, exactly as a fused kernel does.
+__global__ void k_wait_selftest(unsigned long long budget_ns, int signal) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_addr(&bar);
+  mbar_init(b, 1);
+  if (signal) mbar_arrive_expect_tx(b, 0u);  // the one expected arrival, no transaction bytes
+  if (!mbar_wait_bounded(b, 0u, budget_ns)) atomicExch(&g_fused_timeout, 1);
+}
+
+cudaError_t launch_wait_selftest(unsigned long long budget_ns, bool signal, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(budget_ns, signal ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t fused_timed_out(bool* out) {
   int h = 0;
   cudaError_t e = cudaMemcpyFromSymbol(&h, g_fused_timeout, sizeof(int));

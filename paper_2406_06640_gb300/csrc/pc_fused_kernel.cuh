@@ -25,9 +25,10 @@ __device__ __forceinline__ void red_add_l2(float* a, float v) {
 // instantiates the kernel; read and cleared by fused_timed_out)
 static __device__ int g_fused_timeout;
 
-// ---- bounded mbarrier wait (global timer)
+// ---- bounded mbarrier wait (global timer); false once `budget_ns` has passed without the phase
 constexpr unsigned long long kFusedWaitNs = 2000000000ull;  // 2 s
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
+                                                  unsigned long long budget_ns = kFusedWaitNs) {
   const unsigned long long t0 = global_ns();
   for (;;) {
     uint32_t ok;
@@ -39,7 +40,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) 
         : "r"(bar), "r"(phase)
         : "memory");
     if (ok) return true;
-    if (global_ns() - t0 > kFusedWaitNs) return false;
+    if (global_ns() - t0 > budget_ns) return false;
   }
 }
 // largest K * ceil(M / K) over the cluster sizes 1..8 (rows of the per-source slots)

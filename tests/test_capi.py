@@ -92,6 +92,13 @@ def test_null_arguments():
     assert lib.ptycho_destroy(None) == 0
 
 
+def test_wait_selftest_budget_is_validated_before_device_work():
+    lib = pg.load()
+    for bad in (-1, 2_000_000_001):
+        assert lib.ptycho_wait_selftest(ctypes.c_int64(bad), 0, None) == 1
+        assert "budget_ns" in lib.ptycho_last_error().decode()
+
+
 def test_version_string():
     assert "sm_103a" in pg.version()
 

@@ -379,3 +379,32 @@ def test_errors_reported_by_status():
     with pytest.raises(PtychoError) as ei:
         rec.error()
     assert ei.value.status == 1
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A bounded device wait of the fused kernels' kind on a barrier nothing completes gives up after
+    its budget, the host reads PTYCHO_ETIMEOUT, and the device keeps working (failure detection
+    without a fault: a short budget, no trap, no endless loop)."""
+    import ctypes
+    import time
+
+    from paper_2406_06640_gb300 import binding
+
+    dev = _dev()
+    lib = binding.load()
+    s = torch.cuda.Stream(device=dev)
+    sp = ctypes.c_void_p(s.cuda_stream)
+    assert lib.ptycho_wait_selftest(ctypes.c_int64(5_000_000), 1, sp) == 0  # completed barrier: no wait
+    t0 = time.perf_counter()
+    st = lib.ptycho_wait_selftest(ctypes.c_int64(20_000_000), 0, sp)  # nothing arrives: 20 ms budget
+    dt = time.perf_counter() - t0
+    assert st == 6, lib.ptycho_last_error().decode()
+    assert "gave up" in lib.ptycho_last_error().decode()
+    assert 0.02 <= dt < 1.5, dt  # it waited its budget, then returned
+    # the flag was read and cleared, and the context is intact
+    assert lib.ptycho_wait_selftest(ctypes.c_int64(5_000_000), 1, sp) == 0
+    x = torch.arange(4.0, device=dev)
+    assert float(x.sum()) == 6.0
+    p = make_problem(0, scan_side=2, obj_side=96)
+    O, P, E = run_gpu(p, p.params, 1)
+    assert np.isfinite(E).all()
