@@ -58,6 +58,25 @@ PC_ENGINE = [
     ("pc-DM reflection 2 psi_ov - psi lost", "chi = 2.0 * psi_ov - psi[n]", "chi = psi_ov - psi[n]"),
     ("pc-DM state replaced, not differenced", "psi[n] = psi[n] + propagate_backward(Chi_new, prm) - psi_ov",
      "psi[n] = propagate_backward(Chi_new, prm)"),
+    ("window excludes its first iteration", "return any(lo <= t <= hi for (lo, hi) in windows)",
+     "return any(lo < t <= hi for (lo, hi) in windows)"),
+    ("C_n not clamped", "out[n] = min(max(num / den, cmin), cmax)", "out[n] = num / den"),
+    ("constraint touches uncovered pixels", "return np.where(covered, a_c * np.exp(1j * phi_c), O)",
+     "return a_c * np.exp(1j * phi_c)"),
+    ("Eq. 6 blurs the intensity, then takes the root", "AG = blur(np.sqrt(S), g)", "AG = np.sqrt(blur(S, g))"),
+    ("modulus keeps |Psi| only", "return R[None] * Psi, Ihat", "return R[None] * np.abs(Psi), Ihat"),
+    ("rPIE object denominator without (1 - alpha)", "return (1.0 - prm.rpie_alpha_obj, prm.rpie_alpha_obj),",
+     "return (1.0, prm.rpie_alpha_obj),"),
+    ("probe step with the object's beta",
+     "        P_new = P + np.stack([_normalised_step(prm.beta_probe, NP[k], DP, *c_probe) for k in range(K)])\n"
+     "    else:\n        P_new = P.copy()\n    return O_new, P_new, errnum",
+     "        P_new = P + np.stack([_normalised_step(prm.beta_obj, NP[k], DP, *c_probe) for k in range(K)])\n"
+     "    else:\n        P_new = P.copy()\n    return O_new, P_new, errnum"),
+    ("batches all start from the iteration's state", "        O, P, en = _batch_step(I, positions, parts[b], O, P, prm, t, eps, g)",
+     "        O1, P1, en = _batch_step(I, positions, parts[b], O if b < 0 else O, P, prm, t, eps, g)\n"
+     "        O, P = (O1, P1) if b == len(parts) - 1 else (O, P)"),
+    ("last batch dropped", "return [perm[b:b + prm.minibatch] for b in range(0, N, prm.minibatch)]",
+     "return [perm[b:b + prm.minibatch] for b in range(0, N - prm.minibatch, prm.minibatch)]"),
 ]
 
 MONO = [
