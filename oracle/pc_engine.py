@@ -210,7 +210,7 @@ def in_window(t: int, windows) -> bool:
 
 
 # ----------------------------------------------------------------------------------------
-# one iteration and the driver
+# one iteration and the iteration loop
 # ----------------------------------------------------------------------------------------
 
 def _normalised_step(beta, num, den, c_den, c_max):

@@ -843,7 +843,7 @@ __global__ void k_halo_pack(const GemmArgs g, uint16_t* dst) {
   }
 }
 
-// the driver's tensor-map encoder, looked up once through the runtime (no link-time libcuda dependence)
+// the CUDA driver API's tensor-map encoder, looked up once through the runtime (no link-time libcuda dependence)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
