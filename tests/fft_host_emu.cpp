@@ -3,20 +3,24 @@
 // __syncthreads as a std::barrier over the tile's threads. The line-internal swaps' __syncwarp becomes
 // the same barrier: every thread of the tile reaches each of them in the same order, and a barrier
 // over the whole tile orders at least what the warp barrier orders on the device.
-// Usage: fft_host_emu M V   -> prints "forward <rel L2>  roundtrip <rel L2>" against a direct 2-D DFT in
+// Usage: fft_host_emu M V      -> prints "forward <rel L2>  roundtrip <rel L2>" against a direct 2-D DFT in
 // double precision (COL layout out of the forward transform, ROW layout back from the inverse).
+//        fft_host_emu line BL  -> the same for one BL-point line of the staged passes (line_fft of
+// big_line.cuh on 16 threads; frequencies by line_freq).
 #include <barrier>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <random>
+#include <string>
 #include <thread>
 #include <vector>
 
 static std::barrier<>* g_bar;
 #define __syncthreads() g_bar->arrive_and_wait()
 #define __syncwarp() g_bar->arrive_and_wait()
+#include "big_line.cuh"
 #include "fft.cuh"
 
 using namespace ptycho;
@@ -91,7 +95,56 @@ static int run() {
   return 0;
 }
 
+template <int BL>
+static int run_line() {
+  using BS_ = BigShape<BL>;
+  constexpr int E = BS_::E;
+  std::mt19937 rng(BL);
+  std::normal_distribution<double> nd;
+  std::vector<cd> x(BL);
+  for (auto& z : x) z = cd(nd(rng), nd(rng));
+  auto W = [](long e) {
+    const double t = -2.0 * M_PI * (double)(((e % BL) + BL) % BL) / BL;
+    return cd(std::cos(t), std::sin(t));
+  };
+  std::vector<float2> sw(BS_::SWN), tw(BS_::TWN);
+  for (int i = 0; i < BS_::TWN; ++i) {  // as load_tw: W_BL^(t k2) for k2 < E, zero beyond
+    const int t = i / BS_::TWS, k2 = i % BS_::TWS;
+    const cd w = k2 < E ? W((long)t * k2) : cd(0, 0);
+    tw[i] = make_float2((float)w.real(), (float)w.imag());
+  }
+  std::vector<cd> F(BL), B(BL);
+  std::barrier<> bar(BT);
+  g_bar = &bar;
+  std::vector<std::thread> th;
+  for (int t = 0; t < BT; ++t)
+    th.emplace_back([&, t] {
+      float2 a[E];
+      for (int j = 0; j < E; ++j) a[j] = make_float2((float)x[t + 16 * j].real(), (float)x[t + 16 * j].imag());
+      line_fft<BL, false>(a, sw.data(), tw.data(), t);
+      for (int r = 0; r < E; ++r) F[line_freq<BL>(t, r)] = cd(a[r].x, a[r].y);
+      line_fft<BL, true>(a, sw.data(), tw.data(), t);
+      for (int j = 0; j < E; ++j) B[t + 16 * j] = cd(a[j].x, a[j].y);
+    });
+  for (auto& t : th) t.join();
+  double e1 = 0, n1 = 0, e2 = 0, n2 = 0;
+  for (int k = 0; k < BL; ++k) {
+    cd s = 0;
+    for (int n = 0; n < BL; ++n) s += x[n] * W((long)k * n);
+    e1 += std::norm(F[k] - s);
+    n1 += std::norm(s);
+    e2 += std::norm(B[k] / (double)BL - x[k]);
+    n2 += std::norm(x[k]);
+  }
+  std::printf("forward %.3e roundtrip %.3e\n", std::sqrt(e1 / n1), std::sqrt(e2 / n2));
+  return 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc == 3 && std::string(argv[1]) == "line") {
+    const int BL = std::atoi(argv[2]);
+    return BL == 256 ? run_line<256>() : BL == 512 ? run_line<512>() : 2;
+  }
   if (argc != 3) return 2;
   const int M = std::atoi(argv[1]), V = std::atoi(argv[2]);
   if (M == 8 && V == 1) return run<8, 1>();

@@ -39,3 +39,14 @@ def test_device_fft_source_matches_a_direct_dft(emu, M, V):
     _, fwd, _, rt = r.stdout.split()
     # FP32 butterflies and twiddles: ~1e-7 relative per transform (log2(M^2) stages)
     assert float(fwd) < 5e-6 and float(rt) < 5e-6, r.stdout
+
+
+@pytest.mark.parametrize("BL", [256, 512])
+def test_staged_line_transform_source_matches_a_direct_dft(emu, BL):
+    """line_fft of the staged passes (big_line.cuh): one BL-point line on 16 threads, frequencies by
+    line_freq, and the inverse back to x = t + 16 j."""
+    r = subprocess.run([str(emu), "line", str(BL)], stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout
+    _, fwd, _, rt = r.stdout.split()
+    assert float(fwd) < 5e-6 and float(rt) < 5e-6, r.stdout

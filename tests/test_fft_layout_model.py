@@ -158,12 +158,12 @@ def test_model_sees_a_conflicting_stride():
     assert conf > 0
 
 
-# ---------------------------------------------------------------- staged line transforms (csrc/big.cu)
-BIG = FFT.parent / "big.cu"
+# ---------------------------------------------------------------- staged line transforms (csrc/big_line.cuh)
+BIG = FFT.parent / "big_line.cuh"
 
 
 def _big_shape(BL):
-    """LINES and TWS of BigShape<BL>, and the swap row stride BS = BT + 1, read from big.cu."""
+    """LINES and TWS of BigShape<BL>, and the swap row stride BS = BT + 1, read from big_line.cuh."""
     src = BIG.read_text()
     bt = int(re.search(r"constexpr int BT = (\d+);", src).group(1))
     bs = bt + 1
