@@ -167,3 +167,64 @@ def test_batch_launch_count_arguments():
     n = ctypes.c_int32(-1)
     assert lib.ptycho_batch_launches(None, ctypes.byref(n)) == 1
     assert lib.ptycho_launches_per_iteration(None, 1) == 0
+
+
+def test_ctypes_gen_spec_layout_matches_c(tmp_path):
+    from paper_2406_06640_gb300.binding import GenSpec
+
+    fields = [f for f, _ in GenSpec._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "ptycho.h"', "int main(void) {",
+           '  printf("%zu\\n", sizeof(ptycho_gen_spec));']
+    src += [f'  printf("%zu\\n", offsetof(ptycho_gen_spec, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "gen_layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "gen_layout"
+    subprocess.run(["gcc", "-std=c99", f"-I{INCLUDE}", str(c), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(GenSpec)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(GenSpec, f).offset == off, f
+
+
+@pytest.mark.parametrize("S,C,batch", [(20, 32, 64), (16, 8, 64), (128, 80, 64), (128, 32, 0), (128, 32, 1025),
+                                       (16, 32, 1), (528, 32, 64)])
+def test_unet_create_validation(S, C, batch):
+    lib = pg.load()
+    h = ctypes.c_void_p()
+    assert lib.ptycho_unet_create(S, C, batch, 0, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.ptycho_unet_create(128, 32, 64, 0, None, None) == 1
+
+
+def test_warmstart_and_network_null_handles():
+    lib = pg.load()
+    x = np.zeros(16, np.float32)
+    sig = ctypes.c_double()
+    assert lib.ptycho_unet_param_count(None) == 0
+    assert lib.ptycho_unet_set_params(None, x.ctypes.data, 16) == 1
+    assert lib.ptycho_unet_destroy(None) == 0
+    assert lib.ptycho_warmstart(None, x.ctypes.data, x.ctypes.data, 1, 8, 8, 1.0, x.ctypes.data, ctypes.byref(sig)) == 1
+
+
+def test_generator_validation_before_device_work():
+    from paper_2406_06640_gb300.binding import GenSpec
+
+    lib = pg.load()
+    buf = np.zeros(64, np.float32)  # 16-byte aligned by numpy's allocator
+    ok = dict(S=128, noise=1, dose=2e4, lattice_a=16.0, peak=0.1, peak_sd=1.5, cutoff=6.0, vacancy=0.05,
+              target_scale=1.0, key=7)
+
+    def status(n=1, params=None, **over):
+        spec = GenSpec(**dict(ok, **over))
+        p = buf.ctypes.data if params is None else params
+        return lib.ptycho_generate(ctypes.byref(spec), buf.ctypes.data, p, n, 0, None, None, None, None, None, None)
+
+    assert lib.ptycho_generate(None, buf.ctypes.data, buf.ctypes.data, 1, 0, None, None, None, None, None, None) == 1
+    assert status(S=32) == 4
+    assert status(n=-1) == 1
+    for bad in (dict(dose=0.0), dict(lattice_a=-1.0), dict(peak_sd=0.0), dict(cutoff=-1.0), dict(cutoff=40.0),
+                dict(vacancy=1.5), dict(target_scale=0.0), dict(peak=float("nan"))):
+        assert status(**bad) == 1, bad
+    assert status(params=buf.ctypes.data + 4) == 1  # params not 16-byte aligned
+    assert "aligned" in lib.ptycho_last_error().decode()
