@@ -228,3 +228,35 @@ def test_generator_validation_before_device_work():
         assert status(**bad) == 1, bad
     assert status(params=buf.ctypes.data + 4) == 1  # params not 16-byte aligned
     assert "aligned" in lib.ptycho_last_error().decode()
+
+
+def test_entry_points_reject_null_handles_before_device_work():
+    """Every plan, batch, network and utility call given a NULL handle or output returns PTYCHO_EINVAL
+    (or its documented default) from the host, without touching a device."""
+    lib = pg.load()
+    P = ctypes.c_void_p
+    d, i32 = ctypes.c_double(), ctypes.c_int32()
+    buf = (ctypes.c_double * 4)()
+    f = np.zeros(64, np.float32)
+    assert lib.ptycho_error_history(None, buf, 4, ctypes.byref(i32)) == 1
+    assert lib.ptycho_profile(None, 1) == 1
+    assert lib.ptycho_profile_read(None, ctypes.byref(d), ctypes.byref(i32)) == 1
+    assert lib.ptycho_launches_per_iteration(None, 1) == 0
+    assert lib.ptycho_staged_chunk(None) == 0
+    assert lib.ptycho_iterate_batch(None, None, None, 1) == 1
+    assert lib.ptycho_error_batch(None, ctypes.byref(d)) == 1
+    assert lib.ptycho_batch_classes(None, 0, None, ctypes.byref(i32)) == 1
+    assert lib.ptycho_batch_launches(None, ctypes.byref(i32)) == 1
+    assert lib.ptycho_measure_fp32_peak(None, None, None) == 1
+    assert lib.ptycho_unet_forward(None, f.ctypes.data, None, None) == 1
+    assert lib.ptycho_unet_get_params(None, f.ctypes.data, 64) == 1
+    assert lib.ptycho_unet_gradients(None, f.ctypes.data, f.ctypes.data, f.ctypes.data, 0.1, ctypes.byref(d), None) == 1
+    assert lib.ptycho_unet_train_step(None, f.ctypes.data, f.ctypes.data, f.ctypes.data, 0.1, 1e-3, ctypes.byref(d)) == 1
+    lib.ptycho_iterate_static.argtypes = [P, P, P, P, P, ctypes.c_int32, P, P]
+    lib.ptycho_iterate_static.restype = ctypes.c_int
+    assert lib.ptycho_iterate_static(None, None, None, None, None, 1, None, None) == 1
+    assert "params is NULL" in lib.ptycho_last_error().decode()
+    lib.ptycho_gemm_bf16.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    lib.ptycho_gemm_bf16.restype = ctypes.c_int
+    assert lib.ptycho_gemm_bf16(None, None, None, 128, 16, 64, 0, None) == 1
+    assert lib.ptycho_set_staged_chunk(3) == 1
